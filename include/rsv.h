@@ -1,0 +1,163 @@
+/*
+ * rsv.h -- C ABI of librsv: the Hybrid Monte Carlo (HMC) volatility update of
+ * the realized stochastic volatility (RSV) model on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: T. Takaishi, "GPU Computing in Bayesian Inference of Realized
+ * Stochastic Volatility Model", arXiv:1603.08114.
+ *   model            eqs. (1)-(3)   y_t = e^{h_t/2} eps_t,  lnRV_t = xi + h_t + u_t,
+ *                                   h_{t+1} = mu + phi (h_t - mu) + eta_t
+ *   parameters       Sec. 2         theta = (phi, mu, xi, sigma_eta^2, sigma_u^2)
+ *   Hamiltonian      Sec. 3         H(p, h) = 1/2 sum_t p_t^2 + S(h),  S = -ln f(h | theta)
+ *   leapfrog         eqs. (6)-(8)   h += dtau/2 p;  p -= dtau dS/dh;  h += dtau/2 p
+ *   trajectory       Sec. 3         k = n_md repetitions, length l = n_md * dtau
+ *   Metropolis       Sec. 3         accept h' with probability min{1, e^{-dH}}
+ * S(h) (the paper defers f to its ref. [RSV]) is, constants dropped,
+ *   S = sum_t [h_t/2 + (y_t^2/2) e^{-h_t} + (lnRV_t - xi - h_t)^2/(2 sigma_u^2)]
+ *     + (1 - phi^2)(h_1 - mu)^2/(2 sigma_eta^2)
+ *     + sum_{t<T} (h_{t+1} - mu - phi (h_t - mu))^2/(2 sigma_eta^2).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers on the context's device, owned by the
+ *    caller; the library never frees them.  Arrays are dense, 0-based, indexed
+ *    by site t = 0..T-1 (the paper's t = 1..T).  Scalars marked "host" are host
+ *    values.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous on that stream; outputs are valid after the stream
+ *    is synchronised.
+ *  - Arguments are checked before any launch; on RSV_EINVAL nothing is launched
+ *    and no output is touched.  The library never aborts or traps.
+ *  - Conditions found on the device (a non-finite dH, a wait that ran out of
+ *    time) are recorded in a status word of the context and returned by
+ *    rsv_sync_status().
+ *  - rsv_last_error() gives a text for the last non-OK status of the calling
+ *    thread.
+ *  - A context is bound to one device and must not be used from two host
+ *    threads at once.
+ */
+#ifndef RSV_H_
+#define RSV_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSV_ABI_VERSION 1
+
+/* theta of Sec. 2.  Valid: |phi| < 1, sig_eta2 > 0, sig_u2 > 0, all finite. */
+typedef struct rsv_theta {
+    double phi, mu, xi, sig_eta2, sig_u2;
+} rsv_theta;
+
+typedef enum rsv_status {
+    RSV_OK = 0,
+    RSV_EINVAL = 1,       /* bad argument; nothing launched                     */
+    RSV_ENOMEM = 2,       /* workspace allocation failed                        */
+    RSV_ECUDA = 3,        /* a CUDA call failed (text in rsv_last_error)        */
+    RSV_ENONFINITE = 4,   /* a dH was NaN/Inf; that trajectory was rejected     */
+    RSV_ETIMEOUT = 5      /* a device-side wait gave up; results are invalid    */
+} rsv_status;
+
+/* RSV_FP64: every step in FP64.
+ * RSV_MIXED: leapfrog force and updates in FP32 on a compensated (hi, lo)
+ * FP32 state; dH from per-site differences in double-float, accumulated in
+ * FP64; Metropolis test in FP64. */
+typedef enum rsv_precision { RSV_FP64 = 0, RSV_MIXED = 1 } rsv_precision;
+
+typedef struct rsv_ctx rsv_ctx;
+
+/* ---- context --------------------------------------------------------------
+ * rsv_create: bind a context to CUDA device `device` (makes it current).
+ * Owns a small workspace (reduction partials, counters, a status word) that
+ * grows on demand; rsv_reserve() grows it ahead of time so that later calls
+ * allocate nothing (needed before CUDA-graph capture).
+ * rsv_destroy: frees the workspace; NULL is a no-op. */
+rsv_status rsv_create(rsv_ctx** ctx, int device);
+void rsv_destroy(rsv_ctx* ctx);
+rsv_status rsv_reserve(rsv_ctx* ctx, int64_t max_T, int64_t max_series);
+const char* rsv_last_error(void);
+int rsv_abi_version(void);
+/* Synchronise `stream`, return and clear the device status word. */
+rsv_status rsv_sync_status(rsv_ctx* ctx, void* stream);
+/* Fix the tiling of single-series trajectories (rsv_hmc_trajectory,
+ * rsv_hmc_chain): `threads` per block (multiple of 32; <= 256 FP64, <= 384
+ * mixed), `sites_per_thread` (FP64: 4, 8, 16, 28; mixed: 4, 8, 16, 20) and
+ * `tile` owned sites per block (tile + 2 (n_md + 1) + 3 <= threads *
+ * sites_per_thread, else the call that uses it fails with RSV_EINVAL).
+ * All zero restores the automatic plan.  Results do not depend on the tiling. */
+rsv_status rsv_set_schedule(rsv_ctx* ctx, int threads, int sites_per_thread, int64_t tile);
+
+/* ---- S(h) -----------------------------------------------------------------
+ * S(h) of Sec. 3 (see above), FP64, deterministic reduction order.
+ * h, y, lnrv: [T] FP64.  S_out: device FP64 scalar.  T >= 1. */
+rsv_status rsv_action(rsv_ctx* ctx, const double* h, const double* y, const double* lnrv,
+                      int64_t T, rsv_theta theta, double* S_out, void* stream);
+
+/* ---- dS/dh ----------------------------------------------------------------
+ * F_t = dS/dh_t, the derivative in eq. (7):
+ *   F_t = 1/2 - (y_t^2/2) e^{-h_t} - (lnRV_t - xi - h_t)/sigma_u^2 + AR_t,
+ *   AR_t = [(1+phi^2) x_t - phi (x_{t-1} + x_{t+1})]/sigma_eta^2 inside,
+ *   AR_0 = (x_0 - phi x_1)/sigma_eta^2, AR_{T-1} = (x_{T-1} - phi x_{T-2})/sigma_eta^2,
+ *   AR_0 = (1 - phi^2) x_0/sigma_eta^2 if T = 1, with x_t = h_t - mu.
+ * F_out: [T] FP64 (must not alias h). */
+rsv_status rsv_force(rsv_ctx* ctx, const double* h, const double* y, const double* lnrv,
+                     int64_t T, rsv_theta theta, double* F_out, void* stream);
+
+/* ---- one HMC trajectory (Sec. 3) ------------------------------------------
+ * n_md leapfrog steps of size dtau (eqs. (6)-(8)) from (h, p), then
+ * dH = H(p', h') - H(p, h) and the Metropolis test: accept iff ln u < -dH
+ * (a NaN dH rejects and sets RSV_ENONFINITE in the status word).
+ *  h     [T] FP64 in/out: on accept h', else unchanged.
+ *  p     [T] FP64 in/out or NULL.  Non-NULL: the initial momenta p, replaced
+ *        by p' (the end of the trajectory, accepted or not).  NULL: momenta
+ *        p_t ~ N(0, m_t) are drawn from Philox4x64-10 with key {seed, 0} and
+ *        counter {t/4, traj, 0, 0}, Box-Muller on 53-bit (FP64) or 23-bit
+ *        (MIXED, computed in FP32) uniforms (k + 1/2) 2^-bits from the top
+ *        bits of each 64-bit word.
+ *  minv  [T] FP32 inverse diagonal mass 1/m_t > 0, or NULL for m = 1.  With a
+ *        mass, eq. (6) reads h += dtau/2 p/m and H = 1/2 sum p^2/m + S.
+ *  log_u device FP64 scalar ln u, or NULL to draw u from Philox counter
+ *        {0, traj, 1, 0} (53-bit uniform).
+ *  dH_out device FP64 scalar; accept_out device int32 scalar (1 accepted).
+ * Requires T >= 1, n_md >= 1, dtau > 0 finite. */
+rsv_status rsv_hmc_trajectory(rsv_ctx* ctx, double* h, double* p, const double* y,
+                              const double* lnrv, int64_t T, rsv_theta theta, const float* minv,
+                              int n_md, double dtau, rsv_precision prec, uint64_t seed,
+                              uint64_t traj, const double* log_u, double* dH_out,
+                              int32_t* accept_out, void* stream);
+
+/* ---- a chain of trajectories ----------------------------------------------
+ * n_traj HMC trajectories (Sec. 3) with indices traj0 .. traj0+n_traj-1 and
+ * Philox draws as in rsv_hmc_trajectory; if update_theta != 0 each trajectory
+ * is followed by a Gibbs sweep of theta (xi, sigma_u^2, mu, sigma_eta^2, phi;
+ * the paper does not describe its theta update) drawing from Philox counter
+ * {block, traj, 2, 0}.
+ *  h       [T] FP64 in/out: chain state.
+ *  theta   device FP64 [5] = (phi, mu, xi, sigma_eta^2, sigma_u^2), in/out.
+ *  dH_out, accept_out: device [n_traj] FP64 / int32, or NULL.
+ *  theta_out: device [n_traj][5] FP64 (theta after each sweep), or NULL.
+ *  snaps:  device FP32 [n_traj/thin][T]: h after every thin-th trajectory
+ *          (thin >= 1), or NULL.
+ *  fallback_window: if > 0 and minv != NULL, after every fallback_window
+ *          trajectories the mass is switched to m = 1 for the rest of the
+ *          call when that window's acceptance rate is below 0.6.
+ *  mass_used_out: device int32 scalar (1 while the mass is in use), or NULL. */
+rsv_status rsv_hmc_chain(rsv_ctx* ctx, double* h, const double* y, const double* lnrv, int64_t T,
+                         double* theta, const float* minv, int n_md, double dtau,
+                         rsv_precision prec, uint64_t seed, uint64_t traj0, int64_t n_traj,
+                         int update_theta, double* dH_out, int32_t* accept_out,
+                         double* theta_out, float* snaps, int64_t thin, int fallback_window,
+                         int32_t* mass_used_out, void* stream);
+
+/* ---- Philox momenta (exposed for tests of the generator) -----------------
+ * p_t exactly as rsv_hmc_trajectory draws them for (seed, series, traj);
+ * bits = 53 (FP64 path) or 23 (MIXED path). p_out [T] FP64. */
+rsv_status rsv_draw_momenta(rsv_ctx* ctx, uint64_t seed, uint64_t series, uint64_t traj,
+                            int64_t T, const float* minv, int bits, double* p_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSV_H_ */

@@ -1,0 +1,440 @@
+// rsv_api.cu -- the extern "C" entry points of librsv (declared in include/rsv.h).
+//
+// Argument checks, the context's workspace and the order of launches on the
+// caller's stream.  All arithmetic of the method runs in the kernels of
+// rsv_traj.cu, rsv_simple.cu and the other .cu files of this directory.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "rsv.h"
+#include "rsv_ctx.cuh"
+#include "rsv_simple.cuh"
+#include "rsv_traj.cuh"
+
+using namespace rsv;
+
+namespace rsv {
+
+thread_local std::string g_last_error;
+
+rsv_status fail(rsv_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+rsv_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(RSV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool theta_ok(const rsv_theta& t)
+{
+    return std::isfinite(t.phi) && std::isfinite(t.mu) && std::isfinite(t.xi) &&
+           std::isfinite(t.sig_eta2) && std::isfinite(t.sig_u2) && std::fabs(t.phi) < 1.0 &&
+           t.sig_eta2 > 0.0 && t.sig_u2 > 0.0;
+}
+
+ThetaD to_dev(const rsv_theta& t) { return ThetaD{t.phi, t.mu, t.xi, t.sig_eta2, t.sig_u2}; }
+
+// Grow a workspace buffer to at least `bytes`; never shrinks.
+rsv_status Buf::ensure(size_t bytes)
+{
+    if (bytes <= cap) return RSV_OK;
+    if (capture_active())
+        return fail(RSV_EINVAL, "workspace must grow during stream capture; call rsv_reserve first");
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    size_t b = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&ptr, b);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        (void)cudaGetLastError();
+        return fail(RSV_ENOMEM, "cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+    }
+    cap = b;
+    return RSV_OK;
+}
+void Buf::release()
+{
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+}
+
+bool capture_active_on(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+thread_local cudaStream_t g_cur_stream = nullptr;
+bool capture_active() { return capture_active_on(g_cur_stream); }
+
+rsv_status ctx_begin(rsv_ctx* c, void* stream)
+{
+    if (!c) return fail(RSV_EINVAL, "null context");
+    g_cur_stream = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return RSV_OK;
+}
+
+rsv_status ctx_ensure_partials(rsv_ctx* c, int64_t n)
+{
+    return c->partials.ensure((size_t)n * sizeof(double));
+}
+
+rsv_status ctx_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, TileCfg& cfg)
+{
+    if (c->sched_nt) {
+        cfg = fixed_tiles(T, n_md, mixed, mass, c->sched_nt, c->sched_j, c->sched_tile);
+        if (cfg.nt == 0)
+            return fail(RSV_EINVAL, "schedule (%d threads, %d sites/thread, tile %lld) does not "
+                        "fit this call", c->sched_nt, c->sched_j, (long long)c->sched_tile);
+    } else {
+        cfg = plan_tiles(T, n_md, mixed, mass, c->num_sms);
+        if (cfg.nt == 0) return fail(RSV_EINVAL, "n_md too large for an on-chip window");
+    }
+    return ctx_ensure_partials(c, cfg.grid);
+}
+
+}  // namespace rsv
+
+extern "C" {
+
+const char* rsv_last_error(void) { return g_last_error.c_str(); }
+int rsv_abi_version(void) { return RSV_ABI_VERSION; }
+
+rsv_status rsv_create(rsv_ctx** out, int device)
+{
+    if (!out) return fail(RSV_EINVAL, "null output pointer");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(RSV_EINVAL, "device %d out of range", device);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    rsv_ctx* c = new rsv_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    g_cur_stream = nullptr;
+    rsv_status st = c->ints.ensure(kIntSlots * sizeof(int));
+    if (st == RSV_OK) st = c->partials.ensure(4096 * sizeof(double));
+    if (st == RSV_OK) st = c->scalars.ensure(64 * sizeof(double));
+    if (st != RSV_OK) {
+        rsv_destroy(c);
+        return st;
+    }
+    e = cudaMemset(c->ints.ptr, 0, kIntSlots * sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        rsv_destroy(c);
+        return cuda_fail(e, "workspace init");
+    }
+    *out = c;
+    return RSV_OK;
+}
+
+void rsv_destroy(rsv_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (Buf* b : c->all_bufs()) b->release();
+    delete c;
+}
+
+rsv_status rsv_reserve(rsv_ctx* c, int64_t max_T, int64_t max_series)
+{
+    rsv_status st = ctx_begin(c, nullptr);
+    if (st != RSV_OK) return st;
+    if (max_T < 0 || max_series < 0) return fail(RSV_EINVAL, "negative reserve size");
+    const size_t T = (size_t)max_T;
+    if ((st = c->dbuf0.ensure(T * 8)) != RSV_OK) return st;
+    if ((st = c->dbuf1.ensure(T * 8)) != RSV_OK) return st;
+    if ((st = c->fbuf0.ensure(T * 8)) != RSV_OK) return st;
+    if ((st = c->fbuf1.ensure(T * 8)) != RSV_OK) return st;
+    if ((st = c->a_f.ensure(T * 4)) != RSV_OK) return st;
+    if ((st = c->b0_f.ensure(T * 4)) != RSV_OK) return st;
+    if ((st = c->lr_f.ensure(T * 8)) != RSV_OK) return st;
+    if ((st = ctx_ensure_partials(c, (max_T / 64 + 4096))) != RSV_OK) return st;
+    (void)max_series;
+    return RSV_OK;
+}
+
+rsv_status rsv_set_schedule(rsv_ctx* c, int threads, int sites_per_thread, int64_t tile)
+{
+    if (!c) return fail(RSV_EINVAL, "null context");
+    if (threads == 0 && sites_per_thread == 0 && tile == 0) {
+        c->sched_nt = c->sched_j = 0;
+        c->sched_tile = 0;
+        return RSV_OK;
+    }
+    if (threads < 32 || threads % 32 || sites_per_thread < 1 || tile < 1)
+        return fail(RSV_EINVAL, "bad schedule");
+    c->sched_nt = threads;
+    c->sched_j = sites_per_thread;
+    c->sched_tile = tile;
+    return RSV_OK;
+}
+
+rsv_status rsv_sync_status(rsv_ctx* c, void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int w = 0;
+    e = cudaMemcpy(&w, c->ints.as<int>() + kStatus, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read status");
+    e = cudaMemset(c->ints.as<int>() + kStatus, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+    if (w & ST_TIMEOUT) return fail(RSV_ETIMEOUT, "a device-side wait ran out of time");
+    if (w & ST_NONFINITE) return fail(RSV_ENONFINITE, "a dH was not finite (trajectory rejected)");
+    return RSV_OK;
+}
+
+rsv_status rsv_action(rsv_ctx* c, const double* h, const double* y, const double* lnrv,
+                      int64_t T, rsv_theta theta, double* S_out, void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    if (!h || !y || !lnrv || !S_out) return fail(RSV_EINVAL, "null array argument");
+    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
+    if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
+    if ((st = ctx_ensure_partials(c, action_grid(T))) != RSV_OK) return st;
+    cudaError_t e = launch_action(h, y, lnrv, T, to_dev(theta), c->partials.as<double>(),
+                                  reinterpret_cast<unsigned*>(c->ints.as<int>() + kActionCounter),
+                                  S_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? RSV_OK : cuda_fail(e, "action kernel");
+}
+
+rsv_status rsv_force(rsv_ctx* c, const double* h, const double* y, const double* lnrv,
+                     int64_t T, rsv_theta theta, double* F_out, void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    if (!h || !y || !lnrv || !F_out) return fail(RSV_EINVAL, "null array argument");
+    if (F_out == h) return fail(RSV_EINVAL, "F_out must not alias h");
+    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
+    if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
+    cudaError_t e = launch_force(h, y, lnrv, T, to_dev(theta), F_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? RSV_OK : cuda_fail(e, "force kernel");
+}
+
+rsv_status rsv_draw_momenta(rsv_ctx* c, uint64_t seed, uint64_t series, uint64_t traj,
+                            int64_t T, const float* minv, int bits, double* p_out, void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    if (!p_out) return fail(RSV_EINVAL, "null p_out");
+    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1");
+    if (bits != 53 && bits != 23) return fail(RSV_EINVAL, "bits must be 53 or 23");
+    cudaError_t e = launch_draw_momenta(seed, series, traj, T, minv, bits, p_out,
+                                        (cudaStream_t)stream);
+    return e == cudaSuccess ? RSV_OK : cuda_fail(e, "momentum kernel");
+}
+
+rsv_status rsv_hmc_trajectory(rsv_ctx* c, double* h, double* p, const double* y,
+                              const double* lnrv, int64_t T, rsv_theta theta, const float* minv,
+                              int n_md, double dtau, rsv_precision prec, uint64_t seed,
+                              uint64_t traj, const double* log_u, double* dH_out,
+                              int32_t* accept_out, void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    if (!h || !y || !lnrv || !dH_out || !accept_out) return fail(RSV_EINVAL, "null argument");
+    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
+    if (n_md < 1) return fail(RSV_EINVAL, "n_md must be >= 1");
+    if (!(dtau > 0.0) || !std::isfinite(dtau)) return fail(RSV_EINVAL, "dtau must be > 0");
+    if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
+    if (prec != RSV_FP64 && prec != RSV_MIXED) return fail(RSV_EINVAL, "bad precision");
+    if (n_md > (1 << 20)) return fail(RSV_EINVAL, "n_md too large");
+    const bool mixed = prec == RSV_MIXED, mass = minv != nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    TileCfg cfg;
+    if ((st = ctx_plan(c, T, n_md, mixed, mass, cfg)) != RSV_OK) return st;
+    const size_t Tz = (size_t)T;
+    if (p && (st = c->dbuf1.ensure(Tz * 8)) != RSV_OK) return st;  // p'
+    if (!mixed && (st = c->dbuf0.ensure(Tz * 8)) != RSV_OK) return st;  // h'
+    if (mixed) {
+        if ((st = c->fbuf0.ensure(Tz * 8)) != RSV_OK) return st;
+        if ((st = c->fbuf1.ensure(Tz * 8)) != RSV_OK) return st;
+        if ((st = c->a_f.ensure(Tz * 4)) != RSV_OK) return st;
+        if ((st = c->b0_f.ensure(Tz * 4)) != RSV_OK) return st;
+        if ((st = c->lr_f.ensure(Tz * 8)) != RSV_OK) return st;
+    }
+    int* ints = c->ints.as<int>();
+    TrajArgs a;
+    memset(&a, 0, sizeof(a));
+    a.cur = nullptr;
+    a.p_in = p;
+    a.p_out = p ? c->dbuf1.as<double>() : nullptr;
+    a.y = y;
+    a.lnrv = lnrv;
+    a.minv = minv;
+    a.mass_on = nullptr;
+    a.theta = nullptr;
+    a.th_inline = to_dev(theta);
+    a.T = T;
+    a.tile = cfg.tile;
+    a.K = n_md + 1;
+    a.n_md = n_md;
+    a.dtau = dtau;
+    a.seed = seed;
+    a.series = 0;
+    a.traj = traj;
+    a.log_u = log_u;
+    a.partials = c->partials.as<double>();
+    a.counter = reinterpret_cast<unsigned*>(ints + kTrajCounter);
+    a.dH_out = dH_out;
+    a.acc_out = accept_out;
+    a.status = ints + kStatus;
+    cudaError_t e;
+    if (mixed) {
+        a.a_f = c->a_f.as<float>();
+        a.b0_f = c->b0_f.as<float>();
+        a.lr_f = c->lr_f.as<float2>();
+        a.h0f = c->fbuf0.as<float2>();
+        a.h1f = c->fbuf1.as<float2>();
+        if ((e = launch_prep_mixed(y, lnrv, c->a_f.as<float>(), c->b0_f.as<float>(),
+                                   c->lr_f.as<float2>(), T, s)) != cudaSuccess)
+            return cuda_fail(e, "prep kernel");
+        if ((e = launch_h_to_ff(h, c->fbuf0.as<float2>(), T, s)) != cudaSuccess)
+            return cuda_fail(e, "state split kernel");
+        if ((e = launch_traj(a, cfg, true, mass, s)) != cudaSuccess)
+            return cuda_fail(e, "trajectory kernel");
+        if ((e = launch_ff_to_h(c->fbuf1.as<float2>(), h, accept_out, T, s)) != cudaSuccess)
+            return cuda_fail(e, "state join kernel");
+        if (p && (e = launch_commit_fp64(nullptr, nullptr, p, c->dbuf1.as<double>(), accept_out,
+                                         T, s)) != cudaSuccess)
+            return cuda_fail(e, "commit kernel");
+    } else {
+        a.h0d = h;
+        a.h1d = c->dbuf0.as<double>();
+        if ((e = launch_traj(a, cfg, false, mass, s)) != cudaSuccess)
+            return cuda_fail(e, "trajectory kernel");
+        if ((e = launch_commit_fp64(h, c->dbuf0.as<double>(), p, c->dbuf1.as<double>(),
+                                    accept_out, T, s)) != cudaSuccess)
+            return cuda_fail(e, "commit kernel");
+    }
+    return RSV_OK;
+}
+
+rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* lnrv, int64_t T,
+                         double* theta, const float* minv, int n_md, double dtau,
+                         rsv_precision prec, uint64_t seed, uint64_t traj0, int64_t n_traj,
+                         int update_theta, double* dH_out, int32_t* accept_out,
+                         double* theta_out, float* snaps, int64_t thin, int fallback_window,
+                         int32_t* mass_used_out, void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    if (!h || !y || !lnrv || !theta) return fail(RSV_EINVAL, "null argument");
+    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
+    if (n_md < 1 || n_md > (1 << 20)) return fail(RSV_EINVAL, "n_md out of range");
+    if (!(dtau > 0.0) || !std::isfinite(dtau)) return fail(RSV_EINVAL, "dtau must be > 0");
+    if (n_traj < 0) return fail(RSV_EINVAL, "n_traj must be >= 0");
+    if (prec != RSV_FP64 && prec != RSV_MIXED) return fail(RSV_EINVAL, "bad precision");
+    if (snaps && thin < 1) return fail(RSV_EINVAL, "thin must be >= 1 with snapshots");
+    if (fallback_window < 0) return fail(RSV_EINVAL, "fallback_window must be >= 0");
+    if (update_theta) return fail(RSV_EINVAL, "theta update: see rsv_hmc_chain_theta");
+    const bool mixed = prec == RSV_MIXED, mass = minv != nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    TileCfg cfg;
+    if ((st = ctx_plan(c, T, n_md, mixed, mass, cfg)) != RSV_OK) return st;
+    const size_t Tz = (size_t)T;
+    if (mixed) {
+        if ((st = c->fbuf0.ensure(Tz * 8)) != RSV_OK) return st;
+        if ((st = c->fbuf1.ensure(Tz * 8)) != RSV_OK) return st;
+        if ((st = c->a_f.ensure(Tz * 4)) != RSV_OK) return st;
+        if ((st = c->b0_f.ensure(Tz * 4)) != RSV_OK) return st;
+        if ((st = c->lr_f.ensure(Tz * 8)) != RSV_OK) return st;
+    } else {
+        if ((st = c->dbuf0.ensure(Tz * 8)) != RSV_OK) return st;
+    }
+    int* ints = c->ints.as<int>();
+    double* scal = c->scalars.as<double>();
+    cudaError_t e;
+    // cur = 0, fallback state = 0, mass_on = (minv != NULL)
+    if ((e = cudaMemsetAsync(ints + kCur, 0, 4 * sizeof(int), s)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    if (mass && (e = cudaMemsetAsync(ints + kMassOn, 0x01, 1, s)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    TrajArgs a;
+    memset(&a, 0, sizeof(a));
+    a.cur = ints + kCur;
+    a.fb_state = ints + kFbState;
+    a.fallback_window = fallback_window;
+    a.mass_on = ints + kMassOn;
+    a.y = y;
+    a.lnrv = lnrv;
+    a.minv = minv;
+    a.theta = theta;
+    a.T = T;
+    a.tile = cfg.tile;
+    a.K = n_md + 1;
+    a.n_md = n_md;
+    a.dtau = dtau;
+    a.seed = seed;
+    a.series = 0;
+    a.partials = c->partials.as<double>();
+    a.counter = reinterpret_cast<unsigned*>(ints + kTrajCounter);
+    a.status = ints + kStatus;
+    if (mixed) {
+        a.a_f = c->a_f.as<float>();
+        a.b0_f = c->b0_f.as<float>();
+        a.lr_f = c->lr_f.as<float2>();
+        a.h0f = c->fbuf0.as<float2>();
+        a.h1f = c->fbuf1.as<float2>();
+        if ((e = launch_prep_mixed(y, lnrv, c->a_f.as<float>(), c->b0_f.as<float>(),
+                                   c->lr_f.as<float2>(), T, s)) != cudaSuccess)
+            return cuda_fail(e, "prep kernel");
+        if ((e = launch_h_to_ff(h, c->fbuf0.as<float2>(), T, s)) != cudaSuccess)
+            return cuda_fail(e, "state split kernel");
+    } else {
+        a.h0d = h;
+        a.h1d = c->dbuf0.as<double>();
+    }
+    for (int64_t i = 0; i < n_traj; ++i) {
+        a.traj = traj0 + (uint64_t)i;
+        a.dH_out = dH_out ? dH_out + i : scal + kScalDH;
+        a.acc_out = accept_out ? accept_out + i : ints + kScratchAcc;
+        if ((e = launch_traj(a, cfg, mixed, mass, s)) != cudaSuccess)
+            return cuda_fail(e, "trajectory kernel");
+        if (theta_out) {
+            if ((e = cudaMemcpyAsync(theta_out + 5 * i, theta, 5 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                return cuda_fail(e, "theta record");
+        }
+        if (snaps && (i + 1) % thin == 0) {
+            float* dst = snaps + (size_t)((i + 1) / thin - 1) * Tz;
+            e = mixed ? launch_snapshot(nullptr, nullptr, a.h0f, a.h1f, a.cur, dst, T, s)
+                      : launch_snapshot(a.h0d, a.h1d, nullptr, nullptr, a.cur, dst, T, s);
+            if (e != cudaSuccess) return cuda_fail(e, "snapshot kernel");
+        }
+    }
+    // final state back into h
+    e = mixed ? launch_ff_to_h_sel(a.h0f, a.h1f, a.cur, h, T, s)
+              : launch_d_sel(a.h0d, a.h1d, a.cur, h, T, s);
+    if (e != cudaSuccess) return cuda_fail(e, "state copy kernel");
+    if (mass_used_out) {
+        if ((e = cudaMemcpyAsync(mass_used_out, ints + kMassOn, sizeof(int),
+                                 cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "mass flag copy");
+    }
+    return RSV_OK;
+}
+
+}  // extern "C"

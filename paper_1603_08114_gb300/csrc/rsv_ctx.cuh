@@ -1,0 +1,65 @@
+// rsv_ctx.cuh -- the opaque context behind rsv_ctx* (workspace of one device).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rsv.h"
+
+namespace rsv {
+
+// A device buffer that only grows.
+struct Buf {
+    void* ptr = nullptr;
+    size_t cap = 0;
+    rsv_status ensure(size_t bytes);
+    void release();
+    template <typename T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Slots of the small int workspace.
+enum IntSlot : int {
+    kCur = 0,            // chain double-buffer selector
+    kFbState = 1,        // [2] mass fallback window counters
+    kMassOn = 3,         // 1 while the mass is used
+    kStatus = 4,         // status bits (ST_*)
+    kTrajCounter = 5,    // arrival counter of trajectory blocks
+    kActionCounter = 6,  // arrival counter of the action reduction
+    kScratchAcc = 7,     // accept flag when the caller gives none
+    kGibbsCounter = 8,   // arrival counter of the theta reduction
+    kBatchCounter = 16,  // [..] per-call counters of other kernels
+    kIntSlots = 64
+};
+enum ScalSlot : int { kScalDH = 0 };
+
+}  // namespace rsv
+
+struct rsv_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int sched_nt = 0, sched_j = 0;  // rsv_set_schedule override (0 = automatic)
+    int64_t sched_tile = 0;
+    rsv::Buf ints;      // int slots
+    rsv::Buf scalars;   // double scratch scalars
+    rsv::Buf partials;  // per-block partial sums
+    rsv::Buf dbuf0, dbuf1;  // FP64 [T] scratch (proposal h', p')
+    rsv::Buf fbuf0, fbuf1;  // (hi, lo) FP32 state double buffer
+    rsv::Buf a_f, b0_f, lr_f;  // mixed-path per-site constants
+    rsv::Buf gibbs;     // theta-update partial sums
+    rsv::Buf batch;     // batched-path scratch
+    rsv::Buf extra;     // other kernels' scratch
+    std::vector<rsv::Buf*> all_bufs()
+    {
+        return {&ints, &scalars, &partials, &dbuf0, &dbuf1, &fbuf0, &fbuf1, &a_f, &b0_f, &lr_f,
+                &gibbs, &batch, &extra};
+    }
+};
+
+namespace rsv {
+rsv_status fail(rsv_status st, const char* fmt, ...);
+rsv_status cuda_fail(cudaError_t e, const char* what);
+bool capture_active();
+}  // namespace rsv

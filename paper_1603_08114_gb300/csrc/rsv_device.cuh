@@ -1,0 +1,188 @@
+// rsv_device.cuh -- device helpers of librsv (sm_103a).
+//
+// Counter-based generator, Box-Muller, double-float error-free transforms and
+// fixed-order reductions shared by the kernels of this library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rsv {
+
+// Status bits written by kernels into the context status word.
+enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+
+// Philox counter streams (counter word 2).
+enum : uint64_t { STREAM_MOM = 0, STREAM_MH = 1, STREAM_THETA = 2 };
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Each round maps
+// (c0, c1, c2, c3) to (hi(B*c2) ^ c1 ^ k0, lo(B*c2), hi(A*c0) ^ c3 ^ k1, lo(A*c0))
+// with A = 0xD2E7470EE14C6C93, B = 0xCA5A826395121157; between rounds the key
+// advances by the Weyl increments 0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B.
+// ---------------------------------------------------------------------------
+struct u64x4 { uint64_t w[4]; };
+
+__device__ __forceinline__ u64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                               uint64_t c3, uint64_t k0, uint64_t k1)
+{
+    const uint64_t A = 0xD2E7470EE14C6C93ULL, B = 0xCA5A826395121157ULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B97F4A7C15ULL;
+            k1 += 0xBB67AE8584CAA73BULL;
+        }
+        const uint64_t hiA = __umul64hi(A, c0), loA = A * c0;
+        const uint64_t hiB = __umul64hi(B, c2), loB = B * c2;
+        const uint64_t n0 = hiB ^ c1 ^ k0, n2 = hiA ^ c3 ^ k1;
+        c0 = n0;
+        c1 = loB;
+        c2 = n2;
+        c3 = loA;
+    }
+    u64x4 o;
+    o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+    return o;
+}
+
+// Philox block `blk` of stream `stream` for trajectory `traj` of series `series`.
+__device__ __forceinline__ u64x4 philox_block(uint64_t seed, uint64_t series, uint64_t traj,
+                                             uint64_t stream, uint64_t blk)
+{
+    return philox4x64_10(blk, traj, stream, series, seed, 0ULL);
+}
+
+// Uniform in (0,1): (k + 1/2) 2^-53 from the top 53 bits.
+__device__ __forceinline__ double u01_53(uint64_t w)
+{
+    return ((double)(w >> 11) + 0.5) * 0x1.0p-53;
+}
+// Uniform in (0,1) exactly representable in FP32: (k + 1/2) 2^-23, top 23 bits.
+__device__ __forceinline__ float u01_23(uint64_t w)
+{
+    return ((float)(uint32_t)(w >> 41) + 0.5f) * 0x1.0p-23f;
+}
+
+// Box-Muller: r = sqrt(-2 ln u1); (r cos 2 pi u2, r sin 2 pi u2).
+__device__ __forceinline__ void box_muller(double u1, double u2, double& z0, double& z1)
+{
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+__device__ __forceinline__ void box_muller_f(float u1, float u2, float& z0, float& z1)
+{
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+// two_sum (Knuth), fast_two_sum (Dekker, |a| >= |b|), two_prod by FMA.
+// ---------------------------------------------------------------------------
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff two_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    ff p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b)
+{
+    ff p = two_prod(a.hi, b);
+    p.lo = __fmaf_rn(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+// Accumulate a double-float into a double-float (no renormalisation of the
+// small part until read).
+__device__ __forceinline__ void ff_acc(ff& acc, ff v)
+{
+    ff s = two_sum(acc.hi, v.hi);
+    acc.hi = s.hi;
+    acc.lo += s.lo + v.lo;
+}
+__host__ __device__ __forceinline__ ff ff_from_double(double d)
+{
+    const float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// ---------------------------------------------------------------------------
+// Reductions in a fixed order (deterministic): xor-butterfly inside a warp,
+// then warp 0 over the per-warp values in warp order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ ff warp_sum_ff(ff v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = ff_add(v, w);
+    }
+    return v;
+}
+// Block sum; `red` needs blockDim.x/32 doubles.  Result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (warp == 0) {
+        for (int i = lane; i < nw; i += 32) s += red[i];
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+// Theta as stored on the device: (phi, mu, xi, sigma_eta^2, sigma_u^2).
+struct ThetaD {
+    double phi, mu, xi, se2, su2;
+};
+__device__ __forceinline__ ThetaD load_theta(const double* th)
+{
+    return {th[0], th[1], th[2], th[3], th[4]};
+}
+
+}  // namespace rsv

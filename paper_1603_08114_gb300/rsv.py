@@ -1,0 +1,214 @@
+"""Thin Python binding of librsv (include/rsv.h).
+
+Argument marshalling only: every function checks tensor dtypes/devices, passes
+raw device pointers and the current torch CUDA stream to the C entry point of
+the same name, and turns a non-OK status into an exception.  There is no CPU
+fallback: without librsv.so or a GPU the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+RSV_OK, RSV_EINVAL, RSV_ENOMEM, RSV_ECUDA, RSV_ENONFINITE, RSV_ETIMEOUT = range(6)
+RSV_FP64, RSV_MIXED = 0, 1
+_STATUS = {0: "RSV_OK", 1: "RSV_EINVAL", 2: "RSV_ENOMEM", 3: "RSV_ECUDA", 4: "RSV_ENONFINITE",
+           5: "RSV_ETIMEOUT"}
+
+
+class RSVError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Theta(ctypes.Structure):
+    """rsv_theta: (phi, mu, xi, sigma_eta^2, sigma_u^2)."""
+    _fields_ = [("phi", ctypes.c_double), ("mu", ctypes.c_double), ("xi", ctypes.c_double),
+                ("sig_eta2", ctypes.c_double), ("sig_u2", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_INT = ctypes.c_int
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load librsv.so (build it first with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: the CUDA library is not built "
+                               "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        L = ctypes.CDLL(path)
+        L.rsv_last_error.restype = ctypes.c_char_p
+        L.rsv_abi_version.restype = _INT
+        L.rsv_create.argtypes = [ctypes.POINTER(_P), _INT]
+        L.rsv_destroy.argtypes = [_P]
+        L.rsv_destroy.restype = None
+        L.rsv_reserve.argtypes = [_P, _I64, _I64]
+        L.rsv_sync_status.argtypes = [_P, _P]
+        L.rsv_set_schedule.argtypes = [_P, _INT, _INT, _I64]
+        L.rsv_action.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
+        L.rsv_force.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
+        L.rsv_hmc_trajectory.argtypes = [_P, _P, _P, _P, _P, _I64, Theta, _P, _INT,
+                                         ctypes.c_double, _INT, _U64, _U64, _P, _P, _P, _P]
+        L.rsv_hmc_chain.argtypes = [_P, _P, _P, _P, _I64, _P, _P, _INT, ctypes.c_double, _INT,
+                                    _U64, _U64, _I64, _INT, _P, _P, _P, _P, _I64, _INT, _P, _P]
+        L.rsv_draw_momenta.argtypes = [_P, _U64, _U64, _U64, _I64, _P, _INT, _P, _P]
+        for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule", "rsv_action", "rsv_force",
+                     "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta"):
+            getattr(L, name).restype = _INT
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != RSV_OK:
+        raise RSVError(st, lib().rsv_last_error().decode(errors="replace"))
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype, n=None, name="array"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def theta(th) -> Theta:
+    if isinstance(th, Theta):
+        return th
+    return Theta(*[float(v) for v in th])
+
+
+class Context:
+    """An rsv_ctx bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = _P()
+        _check(lib().rsv_create(ctypes.byref(h), int(device)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rsv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rsv_reserve(ctx: Context, max_T: int, max_series: int = 0):
+    _check(lib().rsv_reserve(ctx.handle, int(max_T), int(max_series)))
+
+
+def rsv_set_schedule(ctx: Context, threads: int = 0, sites_per_thread: int = 0, tile: int = 0):
+    _check(lib().rsv_set_schedule(ctx.handle, int(threads), int(sites_per_thread), int(tile)))
+
+
+def rsv_sync_status(ctx: Context):
+    """Synchronise the current stream; raise on a device-side condition."""
+    _check(lib().rsv_sync_status(ctx.handle, _stream()))
+
+
+def rsv_action(ctx: Context, h, y, lnrv, th, S_out=None):
+    T = h.numel()
+    if S_out is None:
+        S_out = torch.empty(1, dtype=torch.float64, device=h.device)
+    _check(lib().rsv_action(ctx.handle, _ptr(h, torch.float64, T, "h"),
+                            _ptr(y, torch.float64, T, "y"), _ptr(lnrv, torch.float64, T, "lnrv"),
+                            T, theta(th), _ptr(S_out, torch.float64, 1, "S_out"), _stream()))
+    return S_out
+
+
+def rsv_force(ctx: Context, h, y, lnrv, th, F_out=None):
+    T = h.numel()
+    if F_out is None:
+        F_out = torch.empty_like(h)
+    _check(lib().rsv_force(ctx.handle, _ptr(h, torch.float64, T, "h"),
+                           _ptr(y, torch.float64, T, "y"), _ptr(lnrv, torch.float64, T, "lnrv"),
+                           T, theta(th), _ptr(F_out, torch.float64, T, "F_out"), _stream()))
+    return F_out
+
+
+def _prec(prec) -> int:
+    if prec in (RSV_FP64, "fp64", "f64"):
+        return RSV_FP64
+    if prec in (RSV_MIXED, "mixed"):
+        return RSV_MIXED
+    raise ValueError(f"unknown precision {prec!r}")
+
+
+def rsv_hmc_trajectory(ctx: Context, h, p, y, lnrv, th, n_md: int, dtau: float, prec="fp64",
+                       minv=None, seed: int = 0, traj: int = 0, log_u=None, dH_out=None,
+                       accept_out=None):
+    """One trajectory in place on h (and p if given); returns (dH, accept) device tensors."""
+    T = h.numel()
+    dev = h.device
+    if dH_out is None:
+        dH_out = torch.empty(1, dtype=torch.float64, device=dev)
+    if accept_out is None:
+        accept_out = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(lib().rsv_hmc_trajectory(
+        ctx.handle, _ptr(h, torch.float64, T, "h"), _ptr(p, torch.float64, T, "p"),
+        _ptr(y, torch.float64, T, "y"), _ptr(lnrv, torch.float64, T, "lnrv"), T, theta(th),
+        _ptr(minv, torch.float32, T, "minv"), int(n_md), float(dtau), _prec(prec), int(seed),
+        int(traj), _ptr(log_u, torch.float64, 1, "log_u"), _ptr(dH_out, torch.float64, 1, "dH"),
+        _ptr(accept_out, torch.int32, 1, "accept"), _stream()))
+    return dH_out, accept_out
+
+
+def rsv_hmc_chain(ctx: Context, h, y, lnrv, theta_dev, n_md: int, dtau: float, n_traj: int,
+                  prec="fp64", minv=None, seed: int = 0, traj0: int = 0, update_theta=False,
+                  dH_out=None, accept_out=None, theta_out=None, snaps=None, thin: int = 1,
+                  fallback_window: int = 0, mass_used_out=None):
+    """n_traj trajectories in place on h and theta_dev (device FP64 [5])."""
+    T = h.numel()
+    _check(lib().rsv_hmc_chain(
+        ctx.handle, _ptr(h, torch.float64, T, "h"), _ptr(y, torch.float64, T, "y"),
+        _ptr(lnrv, torch.float64, T, "lnrv"), T, _ptr(theta_dev, torch.float64, 5, "theta"),
+        _ptr(minv, torch.float32, T, "minv"), int(n_md), float(dtau), _prec(prec), int(seed),
+        int(traj0), int(n_traj), int(bool(update_theta)),
+        _ptr(dH_out, torch.float64, n_traj, "dH_out"),
+        _ptr(accept_out, torch.int32, n_traj, "accept_out"),
+        _ptr(theta_out, torch.float64, 5 * n_traj, "theta_out"),
+        _ptr(snaps, torch.float32, (n_traj // max(thin, 1)) * T if snaps is not None else None,
+             "snaps"),
+        int(thin), int(fallback_window), _ptr(mass_used_out, torch.int32, 1, "mass_used_out"),
+        _stream()))
+
+
+def rsv_draw_momenta(ctx: Context, seed: int, series: int, traj: int, T: int, minv=None,
+                     bits: int = 53, device="cuda"):
+    p = torch.empty(int(T), dtype=torch.float64, device=device)
+    _check(lib().rsv_draw_momenta(ctx.handle, int(seed), int(series), int(traj), int(T),
+                                  _ptr(minv, torch.float32, T, "minv"), int(bits),
+                                  _ptr(p, torch.float64, T, "p"), _stream()))
+    return p
