@@ -486,7 +486,7 @@ __global__ void k_commit_fp64(double* __restrict__ h, const double* __restrict__
                               double* __restrict__ p, const double* __restrict__ pprop,
                               const int* __restrict__ acc, int64_t T)
 {
-    const bool a = *acc != 0;
+    const bool a = h != nullptr && *acc != 0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
         if (a) h[t] = hprop[t];

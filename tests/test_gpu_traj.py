@@ -118,7 +118,7 @@ def test_trajectory_fp64_matches_oracle(rsv, ctx, T):
     _check(r, 1e-12, 1e-9, 1e-9)
 
 
-@pytest.mark.parametrize("T,sched", [(513, (64, 4, 512 - 2 * 21 - 3)),
+@pytest.mark.parametrize("T,sched", [(513, (128, 4, 512 - 2 * 21 - 3)),
                                      (2000, (64, 8, 512 - 2 * 21 - 3)),
                                      (65537, (128, 8, 1024 - 2 * 21 - 3)),
                                      (65537, (256, 28, 256 * 28 - 2 * 21 - 3))])
