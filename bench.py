@@ -1,0 +1,398 @@
+"""Benchmark of the RSV-model HMC volatility update on GB300.
+
+Workload (the single-chain large-series case): T = 2^20 sites of a synthetic
+RSV series (phi, mu, xi, s_eta^2, s_u^2) = (0.95, -0.5, -0.2, 0.05, 0.1), seed 1;
+one step = one chain segment of 200 HMC trajectories of 100 leapfrog steps of
+dtau = 0.005 (momenta, leapfrog, dH, Metropolis for every trajectory), run by
+one rsv_hmc_chain call that also records every trajectory's h for ESS.  The
+chain continues from step to step (the warm-up steps are its burn-in).
+
+Reported: leapfrog site-updates/s (T * n_md * trajectories / time) and ESS/s
+of h (per-site ESS over the step's 200 draws / step time) for the headline
+sampler (mixed precision; diagonal mass when given) and for the plain FP64
+sampler on the same workload.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+T_SITES = 1 << 20
+N_MD = 100
+DTAU = 0.005
+N_TRAJ = 200  # trajectories per step (--traj-per-step changes it for profiling runs)
+SEED_DATA = 1
+METRIC = "leapfrog site-updates/s & ESS/s at T=2^20, mixed+learned vs FP64 plain, 1 GB300"
+UNIT = "site-updates/s"
+WORKLOAD = "rsv-hmc single chain T=2^20, 200 traj x 100 x 0.005 per step"
+# Algorithmic instructions per site and leapfrog step of the mixed kernel on the
+# FP32/issue pipes: innovation (1), AR (1), force (3) + exponent argument (1),
+# special-function exp2 (1), compensated p update (4), compensated h update (4).
+OPS_PER_SITE_STEP_MIXED = 15
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def _barrier_max(ws, value):
+    import torch
+    if ws == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    import torch
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle on this host, single thread, on trajectories of the same
+    workload (T = 2^20, 100 x 0.005) until about budget_s of CPU work."""
+    import oracle
+    from paper_1603_08114_gb300 import synth
+    s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA)
+    h = s.h0.copy()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        r = oracle.chain(h, s.y, s.lnrv, s.theta, N_MD, DTAU, seed=7, n_traj=1, traj0=n)
+        h = r["h"]
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 50:
+            break
+    return {"value": T_SITES * N_MD * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 oracle trajectories of the same workload (T=2^20, 100 x 0.005), "
+                      f"{el:.1f} s, single-threaded C"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the host cores, each step one
+    trajectory of the workload (a bounded sample of one 200-trajectory step)."""
+    import oracle
+    from paper_1603_08114_gb300 import synth
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA)
+    h = s.h0.copy()
+    k = 0
+    for _ in range(args.warmup):
+        h = oracle.chain(h, s.y, s.lnrv, s.theta, N_MD, DTAU, seed=7, n_traj=1, traj0=k)["h"]
+        k += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h = oracle.chain(h, s.y, s.lnrv, s.theta, N_MD, DTAU, seed=7, n_traj=1, traj0=k)["h"]
+        k += 1
+    el = time.perf_counter() - t0
+    v = T_SITES * N_MD * args.steps / el
+    sample = f"1 FP64 oracle trajectory (T=2^20, 100 x 0.005) per step, single-threaded C"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "T": T_SITES, "n_md": N_MD,
+                                        "dtau": DTAU, "step": "1 trajectory"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1603_08114_gb300 import rsv, synth
+
+    ws, rank, local = _dist()
+    dev = torch.device("cuda", local)
+    ctx = rsv.Context(local)
+    s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA + 1000 * rank)
+    y = torch.tensor(s.y, device=dev)
+    lnrv = torch.tensor(s.lnrv, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    snaps = torch.empty(N_TRAJ, T_SITES, dtype=torch.float32, device=dev)
+    acc = torch.empty(N_TRAJ, dtype=torch.int32, device=dev)
+    dH = torch.empty(N_TRAJ, dtype=torch.float64, device=dev)
+    rsv.rsv_reserve(ctx, T_SITES)
+    minv = None
+    if args.mass_file:
+        minv = torch.tensor(np.load(args.mass_file).astype(np.float32), device=dev)
+
+    def arm(prec, mass, warmup, steps, clocks=None, timing=False):
+        h = torch.tensor(s.h0, device=dev)
+        th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
+        traj = 0
+        for _ in range(warmup):
+            rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, N_MD, DTAU, N_TRAJ, prec=prec, minv=mass,
+                              seed=11 + rank, traj0=traj)
+            traj += N_TRAJ
+        rsv.rsv_sync_status(ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        ess_med, ess_min, acc_rate = [], [], []
+        rsv.rsv_stats(ctx, reset=True)
+        rsv.rsv_timing(ctx, timing)
+        _barrier(ws)
+        if clocks:
+            clocks.__enter__()
+        launches = 0
+        for k in range(steps):
+            flush.zero_()
+            l0 = rsv.rsv_stats(ctx, reset=False)[0]
+            ev[k][0].record()
+            rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, N_MD, DTAU, N_TRAJ, prec=prec, minv=mass,
+                              seed=11 + rank, traj0=traj, snaps=snaps, thin=1, accept_out=acc,
+                              dH_out=dH)
+            ev[k][1].record()
+            traj += N_TRAJ
+            launches += rsv.rsv_stats(ctx, reset=False)[0] - l0
+            e = rsv.rsv_ess(ctx, snaps)
+            ess_med.append(e.median())
+            ess_min.append(e.min())
+            acc_rate.append(acc.float().mean())
+        _barrier(ws)
+        if clocks:
+            clocks.__exit__()
+        rsv.rsv_timing(ctx, False)
+        _, traj_launches, traj_ms = rsv.rsv_stats(ctx, reset=True)
+        rsv.rsv_sync_status(ctx)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        total_s = sum(ms) / 1e3
+        total_s = _barrier_max(ws, total_s)
+        sec_per_step = total_s / steps
+        ess_med = [float(x) for x in ess_med]
+        ess_min = [float(x) for x in ess_min]
+        return dict(
+            site_updates_per_s=ws * T_SITES * N_MD * N_TRAJ / sec_per_step,
+            ms_per_step=1e3 * sec_per_step,
+            ess_h_median_per_s=ws * statistics.mean(ess_med) / sec_per_step,
+            ess_h_min_per_s=ws * statistics.mean(ess_min) / sec_per_step,
+            ess_h_median=statistics.mean(ess_med), ess_h_min=statistics.mean(ess_min),
+            accept_rate=float(statistics.mean(float(a) for a in acc_rate)),
+            launches=launches, traj_launches=traj_launches, traj_ms=traj_ms)
+
+    # headline: mixed precision (diagonal mass when given)
+    clocks = Clocks(local)
+    head = arm("mixed", minv, args.warmup, args.steps, clocks=clocks, timing=True)
+    # comparison: plain FP64 sampler, identity mass (at most 3 timed steps)
+    fp64 = None
+    if args.only != "mixed":
+        fp64 = arm("fp64", None, min(args.warmup, 3), min(args.steps, 3))
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs (h, y, lnRV, theta) from pinned memory, the chain, D2H of h' and
+    # the accept/dH records
+    h_host = torch.tensor(s.h0).pin_memory()
+    y_host = torch.tensor(s.y).pin_memory()
+    l_host = torch.tensor(s.lnrv).pin_memory()
+    th_host = torch.tensor(s.theta, dtype=torch.float64).pin_memory()
+    out_h = torch.empty_like(h_host).pin_memory()
+    out_a = torch.empty(N_TRAJ, dtype=torch.int32).pin_memory()
+    out_d = torch.empty(N_TRAJ, dtype=torch.float64).pin_memory()
+    hd = torch.empty(T_SITES, dtype=torch.float64, device=dev)
+    yd = torch.empty_like(hd)
+    ld = torch.empty_like(hd)
+    thd = torch.empty(5, dtype=torch.float64, device=dev)
+    e2e_steps = max(1, min(args.steps, 5))
+    _barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(e2e_steps):
+        hd.copy_(h_host, non_blocking=True)
+        yd.copy_(y_host, non_blocking=True)
+        ld.copy_(l_host, non_blocking=True)
+        thd.copy_(th_host, non_blocking=True)
+        rsv.rsv_hmc_chain(ctx, hd, yd, ld, thd, N_MD, DTAU, N_TRAJ, prec="mixed", minv=minv,
+                          seed=99, traj0=k * N_TRAJ, accept_out=acc, dH_out=dH)
+        out_h.copy_(hd, non_blocking=True)
+        out_a.copy_(acc, non_blocking=True)
+        out_d.copy_(dH, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_s = _barrier_max(ws, e0.elapsed_time(e1) / 1e3) / e2e_steps
+    h2d = 3 * T_SITES * 8 + 5 * 8
+    d2h = T_SITES * 8 + N_TRAJ * (4 + 8)
+
+    peaks, peak_kind = _peaks()
+    sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_clock_mhz * 1e6 / 1e12  # Top/s
+    per_launch_s = head["traj_ms"] / 1e3 / max(head["traj_launches"], 1)
+    ops_per_launch = OPS_PER_SITE_STEP_MIXED * T_SITES * N_MD
+    achieved = ops_per_launch / per_launch_s / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("k_traj_mixed_T2p20")
+        except Exception:
+            traffic = None
+
+    if rank == 0:
+        cpu = cpu_baseline() if (ws == 1 and not args.no_cpu) else None
+        line = {
+            "metric": METRIC, "value": head["site_updates_per_s"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "T": T_SITES, "n_md": N_MD, "dtau": DTAU,
+                       "traj_per_step": N_TRAJ, "precision": "mixed",
+                       "mass": "learned" if minv is not None else "identity",
+                       "l2": "flushed before every step (256 MB write, untimed)",
+                       "parallelism": f"replicas{ws}"},
+            "ess": {"h_median_per_s": head["ess_h_median_per_s"],
+                    "h_min_per_s": head["ess_h_min_per_s"],
+                    "h_median_per_step": head["ess_h_median"],
+                    "h_min_per_step": head["ess_h_min"], "accept_rate": head["accept_rate"]},
+            "fp64_plain": None if fp64 is None else {
+                "site_updates_per_s": fp64["site_updates_per_s"],
+                "ms_per_step": fp64["ms_per_step"],
+                "ess_h_median_per_s": fp64["ess_h_median_per_s"],
+                "ess_h_min_per_s": fp64["ess_h_min_per_s"],
+                "accept_rate": fp64["accept_rate"]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
+                         "frac": achieved / alu_peak, "traffic": traffic,
+                         "kernel": "k_traj_mixed", "peak_kind": "nominal FP32-lane issue "
+                         f"rate 152 SM x 128 x {sm_clock_mhz:.0f} MHz",
+                         "per_launch_ms": per_launch_s * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws * T_SITES * N_MD * N_TRAJ / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": head["launches"],
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mass-file", default=None,
+                    help="npy of FP32 inverse masses for the headline arm")
+    ap.add_argument("--only", default=None, choices=["mixed"],
+                    help="run the headline arm only (profiling)")
+    ap.add_argument("--traj-per-step", type=int, default=None,
+                    help="trajectories per step (profiling; default 200)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.traj_per_step:
+        global N_TRAJ
+        N_TRAJ = int(args.traj_per_step)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -156,6 +156,23 @@ rsv_status rsv_hmc_chain(rsv_ctx* ctx, double* h, const double* y, const double*
 rsv_status rsv_draw_momenta(rsv_ctx* ctx, uint64_t seed, uint64_t series, uint64_t traj,
                             int64_t T, const float* minv, int bits, double* p_out, void* stream);
 
+/* ---- measurement -----------------------------------------------------------
+ * rsv_ess: effective sample size of every column t of x, a [n][T] FP32 matrix
+ * of n chain samples (row k = sample k), by Geyer's initial monotone sequence
+ * estimator (Statistical Science 7, 1992) on the plain autocovariances; ESS is
+ * capped at n log10(n).  ess_out [T] FP32.  n >= 2.  (Not part of the paper's
+ * method; used to report ESS/s.)
+ * rsv_timing: enable (1) / disable (0) CUDA-event timing of every trajectory
+ * kernel launch (skipped while the stream is being captured).
+ * rsv_stats: kernel launches made by the library, trajectory-kernel launches
+ * and their summed device time (ms) since the last reset; synchronises the
+ * recorded events; reset != 0 clears the counters after reading. */
+rsv_status rsv_ess(rsv_ctx* ctx, const float* x, int64_t n, int64_t T, float* ess_out,
+                   void* stream);
+rsv_status rsv_timing(rsv_ctx* ctx, int enable);
+rsv_status rsv_stats(rsv_ctx* ctx, int reset, int64_t* launches, int64_t* traj_launches,
+                     double* traj_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@
 
 #include "rsv.h"
 #include "rsv_ctx.cuh"
+#include "rsv_ess.cuh"
 #include "rsv_simple.cuh"
 #include "rsv_traj.cuh"
 
@@ -95,6 +96,40 @@ rsv_status ctx_ensure_partials(rsv_ctx* c, int64_t n)
     return c->partials.ensure((size_t)n * sizeof(double));
 }
 
+// Count a kernel launch made through launcher f.
+template <class F, class... A>
+cudaError_t counted(rsv_ctx* c, F f, A... a)
+{
+    ++c->launches;
+    return f(a...);
+}
+
+// Launch a trajectory kernel, bracketed by CUDA events when timing is on.
+cudaError_t timed_traj(rsv_ctx* c, const TrajArgs& a, const TileCfg& cfg, bool mixed, bool mass,
+                       cudaStream_t s)
+{
+    const bool rec = c->timing && !capture_active();
+    if (rec) {
+        if (c->ev_used + 2 > c->ev.size()) {
+            for (int i = 0; i < 2; ++i) {
+                cudaEvent_t e;
+                cudaError_t r = cudaEventCreate(&e);
+                if (r != cudaSuccess) return r;
+                c->ev.push_back(e);
+            }
+        }
+        cudaEventRecord(c->ev[c->ev_used], s);
+    }
+    cudaError_t e = launch_traj(a, cfg, mixed, mass, s);
+    if (rec) {
+        cudaEventRecord(c->ev[c->ev_used + 1], s);
+        c->ev_used += 2;
+    }
+    c->launches += 1;
+    c->traj_launches += 1;
+    return e;
+}
+
 rsv_status ctx_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, TileCfg& cfg)
 {
     if (c->sched_nt) {
@@ -151,6 +186,7 @@ void rsv_destroy(rsv_ctx* c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (Buf* b : c->all_bufs()) b->release();
     delete c;
 }
@@ -214,7 +250,7 @@ rsv_status rsv_action(rsv_ctx* c, const double* h, const double* y, const double
     if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
     if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
     if ((st = ctx_ensure_partials(c, action_grid(T))) != RSV_OK) return st;
-    cudaError_t e = launch_action(h, y, lnrv, T, to_dev(theta), c->partials.as<double>(),
+    cudaError_t e = counted(c, launch_action, h, y, lnrv, T, to_dev(theta), c->partials.as<double>(),
                                   reinterpret_cast<unsigned*>(c->ints.as<int>() + kActionCounter),
                                   S_out, (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "action kernel");
@@ -229,7 +265,7 @@ rsv_status rsv_force(rsv_ctx* c, const double* h, const double* y, const double*
     if (F_out == h) return fail(RSV_EINVAL, "F_out must not alias h");
     if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
     if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
-    cudaError_t e = launch_force(h, y, lnrv, T, to_dev(theta), F_out, (cudaStream_t)stream);
+    cudaError_t e = counted(c, launch_force, h, y, lnrv, T, to_dev(theta), F_out, (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "force kernel");
 }
 
@@ -241,7 +277,7 @@ rsv_status rsv_draw_momenta(rsv_ctx* c, uint64_t seed, uint64_t series, uint64_t
     if (!p_out) return fail(RSV_EINVAL, "null p_out");
     if (T < 1) return fail(RSV_EINVAL, "T must be >= 1");
     if (bits != 53 && bits != 23) return fail(RSV_EINVAL, "bits must be 53 or 23");
-    cudaError_t e = launch_draw_momenta(seed, series, traj, T, minv, bits, p_out,
+    cudaError_t e = counted(c, launch_draw_momenta, seed, series, traj, T, minv, bits, p_out,
                                         (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "momentum kernel");
 }
@@ -308,24 +344,24 @@ rsv_status rsv_hmc_trajectory(rsv_ctx* c, double* h, double* p, const double* y,
         a.lr_f = c->lr_f.as<float2>();
         a.h0f = c->fbuf0.as<float2>();
         a.h1f = c->fbuf1.as<float2>();
-        if ((e = launch_prep_mixed(y, lnrv, c->a_f.as<float>(), c->b0_f.as<float>(),
+        if ((e = counted(c, launch_prep_mixed, y, lnrv, c->a_f.as<float>(), c->b0_f.as<float>(),
                                    c->lr_f.as<float2>(), T, s)) != cudaSuccess)
             return cuda_fail(e, "prep kernel");
-        if ((e = launch_h_to_ff(h, c->fbuf0.as<float2>(), T, s)) != cudaSuccess)
+        if ((e = counted(c, launch_h_to_ff, h, c->fbuf0.as<float2>(), T, s)) != cudaSuccess)
             return cuda_fail(e, "state split kernel");
-        if ((e = launch_traj(a, cfg, true, mass, s)) != cudaSuccess)
+        if ((e = timed_traj(c, a, cfg, true, mass, s)) != cudaSuccess)
             return cuda_fail(e, "trajectory kernel");
-        if ((e = launch_ff_to_h(c->fbuf1.as<float2>(), h, accept_out, T, s)) != cudaSuccess)
+        if ((e = counted(c, launch_ff_to_h, c->fbuf1.as<float2>(), h, accept_out, T, s)) != cudaSuccess)
             return cuda_fail(e, "state join kernel");
-        if (p && (e = launch_commit_fp64(nullptr, nullptr, p, c->dbuf1.as<double>(), accept_out,
+        if (p && (e = counted(c, launch_commit_fp64, nullptr, nullptr, p, c->dbuf1.as<double>(), accept_out,
                                          T, s)) != cudaSuccess)
             return cuda_fail(e, "commit kernel");
     } else {
         a.h0d = h;
         a.h1d = c->dbuf0.as<double>();
-        if ((e = launch_traj(a, cfg, false, mass, s)) != cudaSuccess)
+        if ((e = timed_traj(c, a, cfg, false, mass, s)) != cudaSuccess)
             return cuda_fail(e, "trajectory kernel");
-        if ((e = launch_commit_fp64(h, c->dbuf0.as<double>(), p, c->dbuf1.as<double>(),
+        if ((e = counted(c, launch_commit_fp64, h, c->dbuf0.as<double>(), p, c->dbuf1.as<double>(),
                                     accept_out, T, s)) != cudaSuccess)
             return cuda_fail(e, "commit kernel");
     }
@@ -398,10 +434,10 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
         a.lr_f = c->lr_f.as<float2>();
         a.h0f = c->fbuf0.as<float2>();
         a.h1f = c->fbuf1.as<float2>();
-        if ((e = launch_prep_mixed(y, lnrv, c->a_f.as<float>(), c->b0_f.as<float>(),
+        if ((e = counted(c, launch_prep_mixed, y, lnrv, c->a_f.as<float>(), c->b0_f.as<float>(),
                                    c->lr_f.as<float2>(), T, s)) != cudaSuccess)
             return cuda_fail(e, "prep kernel");
-        if ((e = launch_h_to_ff(h, c->fbuf0.as<float2>(), T, s)) != cudaSuccess)
+        if ((e = counted(c, launch_h_to_ff, h, c->fbuf0.as<float2>(), T, s)) != cudaSuccess)
             return cuda_fail(e, "state split kernel");
     } else {
         a.h0d = h;
@@ -411,7 +447,7 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
         a.traj = traj0 + (uint64_t)i;
         a.dH_out = dH_out ? dH_out + i : scal + kScalDH;
         a.acc_out = accept_out ? accept_out + i : ints + kScratchAcc;
-        if ((e = launch_traj(a, cfg, mixed, mass, s)) != cudaSuccess)
+        if ((e = timed_traj(c, a, cfg, mixed, mass, s)) != cudaSuccess)
             return cuda_fail(e, "trajectory kernel");
         if (theta_out) {
             if ((e = cudaMemcpyAsync(theta_out + 5 * i, theta, 5 * sizeof(double),
@@ -420,19 +456,63 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
         }
         if (snaps && (i + 1) % thin == 0) {
             float* dst = snaps + (size_t)((i + 1) / thin - 1) * Tz;
-            e = mixed ? launch_snapshot(nullptr, nullptr, a.h0f, a.h1f, a.cur, dst, T, s)
-                      : launch_snapshot(a.h0d, a.h1d, nullptr, nullptr, a.cur, dst, T, s);
+            e = mixed ? counted(c, launch_snapshot, nullptr, nullptr, a.h0f, a.h1f, a.cur, dst, T, s)
+                      : counted(c, launch_snapshot, a.h0d, a.h1d, nullptr, nullptr, a.cur, dst, T, s);
             if (e != cudaSuccess) return cuda_fail(e, "snapshot kernel");
         }
     }
     // final state back into h
-    e = mixed ? launch_ff_to_h_sel(a.h0f, a.h1f, a.cur, h, T, s)
-              : launch_d_sel(a.h0d, a.h1d, a.cur, h, T, s);
+    e = mixed ? counted(c, launch_ff_to_h_sel, a.h0f, a.h1f, a.cur, h, T, s)
+              : counted(c, launch_d_sel, a.h0d, a.h1d, a.cur, h, T, s);
     if (e != cudaSuccess) return cuda_fail(e, "state copy kernel");
     if (mass_used_out) {
         if ((e = cudaMemcpyAsync(mass_used_out, ints + kMassOn, sizeof(int),
                                  cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return cuda_fail(e, "mass flag copy");
+    }
+    return RSV_OK;
+}
+
+rsv_status rsv_ess(rsv_ctx* c, const float* x, int64_t n, int64_t T, float* ess_out,
+                   void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    if (!x || !ess_out) return fail(RSV_EINVAL, "null argument");
+    if (n < 2 || T < 1) return fail(RSV_EINVAL, "need n >= 2 samples and T >= 1");
+    ++c->launches;
+    cudaError_t e = launch_ess(x, n, T, ess_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? RSV_OK : cuda_fail(e, "ess kernel");
+}
+
+rsv_status rsv_timing(rsv_ctx* c, int enable)
+{
+    if (!c) return fail(RSV_EINVAL, "null context");
+    c->timing = enable != 0;
+    return RSV_OK;
+}
+
+rsv_status rsv_stats(rsv_ctx* c, int reset, int64_t* launches, int64_t* traj_launches,
+                     double* traj_ms)
+{
+    rsv_status st = ctx_begin(c, nullptr);
+    if (st != RSV_OK) return st;
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        cudaError_t e = cudaEventSynchronize(c->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "event sync");
+        float m = 0.f;
+        e = cudaEventElapsedTime(&m, c->ev[i], c->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "event elapsed");
+        ms += m;
+    }
+    if (launches) *launches = c->launches;
+    if (traj_launches) *traj_launches = c->traj_launches;
+    if (traj_ms) *traj_ms = ms;
+    if (reset) {
+        c->launches = 0;
+        c->traj_launches = 0;
+        c->ev_used = 0;
     }
     return RSV_OK;
 }

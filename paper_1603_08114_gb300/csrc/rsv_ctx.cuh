@@ -42,6 +42,12 @@ struct rsv_ctx {
     int num_sms = 0;
     int sched_nt = 0, sched_j = 0;  // rsv_set_schedule override (0 = automatic)
     int64_t sched_tile = 0;
+    // accounting: kernel launches, and CUDA events around trajectory kernels
+    int64_t launches = 0;
+    int64_t traj_launches = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+    size_t ev_used = 0;
     rsv::Buf ints;      // int slots
     rsv::Buf scalars;   // double scratch scalars
     rsv::Buf partials;  // per-block partial sums

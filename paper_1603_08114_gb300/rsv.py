@@ -68,8 +68,13 @@ def lib():
         L.rsv_hmc_chain.argtypes = [_P, _P, _P, _P, _I64, _P, _P, _INT, ctypes.c_double, _INT,
                                     _U64, _U64, _I64, _INT, _P, _P, _P, _P, _I64, _INT, _P, _P]
         L.rsv_draw_momenta.argtypes = [_P, _U64, _U64, _U64, _I64, _P, _INT, _P, _P]
+        L.rsv_ess.argtypes = [_P, _P, _I64, _I64, _P, _P]
+        L.rsv_timing.argtypes = [_P, _INT]
+        L.rsv_stats.argtypes = [_P, _INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                ctypes.POINTER(ctypes.c_double)]
         for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule", "rsv_action", "rsv_force",
-                     "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta"):
+                     "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
+                     "rsv_timing", "rsv_stats"):
             getattr(L, name).restype = _INT
         _lib = L
     return _lib
@@ -212,3 +217,24 @@ def rsv_draw_momenta(ctx: Context, seed: int, series: int, traj: int, T: int, mi
                                   _ptr(minv, torch.float32, T, "minv"), int(bits),
                                   _ptr(p, torch.float64, T, "p"), _stream()))
     return p
+
+
+def rsv_ess(ctx: Context, x):
+    """ESS of every column of x, a [n, T] FP32 CUDA tensor of chain samples."""
+    n, T = x.shape
+    out = torch.empty(T, dtype=torch.float32, device=x.device)
+    _check(lib().rsv_ess(ctx.handle, _ptr(x, torch.float32, n * T, "x"), int(n), int(T),
+                         _ptr(out, torch.float32, T, "ess_out"), _stream()))
+    return out
+
+
+def rsv_timing(ctx: Context, enable: bool = True):
+    _check(lib().rsv_timing(ctx.handle, int(bool(enable))))
+
+
+def rsv_stats(ctx: Context, reset: bool = True):
+    """(launches, trajectory launches, trajectory-kernel ms) since the last reset."""
+    a, b, ms = _I64(), _I64(), ctypes.c_double()
+    _check(lib().rsv_stats(ctx.handle, int(bool(reset)), ctypes.byref(a), ctypes.byref(b),
+                           ctypes.byref(ms)))
+    return a.value, b.value, ms.value
