@@ -151,7 +151,7 @@ def cpu_baseline(budget_s: float = 12.0):
     import oracle
     from paper_1603_08114_gb300 import synth
     s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA)
-    h = s.h0.copy()
+    h = s.h_true.copy()
     n = 0
     t0 = time.perf_counter()
     while True:
@@ -176,7 +176,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA)
-    h = s.h0.copy()
+    h = s.h_true.copy()
     k = 0
     for _ in range(args.warmup):
         h = oracle.chain(h, s.y, s.lnrv, s.theta, N_MD, DTAU, seed=7, n_traj=1, traj0=k)["h"]
@@ -221,7 +221,9 @@ def run_ours(args):
         minv = torch.tensor(np.load(args.mass_file).astype(np.float32), device=dev)
 
     def arm(prec, mass, warmup, steps, clocks=None, timing=False):
-        h = torch.tensor(s.h0, device=dev)
+        # the chain starts from the generator's latent path, a posterior-typical
+        # state (from lnRV - xi the first trajectories are all rejected)
+        h = torch.tensor(s.h_true, device=dev)
         th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
         traj = 0
         for _ in range(warmup):
@@ -284,7 +286,7 @@ def run_ours(args):
     # end to end through the public API with host buffers: H2D of the step's
     # inputs (h, y, lnRV, theta) from pinned memory, the chain, D2H of h' and
     # the accept/dH records
-    h_host = torch.tensor(s.h0).pin_memory()
+    h_host = torch.tensor(s.h_true).pin_memory()
     y_host = torch.tensor(s.y).pin_memory()
     l_host = torch.tensor(s.lnrv).pin_memory()
     th_host = torch.tensor(s.theta, dtype=torch.float64).pin_memory()

@@ -150,6 +150,21 @@ rsv_status rsv_hmc_chain(rsv_ctx* ctx, double* h, const double* y, const double*
                          double* theta_out, float* snaps, int64_t thin, int fallback_window,
                          int32_t* mass_used_out, void* stream);
 
+/* ---- theta update ---------------------------------------------------------
+ * One Gibbs sweep of theta given h (the paper does not describe its theta
+ * update): xi ~ N(mean(lnRV - h), s_u^2/T); s_u^2 ~ IG(T/2, sum(lnRV-xi-h)^2/2);
+ * mu ~ N(m, s_eta^2/P) from eq. (3) and the stationary law of h_1;
+ * s_eta^2 ~ IG(T/2, Q/2); phi by independence Metropolis from the Gaussian
+ * part truncated to (-1,1) with ratio sqrt(1-phi'^2)/sqrt(1-phi^2).  Flat
+ * priors on phi, mu, xi; 1/sigma^2 priors on the variances.  Draws come in
+ * this order from Philox counter {block, traj, 2, series}, key {seed, 0}.
+ *  h [T] FP64, lnrv [T] FP64, theta device FP64 [5] in/out.
+ *  mask: bit 0 xi, 1 s_u^2, 2 mu, 3 s_eta^2, 4 phi (31 = all).
+ *  phi_acc_out: device int32 scalar (1 if the phi proposal was accepted) or NULL. */
+rsv_status rsv_gibbs_theta(rsv_ctx* ctx, const double* h, const double* lnrv, int64_t T,
+                           double* theta, uint64_t seed, uint64_t series, uint64_t traj,
+                           int mask, int32_t* phi_acc_out, void* stream);
+
 /* ---- Philox momenta (exposed for tests of the generator) -----------------
  * p_t exactly as rsv_hmc_trajectory draws them for (seed, series, traj);
  * bits = 53 (FP64 path) or 23 (MIXED path). p_out [T] FP64. */

@@ -39,8 +39,8 @@ def ess_geyer(x: np.ndarray) -> np.ndarray:
     g = autocov(x)
     out = np.empty(x.shape[1])
     for j in range(x.shape[1]):
-        if g[0, j] <= 0.0:
-            out[j] = float(n)
+        if g[0, j] <= 0.0:  # constant column: the chain never moved
+            out[j] = 0.0
             continue
         rho = g[:, j] / g[0, j]
         tau_sum = 0.0

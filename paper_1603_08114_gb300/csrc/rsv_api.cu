@@ -12,6 +12,7 @@
 #include "rsv.h"
 #include "rsv_ctx.cuh"
 #include "rsv_ess.cuh"
+#include "rsv_gibbs.cuh"
 #include "rsv_simple.cuh"
 #include "rsv_traj.cuh"
 
@@ -385,12 +386,14 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
     if (prec != RSV_FP64 && prec != RSV_MIXED) return fail(RSV_EINVAL, "bad precision");
     if (snaps && thin < 1) return fail(RSV_EINVAL, "thin must be >= 1 with snapshots");
     if (fallback_window < 0) return fail(RSV_EINVAL, "fallback_window must be >= 0");
-    if (update_theta) return fail(RSV_EINVAL, "theta update: see rsv_hmc_chain_theta");
     const bool mixed = prec == RSV_MIXED, mass = minv != nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     TileCfg cfg;
     if ((st = ctx_plan(c, T, n_md, mixed, mass, cfg)) != RSV_OK) return st;
     const size_t Tz = (size_t)T;
+    if (update_theta &&
+        (st = c->gibbs.ensure((size_t)gibbs_grid(T) * 8 * sizeof(double))) != RSV_OK)
+        return st;
     if (mixed) {
         if ((st = c->fbuf0.ensure(Tz * 8)) != RSV_OK) return st;
         if ((st = c->fbuf1.ensure(Tz * 8)) != RSV_OK) return st;
@@ -449,7 +452,28 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
         a.acc_out = accept_out ? accept_out + i : ints + kScratchAcc;
         if ((e = timed_traj(c, a, cfg, mixed, mass, s)) != cudaSuccess)
             return cuda_fail(e, "trajectory kernel");
-        if (theta_out) {
+        if (update_theta) {
+            GibbsArgs g;
+            memset(&g, 0, sizeof(g));
+            g.h0d = a.h0d;
+            g.h1d = a.h1d;
+            g.h0f = a.h0f;
+            g.h1f = a.h1f;
+            g.cur = a.cur;
+            g.lnrv = lnrv;
+            g.lr_f = a.lr_f;
+            g.T = T;
+            g.theta = theta;
+            g.theta_out = theta_out ? theta_out + 5 * i : nullptr;
+            g.seed = seed;
+            g.series = 0;
+            g.traj = a.traj;
+            g.mask = 31;
+            g.partials = c->gibbs.as<double>();
+            g.counter = reinterpret_cast<unsigned*>(ints + kGibbsCounter);
+            if ((e = counted(c, launch_gibbs, g, mixed, s)) != cudaSuccess)
+                return cuda_fail(e, "theta kernel");
+        } else if (theta_out) {
             if ((e = cudaMemcpyAsync(theta_out + 5 * i, theta, 5 * sizeof(double),
                                      cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
                 return cuda_fail(e, "theta record");
@@ -471,6 +495,33 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
             return cuda_fail(e, "mass flag copy");
     }
     return RSV_OK;
+}
+
+rsv_status rsv_gibbs_theta(rsv_ctx* c, const double* h, const double* lnrv, int64_t T,
+                           double* theta, uint64_t seed, uint64_t series, uint64_t traj,
+                           int mask, int32_t* phi_acc_out, void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    if (!h || !lnrv || !theta) return fail(RSV_EINVAL, "null argument");
+    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1");
+    if (mask < 0 || mask > 31) return fail(RSV_EINVAL, "mask must be in 0..31");
+    if ((st = c->gibbs.ensure((size_t)gibbs_grid(T) * 8 * sizeof(double))) != RSV_OK) return st;
+    GibbsArgs g;
+    memset(&g, 0, sizeof(g));
+    g.h0d = h;
+    g.lnrv = lnrv;
+    g.T = T;
+    g.theta = theta;
+    g.seed = seed;
+    g.series = series;
+    g.traj = traj;
+    g.mask = mask;
+    g.partials = c->gibbs.as<double>();
+    g.counter = reinterpret_cast<unsigned*>(c->ints.as<int>() + kGibbsCounter);
+    g.phi_acc = phi_acc_out;
+    cudaError_t e = counted(c, launch_gibbs, g, false, (cudaStream_t)stream);
+    return e == cudaSuccess ? RSV_OK : cuda_fail(e, "theta kernel");
 }
 
 rsv_status rsv_ess(rsv_ctx* c, const float* x, int64_t n, int64_t T, float* ess_out,

@@ -5,8 +5,9 @@
 // gamma_k = (1/n) sum_t (x_t - m)(x_{t+k} - m); pair sums
 // Gamma_m = rho_{2m} + rho_{2m+1} taken while positive and made
 // non-increasing; tau = -1 + 2 sum Gamma_m, floored at 1/log10(n) (so ESS
-// <= n log10 n); ESS = n / tau.  One thread per site; the snapshot matrix is
-// [n][T] FP32 (sample-major), so a warp reads 128 contiguous bytes per sample.
+// <= n log10 n); ESS = n / tau; a constant column (zero variance) gets 0.
+// One thread per site; the snapshot matrix is [n][T] FP32 (sample-major), so a
+// warp reads 128 contiguous bytes per sample.
 #include <cmath>
 
 #include "rsv_ess.cuh"
@@ -40,8 +41,8 @@ __global__ void __launch_bounds__(256) k_ess(const float* __restrict__ x, int64_
         return a / (float)n;
     };
     const float g0 = gamma(0);
-    if (!(g0 > 0.f)) {
-        ess[t] = (float)n;
+    if (!(g0 > 0.f)) {  // the chain never moved at this site
+        ess[t] = 0.f;
         return;
     }
     float tau_sum = 0.f, prev = INFINITY;

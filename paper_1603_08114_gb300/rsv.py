@@ -69,12 +69,13 @@ def lib():
                                     _U64, _U64, _I64, _INT, _P, _P, _P, _P, _I64, _INT, _P, _P]
         L.rsv_draw_momenta.argtypes = [_P, _U64, _U64, _U64, _I64, _P, _INT, _P, _P]
         L.rsv_ess.argtypes = [_P, _P, _I64, _I64, _P, _P]
+        L.rsv_gibbs_theta.argtypes = [_P, _P, _P, _I64, _P, _U64, _U64, _U64, _INT, _P, _P]
         L.rsv_timing.argtypes = [_P, _INT]
         L.rsv_stats.argtypes = [_P, _INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                 ctypes.POINTER(ctypes.c_double)]
         for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule", "rsv_action", "rsv_force",
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
-                     "rsv_timing", "rsv_stats"):
+                     "rsv_timing", "rsv_stats", "rsv_gibbs_theta"):
             getattr(L, name).restype = _INT
         _lib = L
     return _lib
@@ -238,3 +239,14 @@ def rsv_stats(ctx: Context, reset: bool = True):
     _check(lib().rsv_stats(ctx.handle, int(bool(reset)), ctypes.byref(a), ctypes.byref(b),
                            ctypes.byref(ms)))
     return a.value, b.value, ms.value
+
+
+def rsv_gibbs_theta(ctx: Context, h, lnrv, theta_dev, seed: int, series: int = 0, traj: int = 0,
+                    mask: int = 31, phi_acc_out=None):
+    """One theta Gibbs sweep in place on theta_dev (device FP64 [5]) given h."""
+    T = h.numel()
+    _check(lib().rsv_gibbs_theta(ctx.handle, _ptr(h, torch.float64, T, "h"),
+                                 _ptr(lnrv, torch.float64, T, "lnrv"), T,
+                                 _ptr(theta_dev, torch.float64, 5, "theta"), int(seed),
+                                 int(series), int(traj), int(mask),
+                                 _ptr(phi_acc_out, torch.int32, 1, "phi_acc_out"), _stream()))

@@ -1,0 +1,89 @@
+"""GPU theta update and theta-sampling chains against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import stats
+from paper_1603_08114_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TH = synth.THETA_STD
+
+
+@pytest.fixture(scope="module")
+def rsv():
+    from paper_1603_08114_gb300 import rsv as r
+    return r
+
+
+@pytest.fixture(scope="module")
+def ctx(rsv):
+    c = rsv.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 100, 2000, 65537])
+@pytest.mark.parametrize("mask", [31, 0b10000, 0b01111])
+def test_gibbs_sweep_matches_oracle(rsv, ctx, T, mask):
+    s = synth.rsv_series(T, TH, seed=T)
+    h = s.h_true + 0.05 * synth.standard_normals(T, 1)
+    for traj in range(4):
+        th = dev(TH)
+        acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        rsv.rsv_gibbs_theta(ctx, dev(h), dev(s.lnrv), th, seed=5, series=0, traj=traj, mask=mask,
+                            phi_acc_out=acc)
+        ref, racc = oracle.gibbs_theta(h, s.lnrv, TH, seed=5, series=0, traj=traj, mask=mask)
+        got = th.cpu().numpy()
+        assert np.allclose(got, ref, rtol=1e-11, atol=1e-13), (got, ref)
+        assert int(acc.item()) == racc
+
+
+def test_chain_with_theta_fp64_matches_oracle(rsv, ctx):
+    T, n, n_md, dtau, seed = 2000, 25, 50, 0.02, 21
+    s = synth.rsv_series(T, TH, seed=0)
+    h = dev(s.h_true)
+    th = dev(TH)
+    ths = torch.empty(n, 5, dtype=torch.float64, device="cuda")
+    acc = torch.empty(n, dtype=torch.int32, device="cuda")
+    rsv.rsv_hmc_chain(ctx, h, dev(s.y), dev(s.lnrv), th, n_md, dtau, n, seed=seed,
+                      update_theta=True, theta_out=ths, accept_out=acc)
+    rsv.rsv_sync_status(ctx)
+    r = oracle.chain(s.h_true, s.y, s.lnrv, TH, n_md, dtau, seed, n, update_theta=True)
+    assert np.array_equal(acc.cpu().numpy(), r["accept"])
+    assert np.allclose(ths.cpu().numpy(), r["thetas"], rtol=1e-9, atol=1e-11)
+    assert np.max(np.abs(h.cpu().numpy() - r["h"])) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_chain_theta_posterior_means_agree_with_oracle(rsv, ctx, prec):
+    """The 2000-site workload with theta sampled: 1000 trajectories of 50 x 0.02.
+    Posterior means of theta and of a few h_t from the GPU chain lie within 3
+    combined Monte-Carlo standard errors of the oracle chain's (different
+    Philox seed, so the chains are independent)."""
+    T, n, n_md, dtau, burn = 2000, 1000, 50, 0.02, 200
+    s = synth.rsv_series(T, TH, seed=0)
+    h = dev(s.h0)
+    th = dev(TH)
+    ths = torch.empty(n, 5, dtype=torch.float64, device="cuda")
+    snaps = torch.empty(n, T, dtype=torch.float32, device="cuda")
+    rsv.rsv_hmc_chain(ctx, h, dev(s.y), dev(s.lnrv), th, n_md, dtau, n, prec=prec, seed=31,
+                      update_theta=True, theta_out=ths, snaps=snaps, thin=1)
+    rsv.rsv_sync_status(ctx)
+    r = oracle.chain(s.h0, s.y, s.lnrv, TH, n_md, dtau, 32, n, update_theta=True, thin=1)
+    g = ths.cpu().numpy()[burn:]
+    o = r["thetas"][burn:]
+    se = np.sqrt(stats.batch_means_mcse(g) ** 2 + stats.batch_means_mcse(o) ** 2)
+    z = np.abs(g.mean(0) - o.mean(0)) / se
+    assert np.all(z < 3.5), z
+    cols = [0, 7, 500, 1999]
+    gh = snaps.cpu().numpy()[burn:, cols].astype(np.float64)
+    oh = r["snaps"][burn:, cols]
+    se = np.sqrt(stats.batch_means_mcse(gh) ** 2 + stats.batch_means_mcse(oh) ** 2)
+    z = np.abs(gh.mean(0) - oh.mean(0)) / se
+    assert np.all(z < 3.5), z
