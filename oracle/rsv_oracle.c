@@ -369,7 +369,8 @@ int orc_gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
             sum_add(&ss, r * r);
         }
         double g = stream_gamma(&st, 0.5 * Td);
-        if (g > 0.0) th->sig_u2 = 0.5 * sum_get(&ss) / g;
+        /* a degenerate state (zero residuals) keeps the old value */
+        if (g > 0.0 && sum_get(&ss) > 0.0) th->sig_u2 = 0.5 * sum_get(&ss) / g;
     }
 
     /* mu */
@@ -395,7 +396,7 @@ int orc_gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
             sum_add(&q, e * e);
         }
         double g2 = stream_gamma(&st, 0.5 * Td);
-        if (g2 > 0.0) th->sig_eta2 = 0.5 * sum_get(&q) / g2;
+        if (g2 > 0.0 && sum_get(&q) > 0.0) th->sig_eta2 = 0.5 * sum_get(&q) / g2;
     }
 
     /* phi */

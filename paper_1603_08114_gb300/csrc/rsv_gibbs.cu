@@ -133,7 +133,7 @@ __device__ void gibbs_draws(const double (&S)[NSTAT], double x0, int64_t T, doub
         const double dxi = xi - xi0;
         const double ss = S[1] - 2.0 * dxi * S[0] + Td * dxi * dxi;
         const double g = st.gamma(0.5 * Td);
-        if (g > 0.0) su2 = 0.5 * ss / g;
+        if (g > 0.0 && ss > 0.0) su2 = 0.5 * ss / g;  // degenerate state: keep
     }
     // mu
     if (mask & 4) {
@@ -149,7 +149,7 @@ __device__ void gibbs_draws(const double (&S)[NSTAT], double x0, int64_t T, doub
         const double Q = (1.0 - phi * phi) * a * a + S[7] - 2.0 * om * dmu * S[6] +
                          (Td - 1.0) * om * om * dmu * dmu;
         const double g = st.gamma(0.5 * Td);
-        if (g > 0.0) se2 = 0.5 * Q / g;
+        if (g > 0.0 && Q > 0.0) se2 = 0.5 * Q / g;
     }
     // phi
     int acc = 0;

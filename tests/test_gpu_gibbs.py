@@ -68,14 +68,16 @@ def test_chain_theta_posterior_means_agree_with_oracle(rsv, ctx, prec):
     Philox seed, so the chains are independent)."""
     T, n, n_md, dtau, burn = 2000, 1000, 50, 0.02, 200
     s = synth.rsv_series(T, TH, seed=0)
-    h = dev(s.h0)
+    # start from a posterior-typical state: at h = lnRV - xi the RV residuals
+    # vanish and the first s_u^2 draw is degenerate
+    h = dev(s.h_true)
     th = dev(TH)
     ths = torch.empty(n, 5, dtype=torch.float64, device="cuda")
     snaps = torch.empty(n, T, dtype=torch.float32, device="cuda")
     rsv.rsv_hmc_chain(ctx, h, dev(s.y), dev(s.lnrv), th, n_md, dtau, n, prec=prec, seed=31,
                       update_theta=True, theta_out=ths, snaps=snaps, thin=1)
     rsv.rsv_sync_status(ctx)
-    r = oracle.chain(s.h0, s.y, s.lnrv, TH, n_md, dtau, 32, n, update_theta=True, thin=1)
+    r = oracle.chain(s.h_true, s.y, s.lnrv, TH, n_md, dtau, 32, n, update_theta=True, thin=1)
     g = ths.cpu().numpy()[burn:]
     o = r["thetas"][burn:]
     se = np.sqrt(stats.batch_means_mcse(g) ** 2 + stats.batch_means_mcse(o) ** 2)
