@@ -81,11 +81,13 @@ int rsv_abi_version(void);
 /* Synchronise `stream`, return and clear the device status word. */
 rsv_status rsv_sync_status(rsv_ctx* ctx, void* stream);
 /* Fix the tiling of single-series trajectories (rsv_hmc_trajectory,
- * rsv_hmc_chain): `threads` per block (multiple of 32; <= 256 FP64, <= 384
- * mixed), `sites_per_thread` (FP64: 4, 8, 16, 28; mixed: 4, 8, 16, 20) and
- * `tile` owned sites per block (tile + 2 (n_md + 1) + 3 <= threads *
- * sites_per_thread, else the call that uses it fails with RSV_EINVAL).
- * All zero restores the automatic plan.  Results do not depend on the tiling. */
+ * rsv_hmc_chain) and of plans created afterwards: `threads` per block
+ * (multiple of 32; <= 256 FP64, <= 384 mixed), `sites_per_thread` (FP64: 4, 8,
+ * 16, 28; mixed: 4, 8, 16, 20) and `tile` owned sites per tile of a series cut
+ * into tiles (tile + 2 (n_md + 1) + 3 <= threads * sites_per_thread, else the
+ * call that uses it fails with RSV_EINVAL).  A single series no longer than
+ * `tile` is kept whole.  All zero restores the automatic plan.  Results do not
+ * depend on the tiling. */
 rsv_status rsv_set_schedule(rsv_ctx* ctx, int threads, int sites_per_thread, int64_t tile);
 
 /* ---- S(h) -----------------------------------------------------------------
@@ -149,6 +151,45 @@ rsv_status rsv_hmc_chain(rsv_ctx* ctx, double* h, const double* y, const double*
                          int update_theta, double* dH_out, int32_t* accept_out,
                          double* theta_out, float* snaps, int64_t thin, int fallback_window,
                          int32_t* mass_used_out, void* stream);
+
+/* ---- many independent series ----------------------------------------------
+ * A plan packs n independent series, stored end to end (series s occupies
+ * [offsets[s], offsets[s+1]) of every packed array), into the register
+ * windows of persistent blocks: series that fit a window are placed whole on
+ * whole warps, side by side; longer ones are cut into halo tiles.  Building a
+ * plan synchronises the device and allocates; running it does neither once the
+ * context workspace has grown (rsv_reserve), so rsv_hmc_batched can be
+ * captured in a CUDA graph.
+ *  offsets: HOST int64 [n_series + 1], offsets[0] = 0, increasing (T_s >= 1).
+ *  with_mass: 1 if rsv_hmc_batched will pass minv.
+ * rsv_plan_info reports the chosen block shape, bins, grid and the number of
+ * series cut into tiles (any output may be NULL). */
+typedef struct rsv_plan rsv_plan;
+rsv_status rsv_plan_create(rsv_ctx* ctx, const int64_t* offsets, int64_t n_series, int n_md,
+                           rsv_precision prec, int with_mass, rsv_plan** plan);
+void rsv_plan_destroy(rsv_plan* plan);
+rsv_status rsv_plan_info(const rsv_plan* plan, int* threads, int* sites_per_thread, int* bins,
+                         int* grid, int* split_series);
+
+/* n_traj HMC trajectories (Sec. 3) of every series of the plan, each with its
+ * own theta, all series advancing together in one persistent launch per
+ * trajectory.  Series s draws its momenta and Metropolis uniform from Philox
+ * with key {seed, 0} and counters {t/4, traj, 0, s} and {0, traj, 1, s}.
+ *  h        packed FP64 in/out (accepted states).
+ *  p        packed FP64 initial momenta (replaced by p'), or NULL to draw;
+ *           non-NULL only with n_traj = 1.
+ *  y, lnrv  packed FP64.   theta: device FP64 [n_series][5].
+ *  minv     packed FP32 inverse masses or NULL (the plan must match).
+ *  log_u    device FP64 [n_series] or NULL (draw); non-NULL only with n_traj = 1.
+ *  dH_out, accept_out: device [n_traj][n_series] FP64 / int32, or NULL.
+ * With RSV_MIXED the state of a series is carried as a (hi, lo) FP32 pair
+ * between trajectories (about 48 significant bits); with n_traj = 1 the h of a
+ * rejected series is left bit-for-bit unchanged. */
+rsv_status rsv_hmc_batched(rsv_ctx* ctx, rsv_plan* plan, double* h, double* p, const double* y,
+                           const double* lnrv, const double* theta, const float* minv,
+                           double dtau, uint64_t seed, uint64_t traj0, int64_t n_traj,
+                           const double* log_u, double* dH_out, int32_t* accept_out,
+                           void* stream);
 
 /* ---- theta update ---------------------------------------------------------
  * One Gibbs sweep of theta given h (the paper does not describe its theta

@@ -15,6 +15,7 @@
 #include "rsv_gibbs.cuh"
 #include "rsv_simple.cuh"
 #include "rsv_traj.cuh"
+#include "rsv_api_common.cuh"
 
 using namespace rsv;
 
@@ -98,52 +99,6 @@ rsv_status ctx_ensure_partials(rsv_ctx* c, int64_t n)
 }
 
 // Count a kernel launch made through launcher f.
-template <class F, class... A>
-cudaError_t counted(rsv_ctx* c, F f, A... a)
-{
-    ++c->launches;
-    return f(a...);
-}
-
-// Launch a trajectory kernel, bracketed by CUDA events when timing is on.
-cudaError_t timed_traj(rsv_ctx* c, const TrajArgs& a, const TileCfg& cfg, bool mixed, bool mass,
-                       cudaStream_t s)
-{
-    const bool rec = c->timing && !capture_active();
-    if (rec) {
-        if (c->ev_used + 2 > c->ev.size()) {
-            for (int i = 0; i < 2; ++i) {
-                cudaEvent_t e;
-                cudaError_t r = cudaEventCreate(&e);
-                if (r != cudaSuccess) return r;
-                c->ev.push_back(e);
-            }
-        }
-        cudaEventRecord(c->ev[c->ev_used], s);
-    }
-    cudaError_t e = launch_traj(a, cfg, mixed, mass, s);
-    if (rec) {
-        cudaEventRecord(c->ev[c->ev_used + 1], s);
-        c->ev_used += 2;
-    }
-    c->launches += 1;
-    c->traj_launches += 1;
-    return e;
-}
-
-rsv_status ctx_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, TileCfg& cfg)
-{
-    if (c->sched_nt) {
-        cfg = fixed_tiles(T, n_md, mixed, mass, c->sched_nt, c->sched_j, c->sched_tile);
-        if (cfg.nt == 0)
-            return fail(RSV_EINVAL, "schedule (%d threads, %d sites/thread, tile %lld) does not "
-                        "fit this call", c->sched_nt, c->sched_j, (long long)c->sched_tile);
-    } else {
-        cfg = plan_tiles(T, n_md, mixed, mass, c->num_sms);
-        if (cfg.nt == 0) return fail(RSV_EINVAL, "n_md too large for an on-chip window");
-    }
-    return ctx_ensure_partials(c, cfg.grid);
-}
 
 }  // namespace rsv
 
@@ -188,6 +143,7 @@ void rsv_destroy(rsv_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (auto& e : c->plans) free_plan(e.plan);
     for (Buf* b : c->all_bufs()) b->release();
     delete c;
 }
@@ -206,7 +162,11 @@ rsv_status rsv_reserve(rsv_ctx* c, int64_t max_T, int64_t max_series)
     if ((st = c->b0_f.ensure(T * 4)) != RSV_OK) return st;
     if ((st = c->lr_f.ensure(T * 8)) != RSV_OK) return st;
     if ((st = ctx_ensure_partials(c, (max_T / 64 + 4096))) != RSV_OK) return st;
-    (void)max_series;
+    const size_t n = (size_t)(max_series > 1 ? max_series : 1);
+    if ((st = c->ser_cur.ensure(n * sizeof(int))) != RSV_OK) return st;
+    if ((st = c->ser_cnt.ensure(n * sizeof(unsigned))) != RSV_OK) return st;
+    if ((st = c->ser_dh.ensure(n * sizeof(double))) != RSV_OK) return st;
+    if ((st = c->ser_acc.ensure(n * sizeof(int))) != RSV_OK) return st;
     return RSV_OK;
 }
 
@@ -281,220 +241,6 @@ rsv_status rsv_draw_momenta(rsv_ctx* c, uint64_t seed, uint64_t series, uint64_t
     cudaError_t e = counted(c, launch_draw_momenta, seed, series, traj, T, minv, bits, p_out,
                                         (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "momentum kernel");
-}
-
-rsv_status rsv_hmc_trajectory(rsv_ctx* c, double* h, double* p, const double* y,
-                              const double* lnrv, int64_t T, rsv_theta theta, const float* minv,
-                              int n_md, double dtau, rsv_precision prec, uint64_t seed,
-                              uint64_t traj, const double* log_u, double* dH_out,
-                              int32_t* accept_out, void* stream)
-{
-    rsv_status st = ctx_begin(c, stream);
-    if (st != RSV_OK) return st;
-    if (!h || !y || !lnrv || !dH_out || !accept_out) return fail(RSV_EINVAL, "null argument");
-    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
-    if (n_md < 1) return fail(RSV_EINVAL, "n_md must be >= 1");
-    if (!(dtau > 0.0) || !std::isfinite(dtau)) return fail(RSV_EINVAL, "dtau must be > 0");
-    if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
-    if (prec != RSV_FP64 && prec != RSV_MIXED) return fail(RSV_EINVAL, "bad precision");
-    if (n_md > (1 << 20)) return fail(RSV_EINVAL, "n_md too large");
-    const bool mixed = prec == RSV_MIXED, mass = minv != nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
-    TileCfg cfg;
-    if ((st = ctx_plan(c, T, n_md, mixed, mass, cfg)) != RSV_OK) return st;
-    const size_t Tz = (size_t)T;
-    if (p && (st = c->dbuf1.ensure(Tz * 8)) != RSV_OK) return st;  // p'
-    if (!mixed && (st = c->dbuf0.ensure(Tz * 8)) != RSV_OK) return st;  // h'
-    if (mixed) {
-        if ((st = c->fbuf0.ensure(Tz * 8)) != RSV_OK) return st;
-        if ((st = c->fbuf1.ensure(Tz * 8)) != RSV_OK) return st;
-        if ((st = c->a_f.ensure(Tz * 4)) != RSV_OK) return st;
-        if ((st = c->b0_f.ensure(Tz * 4)) != RSV_OK) return st;
-        if ((st = c->lr_f.ensure(Tz * 8)) != RSV_OK) return st;
-    }
-    int* ints = c->ints.as<int>();
-    TrajArgs a;
-    memset(&a, 0, sizeof(a));
-    a.cur = nullptr;
-    a.p_in = p;
-    a.p_out = p ? c->dbuf1.as<double>() : nullptr;
-    a.y = y;
-    a.lnrv = lnrv;
-    a.minv = minv;
-    a.mass_on = nullptr;
-    a.theta = nullptr;
-    a.th_inline = to_dev(theta);
-    a.T = T;
-    a.tile = cfg.tile;
-    a.K = n_md + 1;
-    a.n_md = n_md;
-    a.dtau = dtau;
-    a.seed = seed;
-    a.series = 0;
-    a.traj = traj;
-    a.log_u = log_u;
-    a.partials = c->partials.as<double>();
-    a.counter = reinterpret_cast<unsigned*>(ints + kTrajCounter);
-    a.dH_out = dH_out;
-    a.acc_out = accept_out;
-    a.status = ints + kStatus;
-    cudaError_t e;
-    if (mixed) {
-        a.a_f = c->a_f.as<float>();
-        a.b0_f = c->b0_f.as<float>();
-        a.lr_f = c->lr_f.as<float2>();
-        a.h0f = c->fbuf0.as<float2>();
-        a.h1f = c->fbuf1.as<float2>();
-        if ((e = counted(c, launch_prep_mixed, y, lnrv, c->a_f.as<float>(), c->b0_f.as<float>(),
-                                   c->lr_f.as<float2>(), T, s)) != cudaSuccess)
-            return cuda_fail(e, "prep kernel");
-        if ((e = counted(c, launch_h_to_ff, h, c->fbuf0.as<float2>(), T, s)) != cudaSuccess)
-            return cuda_fail(e, "state split kernel");
-        if ((e = timed_traj(c, a, cfg, true, mass, s)) != cudaSuccess)
-            return cuda_fail(e, "trajectory kernel");
-        if ((e = counted(c, launch_ff_to_h, c->fbuf1.as<float2>(), h, accept_out, T, s)) != cudaSuccess)
-            return cuda_fail(e, "state join kernel");
-        if (p && (e = counted(c, launch_commit_fp64, nullptr, nullptr, p, c->dbuf1.as<double>(), accept_out,
-                                         T, s)) != cudaSuccess)
-            return cuda_fail(e, "commit kernel");
-    } else {
-        a.h0d = h;
-        a.h1d = c->dbuf0.as<double>();
-        if ((e = timed_traj(c, a, cfg, false, mass, s)) != cudaSuccess)
-            return cuda_fail(e, "trajectory kernel");
-        if ((e = counted(c, launch_commit_fp64, h, c->dbuf0.as<double>(), p, c->dbuf1.as<double>(),
-                                    accept_out, T, s)) != cudaSuccess)
-            return cuda_fail(e, "commit kernel");
-    }
-    return RSV_OK;
-}
-
-rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* lnrv, int64_t T,
-                         double* theta, const float* minv, int n_md, double dtau,
-                         rsv_precision prec, uint64_t seed, uint64_t traj0, int64_t n_traj,
-                         int update_theta, double* dH_out, int32_t* accept_out,
-                         double* theta_out, float* snaps, int64_t thin, int fallback_window,
-                         int32_t* mass_used_out, void* stream)
-{
-    rsv_status st = ctx_begin(c, stream);
-    if (st != RSV_OK) return st;
-    if (!h || !y || !lnrv || !theta) return fail(RSV_EINVAL, "null argument");
-    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
-    if (n_md < 1 || n_md > (1 << 20)) return fail(RSV_EINVAL, "n_md out of range");
-    if (!(dtau > 0.0) || !std::isfinite(dtau)) return fail(RSV_EINVAL, "dtau must be > 0");
-    if (n_traj < 0) return fail(RSV_EINVAL, "n_traj must be >= 0");
-    if (prec != RSV_FP64 && prec != RSV_MIXED) return fail(RSV_EINVAL, "bad precision");
-    if (snaps && thin < 1) return fail(RSV_EINVAL, "thin must be >= 1 with snapshots");
-    if (fallback_window < 0) return fail(RSV_EINVAL, "fallback_window must be >= 0");
-    const bool mixed = prec == RSV_MIXED, mass = minv != nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
-    TileCfg cfg;
-    if ((st = ctx_plan(c, T, n_md, mixed, mass, cfg)) != RSV_OK) return st;
-    const size_t Tz = (size_t)T;
-    if (update_theta &&
-        (st = c->gibbs.ensure((size_t)gibbs_grid(T) * 8 * sizeof(double))) != RSV_OK)
-        return st;
-    if (mixed) {
-        if ((st = c->fbuf0.ensure(Tz * 8)) != RSV_OK) return st;
-        if ((st = c->fbuf1.ensure(Tz * 8)) != RSV_OK) return st;
-        if ((st = c->a_f.ensure(Tz * 4)) != RSV_OK) return st;
-        if ((st = c->b0_f.ensure(Tz * 4)) != RSV_OK) return st;
-        if ((st = c->lr_f.ensure(Tz * 8)) != RSV_OK) return st;
-    } else {
-        if ((st = c->dbuf0.ensure(Tz * 8)) != RSV_OK) return st;
-    }
-    int* ints = c->ints.as<int>();
-    double* scal = c->scalars.as<double>();
-    cudaError_t e;
-    // cur = 0, fallback state = 0, mass_on = (minv != NULL)
-    if ((e = cudaMemsetAsync(ints + kCur, 0, 4 * sizeof(int), s)) != cudaSuccess)
-        return cuda_fail(e, "memset");
-    if (mass && (e = cudaMemsetAsync(ints + kMassOn, 0x01, 1, s)) != cudaSuccess)
-        return cuda_fail(e, "memset");
-    TrajArgs a;
-    memset(&a, 0, sizeof(a));
-    a.cur = ints + kCur;
-    a.fb_state = ints + kFbState;
-    a.fallback_window = fallback_window;
-    a.mass_on = ints + kMassOn;
-    a.y = y;
-    a.lnrv = lnrv;
-    a.minv = minv;
-    a.theta = theta;
-    a.T = T;
-    a.tile = cfg.tile;
-    a.K = n_md + 1;
-    a.n_md = n_md;
-    a.dtau = dtau;
-    a.seed = seed;
-    a.series = 0;
-    a.partials = c->partials.as<double>();
-    a.counter = reinterpret_cast<unsigned*>(ints + kTrajCounter);
-    a.status = ints + kStatus;
-    if (mixed) {
-        a.a_f = c->a_f.as<float>();
-        a.b0_f = c->b0_f.as<float>();
-        a.lr_f = c->lr_f.as<float2>();
-        a.h0f = c->fbuf0.as<float2>();
-        a.h1f = c->fbuf1.as<float2>();
-        if ((e = counted(c, launch_prep_mixed, y, lnrv, c->a_f.as<float>(), c->b0_f.as<float>(),
-                                   c->lr_f.as<float2>(), T, s)) != cudaSuccess)
-            return cuda_fail(e, "prep kernel");
-        if ((e = counted(c, launch_h_to_ff, h, c->fbuf0.as<float2>(), T, s)) != cudaSuccess)
-            return cuda_fail(e, "state split kernel");
-    } else {
-        a.h0d = h;
-        a.h1d = c->dbuf0.as<double>();
-    }
-    for (int64_t i = 0; i < n_traj; ++i) {
-        a.traj = traj0 + (uint64_t)i;
-        a.dH_out = dH_out ? dH_out + i : scal + kScalDH;
-        a.acc_out = accept_out ? accept_out + i : ints + kScratchAcc;
-        if ((e = timed_traj(c, a, cfg, mixed, mass, s)) != cudaSuccess)
-            return cuda_fail(e, "trajectory kernel");
-        if (update_theta) {
-            GibbsArgs g;
-            memset(&g, 0, sizeof(g));
-            g.h0d = a.h0d;
-            g.h1d = a.h1d;
-            g.h0f = a.h0f;
-            g.h1f = a.h1f;
-            g.cur = a.cur;
-            g.lnrv = lnrv;
-            g.lr_f = a.lr_f;
-            g.T = T;
-            g.theta = theta;
-            g.theta_out = theta_out ? theta_out + 5 * i : nullptr;
-            g.seed = seed;
-            g.series = 0;
-            g.traj = a.traj;
-            g.mask = 31;
-            g.partials = c->gibbs.as<double>();
-            g.counter = reinterpret_cast<unsigned*>(ints + kGibbsCounter);
-            if ((e = counted(c, launch_gibbs, g, mixed, s)) != cudaSuccess)
-                return cuda_fail(e, "theta kernel");
-        } else if (theta_out) {
-            if ((e = cudaMemcpyAsync(theta_out + 5 * i, theta, 5 * sizeof(double),
-                                     cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-                return cuda_fail(e, "theta record");
-        }
-        if (snaps && (i + 1) % thin == 0) {
-            float* dst = snaps + (size_t)((i + 1) / thin - 1) * Tz;
-            e = mixed ? counted(c, launch_snapshot, nullptr, nullptr, a.h0f, a.h1f, a.cur, dst, T, s)
-                      : counted(c, launch_snapshot, a.h0d, a.h1d, nullptr, nullptr, a.cur, dst, T, s);
-            if (e != cudaSuccess) return cuda_fail(e, "snapshot kernel");
-        }
-    }
-    // final state back into h
-    e = mixed ? counted(c, launch_ff_to_h_sel, a.h0f, a.h1f, a.cur, h, T, s)
-              : counted(c, launch_d_sel, a.h0d, a.h1d, a.cur, h, T, s);
-    if (e != cudaSuccess) return cuda_fail(e, "state copy kernel");
-    if (mass_used_out) {
-        if ((e = cudaMemcpyAsync(mass_used_out, ints + kMassOn, sizeof(int),
-                                 cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-            return cuda_fail(e, "mass flag copy");
-    }
-    return RSV_OK;
 }
 
 rsv_status rsv_gibbs_theta(rsv_ctx* c, const double* h, const double* lnrv, int64_t T,

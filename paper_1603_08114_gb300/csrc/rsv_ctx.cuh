@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "rsv.h"
+#include "rsv_traj.cuh"
 
 namespace rsv {
 
@@ -37,9 +38,25 @@ enum ScalSlot : int { kScalDH = 0 };
 
 }  // namespace rsv
 
+struct rsv_plan {
+    rsv::Plan plan;
+    int device = 0;
+};
+
 struct rsv_ctx {
     int device = 0;
     int num_sms = 0;
+    // single-series plans, keyed by (T, n_md, precision, mass, schedule)
+    struct Cached {
+        int64_t T;
+        int n_md;
+        bool mixed, mass;
+        int nt, j;
+        int64_t tile;
+        rsv::Plan plan;
+    };
+    std::vector<Cached> plans;
+    rsv::Buf ser_cur, ser_cnt, ser_dh, ser_acc;  // per-series scratch
     int sched_nt = 0, sched_j = 0;  // rsv_set_schedule override (0 = automatic)
     int64_t sched_tile = 0;
     // accounting: kernel launches, and CUDA events around trajectory kernels
@@ -60,7 +77,7 @@ struct rsv_ctx {
     std::vector<rsv::Buf*> all_bufs()
     {
         return {&ints, &scalars, &partials, &dbuf0, &dbuf1, &fbuf0, &fbuf1, &a_f, &b0_f, &lr_f,
-                &gibbs, &batch, &extra};
+                &gibbs, &batch, &extra, &ser_cur, &ser_cnt, &ser_dh, &ser_acc};
     }
 };
 

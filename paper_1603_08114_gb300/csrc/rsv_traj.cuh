@@ -1,83 +1,114 @@
-// rsv_traj.cuh -- launch interface of the trajectory kernels (host side).
+// rsv_traj.cuh -- the trajectory kernels and their work plan (host side).
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "rsv_device.cuh"
 
 namespace rsv {
 
-// Arguments of one HMC trajectory over one series, split into tiles.  Tile b
-// owns sites [b*tile, min(T,(b+1)*tile)) and integrates the window extended by
-// K = n_md + 1 sites on each side (left edge rounded down to a multiple of 4),
-// so that its owned sites (and the right neighbour needed by dH) are exact
-// after n_md steps without any exchange between tiles.
-struct TrajArgs {
-    // FP64 state (FP64 path): h0/h1 double buffer; cur selects the input.
-    const double* h0d;
-    double* h1d;
-    // double-float state (mixed path): (hi, lo) of h.
-    const float2* h0f;
-    float2* h1f;
-    int* cur;                 // device: 0 -> read buffer 0, write buffer 1; NULL = 0 always
-    const double* p_in;       // optional initial momenta (FP64)
-    double* p_out;            // optional p' (FP64), must not alias p_in
-    const double* y;          // FP64 path inputs
-    const double* lnrv;
-    const float* a_f;         // mixed path per-site constants: y^2/2
-    const float* b0_f;        //   log2(y^2/2)
-    const float2* lr_f;       //   lnRV as (hi, lo)
-    const float* minv;        // optional inverse mass (FP32)
-    const int* mass_on;       // optional device flag; 0 = use m = 1
-    const double* theta;      // device [5], or NULL to use th_inline
-    ThetaD th_inline;
+// One contiguous run of one series inside one bin (a block's register window).
+// A bin holds either several whole series side by side (each on whole warps),
+// or one tile of a series too long for a window.  A tile integrates the window
+// [wlo, whi) = its owned sites [lo, hi) widened by K = n_md + 1 sites on both
+// sides (wlo rounded down to a multiple of 4), so that its owned sites and the
+// right neighbour that dH needs are exact after n_md steps with no exchange
+// between tiles.  Indices are series-local.
+struct Seg {
+    int64_t lo, hi;    // owned sites
+    int64_t wlo, whi;  // integrated window
+    int series;
+    int warp0, nwarp;  // placement in the bin
+    int split;         // 1: one tile of a series spread over several bins
+};
+
+struct SerInfo {
+    int64_t off;  // first index of the series in the packed arrays
     int64_t T;
-    int64_t tile;
-    int K;
+    int nseg;     // tiles of a split series (1 for a whole series)
+    int seg0;     // segment id of its first tile (tiles have consecutive ids)
+};
+
+// Kernel configuration and the device copy of a plan.
+struct Plan {
+    int nt = 0, j = 0;          // threads per block, sites per thread
+    int nbins = 0, grid = 0;
+    size_t smem = 0;
+    int64_t nsegs = 0;          // partials are indexed by segment id
+    int nseries = 0;
+    int nsplit = 0;             // series spread over several bins
+    int64_t total = 0;          // packed length
+    // device arrays (owned by the plan)
+    Seg* d_segs = nullptr;
+    int* d_bin_first = nullptr;  // [nbins + 1]
+    int* d_bin_seg = nullptr;    // segment ids, bin-major
+    SerInfo* d_ser = nullptr;
+    int n_md = 0;
+    bool mixed = false, mass = false;
+};
+
+struct TrajArgs {
+    const Seg* segs;
+    const int* bin_first;
+    const int* bin_seg;
+    int nbins;
+    const SerInfo* ser;
+    // theta: device [nseries][5], or NULL to use th_inline for every series
+    const double* theta;
+    ThetaD th_inline;
+    int* ser_cur;        // buffer selector per series (NULL: all 0)
+    unsigned* ser_cnt;   // arrival counters of split series (zero between launches)
+    double* partials;    // per segment id
+    double* dH_out;      // per series
+    int* acc_out;        // per series
+    const double* log_u; // per series, or NULL (drawn from Philox)
+    // state: FP64 double buffer (FP64 path) or (hi, lo) FP32 double buffer (mixed)
+    double* h0d;
+    double* h1d;
+    float2* h0f;
+    float2* h1f;
+    const double* p_in;  // optional initial momenta (FP64, packed)
+    double* p_out;       // optional p' (FP64, packed), must not alias p_in
+    const double* y;     // FP64 path
+    const double* lnrv;
+    const float* a_f;    // mixed path: y^2/2, log2(y^2/2), lnRV as (hi, lo)
+    const float* b0_f;
+    const float2* lr_f;
+    const float* minv;   // optional inverse mass (FP32, packed)
+    const int* mass_on;  // optional flag; 0 = use m = 1
     int n_md;
     double dtau;
-    uint64_t seed, series, traj;
-    const double* log_u;      // optional device scalar
-    double* partials;         // [gridDim.x]
-    unsigned* counter;        // zero before launch; last block resets it
-    double* dH_out;           // device scalar
-    int* acc_out;             // device scalar
+    uint64_t seed, traj;
     int* status;
-    // chain bookkeeping (optional): mass fallback over windows of trajectories
-    int* fb_state;            // [2]: accepted count in window, trajectories in window
+    int* fb_state;       // [2] mass fallback window counters (single series)
     int fallback_window;
 };
 
-// Kernel configuration: threads per block and sites per thread.
-struct TileCfg {
-    int nt;
-    int j;
-    int64_t tile;
-    int grid;
-    size_t smem;
-};
+// Build a plan for the series with the given offsets (host, [n+1]).
+// sched_nt / sched_j / sched_tile > 0 fix the tiling, 0 chooses it.
+// Returns false (reason in *why) if no tiling fits.
+bool make_plan(const int64_t* offsets, int n, int n_md, bool mixed, bool mass, int num_sms,
+               int sched_nt, int sched_j, int64_t sched_tile, Plan& plan, const char** why);
+void free_plan(Plan& plan);
 
-// Choose a tiling for a series of length T (window capacity nt*j per block).
-TileCfg plan_tiles(int64_t T, int n_md, bool mixed, bool mass, int num_sms);
-// The fixed tiling (nt, j, tile), or nt = 0 if it is not valid for this call.
-TileCfg fixed_tiles(int64_t T, int n_md, bool mixed, bool mass, int nt, int j, int64_t tile);
+cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st);
+// Resident blocks per SM of a trajectory kernel configuration (0 if invalid).
+int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem);
 
-cudaError_t launch_traj(const TrajArgs& a, const TileCfg& c, bool mixed, bool mass,
-                        cudaStream_t st);
 cudaError_t launch_commit_fp64(double* h, const double* hprop, double* p, const double* pprop,
                                const int* acc, int64_t T, cudaStream_t st);
 cudaError_t launch_prep_mixed(const double* y, const double* lnrv, float* a_f, float* b0_f,
                               float2* lr_f, int64_t T, cudaStream_t st);
 cudaError_t launch_h_to_ff(const double* h, float2* hf, int64_t T, cudaStream_t st);
-cudaError_t launch_ff_to_h(const float2* hf, double* h, const int* acc, int64_t T,
-                           cudaStream_t st);
-cudaError_t launch_ff_to_h_sel(const float2* b0, const float2* b1, const int* cur, double* h,
-                               int64_t T, cudaStream_t st);
-cudaError_t launch_d_sel(const double* b0, const double* b1, const int* cur, double* h,
-                         int64_t T, cudaStream_t st);
-cudaError_t launch_snapshot(const double* b0, const double* b1, const float2* f0,
-                            const float2* f1, const int* cur, float* out, int64_t T,
-                            cudaStream_t st);
+// Write the current state of every series into h (packed FP64): FP64 path
+// from h1d where cur[s] = 1 (h0d is h itself); mixed path from the (hi, lo)
+// buffer cur[s], restricted to series with acc[s] = 1 when acc != NULL.
+cudaError_t launch_finalize(const Plan& p, const int* cur, const int* acc, const double* h1d,
+                            const float2* h0f, const float2* h1f, double* h, cudaStream_t st);
+cudaError_t launch_snapshot(const Plan& p, const int* cur, const double* h0d, const double* h1d,
+                            const float2* h0f, const float2* h1f, float* out, cudaStream_t st);
 
 }  // namespace rsv

@@ -70,12 +70,19 @@ def lib():
         L.rsv_draw_momenta.argtypes = [_P, _U64, _U64, _U64, _I64, _P, _INT, _P, _P]
         L.rsv_ess.argtypes = [_P, _P, _I64, _I64, _P, _P]
         L.rsv_gibbs_theta.argtypes = [_P, _P, _P, _I64, _P, _U64, _U64, _U64, _INT, _P, _P]
+        L.rsv_plan_create.argtypes = [_P, _P, _I64, _INT, _INT, _INT, ctypes.POINTER(_P)]
+        L.rsv_plan_destroy.argtypes = [_P]
+        L.rsv_plan_destroy.restype = None
+        L.rsv_plan_info.argtypes = [_P] + [ctypes.POINTER(_INT)] * 5
+        L.rsv_hmc_batched.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_double, _U64,
+                                      _U64, _I64, _P, _P, _P, _P]
         L.rsv_timing.argtypes = [_P, _INT]
         L.rsv_stats.argtypes = [_P, _INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                 ctypes.POINTER(ctypes.c_double)]
         for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule", "rsv_action", "rsv_force",
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
-                     "rsv_timing", "rsv_stats", "rsv_gibbs_theta"):
+                     "rsv_timing", "rsv_stats", "rsv_gibbs_theta", "rsv_plan_create",
+                     "rsv_plan_info", "rsv_hmc_batched"):
             getattr(L, name).restype = _INT
         _lib = L
     return _lib
@@ -250,3 +257,54 @@ def rsv_gibbs_theta(ctx: Context, h, lnrv, theta_dev, seed: int, series: int = 0
                                  _ptr(theta_dev, torch.float64, 5, "theta"), int(seed),
                                  int(series), int(traj), int(mask),
                                  _ptr(phi_acc_out, torch.int32, 1, "phi_acc_out"), _stream()))
+
+
+class Plan:
+    """An rsv_plan: n independent series packed end to end (offsets [n+1])."""
+
+    def __init__(self, ctx: Context, offsets, n_md: int, prec="mixed", with_mass=False):
+        import numpy as np
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.n_series = len(off) - 1
+        self.total = int(off[-1])
+        self.ctx = ctx
+        self.prec = _prec(prec)
+        h = _P()
+        _check(lib().rsv_plan_create(ctx.handle, off.ctypes.data_as(_P), self.n_series, int(n_md),
+                                     self.prec, int(bool(with_mass)), ctypes.byref(h)))
+        self.handle = h
+
+    def info(self):
+        v = [_INT() for _ in range(5)]
+        _check(lib().rsv_plan_info(self.handle, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("threads", "sites_per_thread", "bins", "grid", "split_series"),
+                        [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rsv_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rsv_plan_create(ctx: Context, offsets, n_md: int, prec="mixed", with_mass=False) -> Plan:
+    return Plan(ctx, offsets, n_md, prec, with_mass)
+
+
+def rsv_hmc_batched(ctx: Context, plan: Plan, h, y, lnrv, theta_dev, dtau: float, p=None,
+                    minv=None, seed: int = 0, traj0: int = 0, n_traj: int = 1, log_u=None,
+                    dH_out=None, accept_out=None):
+    """n_traj trajectories of every series of the plan, in place on h (packed FP64)."""
+    N, n = plan.total, plan.n_series
+    _check(lib().rsv_hmc_batched(
+        ctx.handle, plan.handle, _ptr(h, torch.float64, N, "h"), _ptr(p, torch.float64, N, "p"),
+        _ptr(y, torch.float64, N, "y"), _ptr(lnrv, torch.float64, N, "lnrv"),
+        _ptr(theta_dev, torch.float64, 5 * n, "theta"), _ptr(minv, torch.float32, N, "minv"),
+        float(dtau), int(seed), int(traj0), int(n_traj), _ptr(log_u, torch.float64, n, "log_u"),
+        _ptr(dH_out, torch.float64, n * n_traj, "dH_out"),
+        _ptr(accept_out, torch.int32, n * n_traj, "accept_out"), _stream()))
