@@ -62,30 +62,33 @@ def test_chain_with_theta_fp64_matches_oracle(rsv, ctx):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_chain_theta_posterior_means_agree_with_oracle(rsv, ctx, prec):
-    """The 2000-site workload with theta sampled: 1000 trajectories of 50 x 0.02.
-    Posterior means of theta and of a few h_t from the GPU chain lie within 3
-    combined Monte-Carlo standard errors of the oracle chain's (different
-    Philox seed, so the chains are independent)."""
-    T, n, n_md, dtau, burn = 2000, 1000, 50, 0.02, 200
+    """The 2000-site workload with theta sampled (50 x 0.02 per trajectory).
+    Posterior means of theta and of a few h_t from the GPU chain lie within
+    3.5 combined Monte-Carlo standard errors (sd / sqrt(ESS), Geyer) of the
+    oracle chain's (different Philox seed, so the chains are independent).
+    theta mixes slowly (phi, s_eta^2 autocorrelation times of ~100), hence
+    4000 trajectories."""
+    T, n, n_md, dtau, burn = 2000, 4000, 50, 0.02, 500
     s = synth.rsv_series(T, TH, seed=0)
     # start from a posterior-typical state: at h = lnRV - xi the RV residuals
     # vanish and the first s_u^2 draw is degenerate
     h = dev(s.h_true)
     th = dev(TH)
     ths = torch.empty(n, 5, dtype=torch.float64, device="cuda")
-    snaps = torch.empty(n, T, dtype=torch.float32, device="cuda")
+    snaps = torch.empty(n // 2, T, dtype=torch.float32, device="cuda")
     rsv.rsv_hmc_chain(ctx, h, dev(s.y), dev(s.lnrv), th, n_md, dtau, n, prec=prec, seed=31,
-                      update_theta=True, theta_out=ths, snaps=snaps, thin=1)
+                      update_theta=True, theta_out=ths, snaps=snaps, thin=2)
     rsv.rsv_sync_status(ctx)
-    r = oracle.chain(s.h_true, s.y, s.lnrv, TH, n_md, dtau, 32, n, update_theta=True, thin=1)
+    r = oracle.chain(s.h_true, s.y, s.lnrv, TH, n_md, dtau, 32, n, update_theta=True, thin=2)
+    def mcse(x):
+        return x.std(0, ddof=1) / np.sqrt(stats.ess_geyer(x))
+
     g = ths.cpu().numpy()[burn:]
     o = r["thetas"][burn:]
-    se = np.sqrt(stats.batch_means_mcse(g) ** 2 + stats.batch_means_mcse(o) ** 2)
-    z = np.abs(g.mean(0) - o.mean(0)) / se
+    z = np.abs(g.mean(0) - o.mean(0)) / np.sqrt(mcse(g) ** 2 + mcse(o) ** 2)
     assert np.all(z < 3.5), z
     cols = [0, 7, 500, 1999]
-    gh = snaps.cpu().numpy()[burn:, cols].astype(np.float64)
-    oh = r["snaps"][burn:, cols]
-    se = np.sqrt(stats.batch_means_mcse(gh) ** 2 + stats.batch_means_mcse(oh) ** 2)
-    z = np.abs(gh.mean(0) - oh.mean(0)) / se
+    gh = snaps.cpu().numpy()[burn // 2:, cols].astype(np.float64)
+    oh = r["snaps"][burn // 2:, cols]
+    z = np.abs(gh.mean(0) - oh.mean(0)) / np.sqrt(mcse(gh) ** 2 + mcse(oh) ** 2)
     assert np.all(z < 3.5), z
