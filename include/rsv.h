@@ -96,6 +96,28 @@ rsv_status rsv_set_schedule(rsv_ctx* ctx, int threads, int sites_per_thread, int
 rsv_status rsv_action(rsv_ctx* ctx, const double* h, const double* y, const double* lnrv,
                       int64_t T, rsv_theta theta, double* S_out, void* stream);
 
+/* ---- S(h) without allocation ----------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory: code running while a CUDA graph is being
+ * captured (an allocation there is not part of the graph and breaks its
+ * replay), plug-ins inside a host application that owns the device memory
+ * pool, and real-time loops that must not wait on the allocator.
+ * It computes the same S(h) as rsv_action, on the CURRENT device and without a
+ * context.  Its scratch (one FP64 partial sum per block of 2048 sites and an
+ * arrival counter, 33 KB) is a fixed array in device memory that every device
+ * which loads the library holds until the process exits; nothing is allocated
+ * or freed.  Limits and behaviour:
+ *  - T must be 1 .. 8,388,608 (4096 blocks of 2048 sites); larger T returns
+ *    RSV_EINVAL before any launch (use rsv_action).
+ *  - The first call on a device looks up the array's device address (one-time
+ *    set-up); make that first call before any stream capture.
+ *  - All calls share the one array: calls that can overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the caller.
+ *    The arrival counter is cleared by each call before its launch.
+ *  - Errors are returned as by rsv_action; rsv_last_error() gives the text. */
+rsv_status rsv_action_noalloc(const double* h, const double* y, const double* lnrv, int64_t T,
+                              rsv_theta theta, double* S_out, void* stream);
+
 /* ---- dS/dh ----------------------------------------------------------------
  * F_t = dS/dh_t, the derivative in eq. (7):
  *   F_t = 1/2 - (y_t^2/2) e^{-h_t} - (lnRV_t - xi - h_t)/sigma_u^2 + AR_t,
