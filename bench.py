@@ -2,9 +2,9 @@
 
 Workload (the single-chain large-series case): T = 2^20 sites of a synthetic
 RSV series (phi, mu, xi, s_eta^2, s_u^2) = (0.95, -0.5, -0.2, 0.05, 0.1), seed 1;
-one step = one chain segment of 200 HMC trajectories of 100 leapfrog steps of
-dtau = 0.005 (momenta, leapfrog, dH, Metropolis for every trajectory), run by
-one rsv_hmc_chain call that also records every trajectory's h for ESS.  The
+one step = one chain segment of 200 HMC sweeps (momenta, 100 leapfrog steps of
+dtau = 0.005, dH, Metropolis, then a Gibbs sweep of theta), run by one
+rsv_hmc_chain call that also records every trajectory's h and theta for ESS.  The
 chain continues from step to step (the warm-up steps are its burn-in).
 
 Reported: leapfrog site-updates/s (T * n_md * trajectories / time) and ESS/s
@@ -38,6 +38,7 @@ N_TRAJ = 200  # trajectories per step (--traj-per-step changes it for profiling 
 SEED_DATA = 1
 METRIC = "leapfrog site-updates/s & ESS/s at T=2^20, mixed+learned vs FP64 plain, 1 GB300"
 UNIT = "site-updates/s"
+THETA_NAMES = ("phi", "mu", "xi", "sig_eta2", "sig_u2")
 WORKLOAD = "rsv-hmc single chain T=2^20, 200 traj x 100 x 0.005 per step"
 # Algorithmic instructions per site and leapfrog step of the mixed kernel on the
 # FP32/issue pipes: innovation (1), AR (1), force (3) + exponent argument (1),
@@ -220,20 +221,23 @@ def run_ours(args):
     if args.mass_file:
         minv = torch.tensor(np.load(args.mass_file).astype(np.float32), device=dev)
 
+    thetas = torch.empty(N_TRAJ, 5, dtype=torch.float64, device=dev)
+
     def arm(prec, mass, warmup, steps, clocks=None, timing=False):
         # the chain starts from the generator's latent path, a posterior-typical
-        # state (from lnRV - xi the first trajectories are all rejected)
+        # state (from lnRV - xi the first trajectories are all rejected); every
+        # trajectory is followed by a Gibbs sweep of theta
         h = torch.tensor(s.h_true, device=dev)
         th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
         traj = 0
         for _ in range(warmup):
             rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, N_MD, DTAU, N_TRAJ, prec=prec, minv=mass,
-                              seed=11 + rank, traj0=traj)
+                              seed=11 + rank, traj0=traj, update_theta=True)
             traj += N_TRAJ
         rsv.rsv_sync_status(ctx)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
-        ess_med, ess_min, acc_rate = [], [], []
+        ess_med, ess_min, ess_th, acc_rate = [], [], [], []
         rsv.rsv_stats(ctx, reset=True)
         rsv.rsv_timing(ctx, timing)
         _barrier(ws)
@@ -246,13 +250,14 @@ def run_ours(args):
             ev[k][0].record()
             rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, N_MD, DTAU, N_TRAJ, prec=prec, minv=mass,
                               seed=11 + rank, traj0=traj, snaps=snaps, thin=1, accept_out=acc,
-                              dH_out=dH)
+                              dH_out=dH, update_theta=True, theta_out=thetas)
             ev[k][1].record()
             traj += N_TRAJ
             launches += rsv.rsv_stats(ctx, reset=False)[0] - l0
             e = rsv.rsv_ess(ctx, snaps)
             ess_med.append(e.median())
             ess_min.append(e.min())
+            ess_th.append(rsv.rsv_ess(ctx, thetas.float().contiguous()))
             acc_rate.append(acc.float().mean())
         _barrier(ws)
         if clocks:
@@ -266,22 +271,77 @@ def run_ours(args):
         sec_per_step = total_s / steps
         ess_med = [float(x) for x in ess_med]
         ess_min = [float(x) for x in ess_min]
+        ess_th = torch.stack(ess_th).mean(0).cpu().numpy()
         return dict(
             site_updates_per_s=ws * T_SITES * N_MD * N_TRAJ / sec_per_step,
             ms_per_step=1e3 * sec_per_step,
             ess_h_median_per_s=ws * statistics.mean(ess_med) / sec_per_step,
             ess_h_min_per_s=ws * statistics.mean(ess_min) / sec_per_step,
             ess_h_median=statistics.mean(ess_med), ess_h_min=statistics.mean(ess_min),
+            ess_theta_per_s={n: ws * float(v) / sec_per_step
+                             for n, v in zip(THETA_NAMES, ess_th)},
+            ess_theta_per_step={n: float(v) for n, v in zip(THETA_NAMES, ess_th)},
             accept_rate=float(statistics.mean(float(a) for a in acc_rate)),
             launches=launches, traj_launches=traj_launches, traj_ms=traj_ms)
+
+    def batched_leg(steps):
+        """The 4096-series workload: one persistent launch per trajectory of all
+        series, autotuned block shape, replayed from a CUDA graph."""
+        from paper_1603_08114_gb300 import autotune
+        b = synth.rsv_batch(4096, 500, 8192, seed=2)
+        n = len(b.offsets) - 1
+        N = int(b.offsets[-1])
+        yb, lb = torch.tensor(b.y, device=dev), torch.tensor(b.lnrv, device=dev)
+        thb = torch.tensor(b.theta.ravel(), device=dev)
+        h0 = torch.tensor(b.h_true, device=dev)
+        hb = h0.clone()
+        rsv.rsv_reserve(ctx, max(N, T_SITES), n)
+        plan, sched = autotune.tune_plan(ctx, b.offsets, 50, "mixed", yb, lb, thb, 0.02, h0)
+        accb = torch.empty(n, dtype=torch.int32, device=dev)
+        traj = torch.zeros(1, dtype=torch.int64)
+        rsv.rsv_hmc_batched(ctx, plan, hb, yb, lb, thb, 0.02, seed=3, traj0=0, accept_out=accb)
+        torch.cuda.synchronize()
+        stream = torch.cuda.Stream()
+        graphs = []
+        with torch.cuda.stream(stream):
+            for k in range(steps + 3):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    rsv.rsv_hmc_batched(ctx, plan, hb, yb, lb, thb, 0.02, seed=3, traj0=1 + k,
+                                        accept_out=accb)
+                graphs.append(g)
+        for g in graphs[:3]:
+            g.replay()
+        torch.cuda.synchronize()
+        rates = []
+        ms = 0.0
+        for g in graphs[3:]:
+            flush.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            c.record()
+            c.synchronize()
+            ms += a.elapsed_time(c)
+            rates.append(float(accb.float().mean()))
+        rsv.rsv_sync_status(ctx)
+        info = plan.info()
+        plan.close()
+        return {"site_updates_per_s": N * 50 * steps / (ms / 1e3), "ms_per_trajectory": ms / steps,
+                "series": n, "sites": N, "n_md": 50, "dtau": 0.02, "precision": "mixed",
+                "accept_rate": statistics.mean(rates), "graph": True,
+                "schedule": {"threads": sched["threads"], "sites_per_thread":
+                             sched["sites_per_thread"], "cached": sched["cached"], **info}}
 
     # headline: mixed precision (diagonal mass when given)
     clocks = Clocks(local)
     head = arm("mixed", minv, args.warmup, args.steps, clocks=clocks, timing=True)
     # comparison: plain FP64 sampler, identity mass (at most 3 timed steps)
     fp64 = None
+    batched = None
     if args.only != "mixed":
         fp64 = arm("fp64", None, min(args.warmup, 3), min(args.steps, 3))
+        batched = batched_leg(max(3, min(args.steps, 10)))
 
     # end to end through the public API with host buffers: H2D of the step's
     # inputs (h, y, lnRV, theta) from pinned memory, the chain, D2H of h' and
@@ -346,13 +406,18 @@ def run_ours(args):
             "ess": {"h_median_per_s": head["ess_h_median_per_s"],
                     "h_min_per_s": head["ess_h_min_per_s"],
                     "h_median_per_step": head["ess_h_median"],
-                    "h_min_per_step": head["ess_h_min"], "accept_rate": head["accept_rate"]},
+                    "h_min_per_step": head["ess_h_min"],
+                    "theta_per_s": head["ess_theta_per_s"],
+                    "theta_per_step": head["ess_theta_per_step"],
+                    "accept_rate": head["accept_rate"]},
             "fp64_plain": None if fp64 is None else {
                 "site_updates_per_s": fp64["site_updates_per_s"],
                 "ms_per_step": fp64["ms_per_step"],
                 "ess_h_median_per_s": fp64["ess_h_median_per_s"],
                 "ess_h_min_per_s": fp64["ess_h_min_per_s"],
+                "ess_theta_per_s": fp64["ess_theta_per_s"],
                 "accept_rate": fp64["accept_rate"]},
+            "batched": batched,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
                          "kernel": "k_traj_mixed", "peak_kind": "nominal FP32-lane issue "
