@@ -297,9 +297,10 @@ def run_ours(args):
         hb = h0.clone()
         rsv.rsv_reserve(ctx, max(N, T_SITES), n)
         plan, sched = autotune.tune_plan(ctx, b.offsets, 50, "mixed", yb, lb, thb, 0.02, h0)
-        accb = torch.empty(n, dtype=torch.int32, device=dev)
-        traj = torch.zeros(1, dtype=torch.int64)
-        rsv.rsv_hmc_batched(ctx, plan, hb, yb, lb, thb, 0.02, seed=3, traj0=0, accept_out=accb)
+        per_graph = 10  # trajectories of every series per graph replay
+        accb = torch.empty(per_graph * n, dtype=torch.int32, device=dev)
+        rsv.rsv_hmc_batched(ctx, plan, hb, yb, lb, thb, 0.02, seed=3, traj0=0, n_traj=per_graph,
+                            accept_out=accb)
         torch.cuda.synchronize()
         stream = torch.cuda.Stream()
         graphs = []
@@ -307,7 +308,8 @@ def run_ours(args):
             for k in range(steps + 3):
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=stream):
-                    rsv.rsv_hmc_batched(ctx, plan, hb, yb, lb, thb, 0.02, seed=3, traj0=1 + k,
+                    rsv.rsv_hmc_batched(ctx, plan, hb, yb, lb, thb, 0.02, seed=3,
+                                        traj0=per_graph * (1 + k), n_traj=per_graph,
                                         accept_out=accb)
                 graphs.append(g)
         for g in graphs[:3]:
@@ -327,9 +329,11 @@ def run_ours(args):
         rsv.rsv_sync_status(ctx)
         info = plan.info()
         plan.close()
-        return {"site_updates_per_s": N * 50 * steps / (ms / 1e3), "ms_per_trajectory": ms / steps,
+        ntr = per_graph * steps
+        return {"site_updates_per_s": N * 50 * ntr / (ms / 1e3), "ms_per_trajectory": ms / ntr,
                 "series": n, "sites": N, "n_md": 50, "dtau": 0.02, "precision": "mixed",
                 "accept_rate": statistics.mean(rates), "graph": True,
+                "trajectories_per_graph": per_graph,
                 "schedule": {"threads": sched["threads"], "sites_per_thread":
                              sched["sites_per_thread"], "cached": sched["cached"], **info}}
 
