@@ -159,7 +159,6 @@ rsv_status rsv_reserve(rsv_ctx* c, int64_t max_T, int64_t max_series)
     if ((st = c->fbuf0.ensure(T * 8)) != RSV_OK) return st;
     if ((st = c->fbuf1.ensure(T * 8)) != RSV_OK) return st;
     if ((st = c->a_f.ensure(T * 4)) != RSV_OK) return st;
-    if ((st = c->b0_f.ensure(T * 4)) != RSV_OK) return st;
     if ((st = c->lr_f.ensure(T * 8)) != RSV_OK) return st;
     if ((st = ctx_ensure_partials(c, (max_T / 64 + 4096))) != RSV_OK) return st;
     const size_t n = (size_t)(max_series > 1 ? max_series : 1);

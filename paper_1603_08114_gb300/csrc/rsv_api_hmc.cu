@@ -87,7 +87,6 @@ rsv_status ensure_plan_ws(rsv_ctx* c, const Plan& p, bool mixed, bool need_p)
         if ((st = c->fbuf0.ensure(N * 8)) != RSV_OK) return st;
         if ((st = c->fbuf1.ensure(N * 8)) != RSV_OK) return st;
         if ((st = c->a_f.ensure(N * 4)) != RSV_OK) return st;
-        if ((st = c->b0_f.ensure(N * 4)) != RSV_OK) return st;
         if ((st = c->lr_f.ensure(N * 8)) != RSV_OK) return st;
     } else {
         if ((st = c->dbuf0.ensure(N * 8)) != RSV_OK) return st;
@@ -166,12 +165,11 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
     a.fallback_window = o.fallback_window;
     if (mixed) {
         a.a_f = c->a_f.as<float>();
-        a.b0_f = c->b0_f.as<float>();
         a.lr_f = c->lr_f.as<float2>();
         a.h0f = c->fbuf0.as<float2>();
         a.h1f = c->fbuf1.as<float2>();
         if ((e = counted(c, launch_prep_mixed, o.y, o.lnrv, c->a_f.as<float>(),
-                         c->b0_f.as<float>(), c->lr_f.as<float2>(), P.total, s)) != cudaSuccess)
+                         c->lr_f.as<float2>(), P.total, s)) != cudaSuccess)
             return cuda_fail(e, "prep kernel");
         if ((e = counted(c, launch_h_to_ff, (const double*)o.h, c->fbuf0.as<float2>(), P.total,
                          s)) != cudaSuccess)

@@ -139,6 +139,44 @@ __host__ __device__ __forceinline__ ff ff_from_double(double d)
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// Table of 2^(j/32), j = 0..31, as double-float pairs (filled by ff_exp_table).
+__device__ __forceinline__ void ff_exp_table(float2* tab)
+{
+    for (int j = threadIdx.x; j < 32; j += blockDim.x) {
+        const ff v = ff_from_double(exp2((double)j / 32.0));
+        tab[j] = make_float2(v.hi, v.lo);
+    }
+}
+
+// e^t in double-float (relative error ~1e-12 for |t| < 80, the caller's
+// range), table-driven:
+// t = k ln2/32 + r with k = rint(32 t / ln2), |r| <= ln2/64; e^t =
+// 2^(k div 32) 2^((k mod 32)/32) e^r, e^r = 1 + r + q with the tail
+// q = r^2 (1/2 + r/6 + r^2/24 + r^3/120) in FP32 (|q| < 6e-5, so its FP32
+// rounding is below 1e-11 of the result).  ln2/32 is split into a 24-bit
+// head and a tail so that k * head is exact through two_prod.
+__device__ __forceinline__ ff ff_exp(ff t, const float2* tab)
+{
+    const float C_hi = 0x1.62e43p-6f, C_lo = -0x1.05c61p-34f;  // ln2/32
+    const float kf = rintf(t.hi * 46.166241308446828f);       // 32/ln2
+    const int k = (int)kf;
+    ff kc = two_prod(kf, C_hi);
+    kc.lo = fmaf(kf, C_lo, kc.lo);
+    const ff r = ff_sub(t, kc);
+    const float x = r.hi;
+    const float q = x * x * fmaf(x, fmaf(x, fmaf(x, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f), 0.5f);
+    ff s = two_sum(x, q);
+    s.lo += r.lo;
+    ff e = two_sum(1.0f, s.hi);
+    e.lo += s.lo;
+    e = fast_two_sum(e.hi, e.lo);
+    const float2 tv = tab[k & 31];
+    ff res = ff_mul(ff{tv.x, tv.y}, e);
+    // 2^(k div 32) as an exact power of two (|t| < 80 keeps it normal)
+    const float sc = __int_as_float(((k >> 5) + 127) << 23);
+    return ff{res.hi * sc, res.lo * sc};
+}
+
 // ---------------------------------------------------------------------------
 // Reductions in a fixed order (deterministic): xor-butterfly inside a warp,
 // then warp 0 over the per-warp values in warp order.

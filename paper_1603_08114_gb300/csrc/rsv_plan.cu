@@ -27,7 +27,7 @@ const int kJ_mixed[] = {4, 8, 16, 20};
 size_t smem_for(bool mixed, bool mass, int nt, int j)
 {
     const size_t W = (size_t)nt * (size_t)j;
-    return mixed ? 4 * W * sizeof(float) : (2 + (mass ? 1 : 0)) * W * sizeof(double);
+    return mixed ? 3 * W * sizeof(float) : (2 + (mass ? 1 : 0)) * W * sizeof(double);
 }
 
 bool valid_j(bool mixed, int j)
@@ -115,8 +115,12 @@ bool make_plan(const int64_t* off, int n, int n_md, bool mixed, bool mass, int n
                             continue;
                         }
                     }
-                    const int64_t waves = (b + num_sms - 1) / num_sms;
-                    double cost = (double)waves * (double)cap;
+                    // blocks resident per SM share it: an SM's work per wave
+                    // is bps windows
+                    int bps = blocks_per_sm(mixed, mass, js[ji], t, smem_for(mixed, mass, t, js[ji]));
+                    if (bps < 1) continue;
+                    const int64_t waves = (b + (int64_t)num_sms * bps - 1) / ((int64_t)num_sms * bps);
+                    double cost = (double)waves * (double)cap * bps;
                     cost *= 1.0 + 1e-3 * (double)(ntmax(mixed) - t) / ntmax(mixed);
                     if (cost < best) {
                         best = cost;

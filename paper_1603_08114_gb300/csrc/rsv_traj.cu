@@ -335,9 +335,12 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
 }
 
 // ---------------------------------------------------------------------------
-// Mixed path: FP32 leapfrog on a compensated (hi, lo) state; dH from
-// double-float per-site differences, accumulated in FP64 across threads.
-// Dynamic shared memory (slot-major): x0 hi/lo, p0 hi/lo [W each].
+// Mixed path: FP32 leapfrog on compensated (hi, lo) FP32 pairs for both the
+// position and the momentum (a random walk of their FP32 roundings over n_md
+// steps would otherwise dominate dH at 2^22 sites); dH from double-float
+// per-site differences, accumulated in FP64 across threads.
+// Dynamic shared memory (slot-major): x0 hi/lo and p0 [W each] (p0 enters
+// every trajectory with lo = 0: drawn in FP32, or rounded from p_in).
 // ---------------------------------------------------------------------------
 template <int J, bool MASS>
 __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
@@ -345,12 +348,13 @@ __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_wseg[NWMAX], s_wacc[NWMAX], s_flag;
     __shared__ double s_wpart[NWMAX], s_red[32], s_edge_d[4 * NWMAX], s_split;
+    __shared__ float2 s_exptab[32];
     const int NT = blockDim.x, W = NT * J, nw = NT >> 5, tid = threadIdx.x;
     float* s_edge = reinterpret_cast<float*>(s_edge_d);
+    ff_exp_table(s_exptab);
     float* s_x0h = reinterpret_cast<float*>(smem_raw);
     float* s_x0l = s_x0h + W;
     float* s_p0h = s_x0l + W;
-    float* s_p0l = s_p0h + W;
     const bool mass_on = MASS && (A.mass_on == nullptr || *A.mass_on != 0);
     const float dt = (float)A.dtau;
 
@@ -365,12 +369,12 @@ __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
         const float ief = (float)(1.0 / th.se2), iuf = (float)(1.0 / th.su2);
         const ff mu_ff = ff_from_double(th.mu);
         const ff ximu_ff = ff_from_double(th.xi + th.mu);
-        const float bshift = (float)(th.mu * 1.4426950408889634);
+        const float cmu = (float)(-th.mu * 1.4426950408889634);  // exponent of e^{-mu}
         const int64_t off = v.si.off, wlo = v.g.wlo;
         float2* hin = v.cur ? A.h1f : A.h0f;
         float2* hout = v.g.split ? (v.cur ? A.h0f : A.h1f) : hin;
 
-        float xh[J], xl[J], ph[J], pl[J], bm[J], kf[J];
+        float xh[J], xl[J], ph[J], pl[J], af[J], kf[J];
         float dtm[MASS ? J : 1];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -383,8 +387,7 @@ __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
             x = fast_two_sum(x.hi, x.lo);
             xh[j] = x.hi;
             xl[j] = x.lo;
-            const float b0 = act ? A.b0_f[s] : -INFINITY;
-            bm[j] = b0 - bshift;  // log2(y^2/2 e^{-mu})
+            af[j] = act ? A.a_f[s] : 0.0f;  // y^2/2
             const float2 lr = act ? A.lr_f[s] : make_float2(ximu_ff.hi, ximu_ff.lo);
             ff cp = two_sum(lr.x, -ximu_ff.hi);  // c' = lnRV - xi - mu
             cp.lo += lr.y - ximu_ff.lo;
@@ -396,9 +399,7 @@ __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
             for (int j = 0; j < J; ++j) {
                 const int i = base + j;
                 const double pv = i < v.n ? A.p_in[off + wlo + i] : 0.0;
-                const ff pf = ff_from_double(pv);
-                ph[j] = pf.hi;
-                pl[j] = pf.lo;
+                ph[j] = (float)pv;
             }
         } else {
 #pragma unroll
@@ -410,17 +411,15 @@ __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
                 box_muller_f(u01_23(r.w[2]), u01_23(r.w[3]), ph[4 * q + 2], ph[4 * q + 3]);
             }
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
+            for (int j = 0; j < J; ++j)
                 if (MASS) ph[j] = ph[j] / sqrtf(dtm[MASS ? j : 0]);
-                pl[j] = 0.0f;
-            }
         }
 #pragma unroll
         for (int j = 0; j < J; ++j) {
+            pl[j] = 0.0f;
             s_x0h[j * NT + tid] = xh[j];
             s_x0l[j * NT + tid] = xl[j];
             s_p0h[j * NT + tid] = ph[j];
-            s_p0l[j * NT + tid] = pl[j];
             if (MASS) dtm[MASS ? j : 0] *= dt;  // dtau / m_t
         }
         int par = 0;
@@ -451,7 +450,8 @@ __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
                 eprev = e[j];
                 float f = fmaf(iuf, xh[j], kf[j]);
                 f = fmaf(ief, ar, f);
-                f -= ex2_approx(fmaf(-kLog2e, xh[j], bm[j]));
+                // (y^2/2) e^{-h} = a 2^{-(x + mu) log2 e}: a small exponent argument
+                f = fmaf(-af[j], ex2_approx(fmaf(-kLog2e, xh[j], cmu)), f);
                 cupd(ph[j], pl[j], -dt, f);
             }
             const float hs = (k + 1 < A.n_md) ? 1.0f : 0.5f;
@@ -482,12 +482,10 @@ __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
                 const ff x0 = {s_x0h[j * NT + tid], s_x0l[j * NT + tid]};
                 const ff d = ff_sub(x1, x0);
                 ff_acc(accL, d);
-                ff q1 = two_prod(ph[j], ph[j]);
+                const float p0h = s_p0h[j * NT + tid];
+                ff q1 = two_prod(ph[j], ph[j]);  // p'^2 = (hi + lo)^2 to ~2^-48
                 q1.lo = fmaf(2.0f * ph[j], pl[j], q1.lo);
-                const float p0h = s_p0h[j * NT + tid], p0l = s_p0l[j * NT + tid];
-                ff q0 = two_prod(p0h, p0h);
-                q0.lo = fmaf(2.0f * p0h, p0l, q0.lo);
-                ff dk = ff_sub(q1, q0);
+                ff dk = ff_sub(q1, two_prod(p0h, p0h));
                 if (MASS) dk = ff_mul_f(dk, dtm[MASS ? j : 0] / dt);
                 ff_acc(accK, dk);
                 const float2 lr = A.lr_f[off + s];
@@ -513,9 +511,10 @@ __global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
                     const double a1 = ff_to_double(x1), a0 = ff_to_double(x0);
                     stat = 0.5 * (1.0 - th.phi * th.phi) / th.se2 * (a1 * a1 - a0 * a0);
                 }
-                const float h0f = x0.hi + mu_ff.hi;
-                const float E0 = A.a_f[off + s] * expf(-h0f);
-                ff_acc(accE, ff{E0 * expm1f(-d.hi), 0.0f});
+                // a (e^{-h'} - e^{-h}) with both exponentials in double-float
+                const ff E1 = ff_exp(ff_sub(ff{-mu_ff.hi, -mu_ff.lo}, x1), s_exptab);
+                const ff E0 = ff_exp(ff_sub(ff{-mu_ff.hi, -mu_ff.lo}, x0), s_exptab);
+                ff_acc(accE, ff_mul_f(ff_sub(E1, E0), af[j]));
             }
         }
         ff tot = ff_add(ff_add(ff_mul_f(accK, 0.5f), ff_mul_f(accL, 0.5f)), accE);
@@ -562,14 +561,12 @@ __global__ void k_commit_fp64(double* __restrict__ h, const double* __restrict__
 }
 
 __global__ void k_prep_mixed(const double* __restrict__ y, const double* __restrict__ lnrv,
-                             float* __restrict__ a_f, float* __restrict__ b0_f,
-                             float2* __restrict__ lr_f, int64_t T)
+                             float* __restrict__ a_f, float2* __restrict__ lr_f, int64_t T)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
         const double a = 0.5 * y[t] * y[t];
         a_f[t] = (float)a;
-        b0_f[t] = a > 0.0 ? (float)log2(a) : -INFINITY;
         const ff l = ff_from_double(lnrv[t]);
         lr_f[t] = make_float2(l.hi, l.lo);
     }
@@ -729,10 +726,10 @@ cudaError_t launch_commit_fp64(double* h, const double* hprop, double* p, const 
     k_commit_fp64<<<grid_for(T), 256, 0, st>>>(h, hprop, p, pprop, acc, T);
     return cudaGetLastError();
 }
-cudaError_t launch_prep_mixed(const double* y, const double* lnrv, float* a_f, float* b0_f,
-                              float2* lr_f, int64_t T, cudaStream_t st)
+cudaError_t launch_prep_mixed(const double* y, const double* lnrv, float* a_f, float2* lr_f,
+                              int64_t T, cudaStream_t st)
 {
-    k_prep_mixed<<<grid_for(T), 256, 0, st>>>(y, lnrv, a_f, b0_f, lr_f, T);
+    k_prep_mixed<<<grid_for(T), 256, 0, st>>>(y, lnrv, a_f, lr_f, T);
     return cudaGetLastError();
 }
 cudaError_t launch_h_to_ff(const double* h, float2* hf, int64_t T, cudaStream_t st)

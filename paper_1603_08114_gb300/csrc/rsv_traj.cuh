@@ -74,8 +74,7 @@ struct TrajArgs {
     double* p_out;       // optional p' (FP64, packed), must not alias p_in
     const double* y;     // FP64 path
     const double* lnrv;
-    const float* a_f;    // mixed path: y^2/2, log2(y^2/2), lnRV as (hi, lo)
-    const float* b0_f;
+    const float* a_f;    // mixed path: y^2/2 and lnRV as (hi, lo)
     const float2* lr_f;
     const float* minv;   // optional inverse mass (FP32, packed)
     const int* mass_on;  // optional flag; 0 = use m = 1
@@ -100,8 +99,8 @@ int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem);
 
 cudaError_t launch_commit_fp64(double* h, const double* hprop, double* p, const double* pprop,
                                const int* acc, int64_t T, cudaStream_t st);
-cudaError_t launch_prep_mixed(const double* y, const double* lnrv, float* a_f, float* b0_f,
-                              float2* lr_f, int64_t T, cudaStream_t st);
+cudaError_t launch_prep_mixed(const double* y, const double* lnrv, float* a_f, float2* lr_f,
+                              int64_t T, cudaStream_t st);
 cudaError_t launch_h_to_ff(const double* h, float2* hf, int64_t T, cudaStream_t st);
 // Write the current state of every series into h (packed FP64): FP64 path
 // from h1d where cur[s] = 1 (h0d is h itself); mixed path from the (hi, lo)
