@@ -228,6 +228,51 @@ rsv_status rsv_gibbs_theta(rsv_ctx* ctx, const double* h, const double* lnrv, in
                            double* theta, uint64_t seed, uint64_t series, uint64_t traj,
                            int mask, int32_t* phi_acc_out, void* stream);
 
+/* ---- learned diagonal mass ---------------------------------------------------
+ * The paper has no learned part; these calls build the per-site mass m_t used
+ * through `minv` above.  m_t = softplus(z_t) + 1e-3, z_t a 20 -> 32 -> 32 -> 1
+ * MLP (tanh hidden units) on 20 standardised features of site t computed from
+ * a FROZEN posterior mean hbar (never from the current h, so HMC stays exact),
+ * trained by Adam (b1 0.9, b2 0.999, eps 1e-8) on the mean squared error of
+ * log m_t against log(1 / Var(h_t)).  Matmuls in BF16 with FP32 accumulation
+ * (tensor cores), everything else FP32; FP32 master weights.
+ * Parameters: FP32 [RSV_MLP_NPARAM] = W1[32][20] b1[32] W2[32][32] b2[32]
+ * W3[32] b3 (row-major W[out][in]).
+ *
+ * rsv_welford_update: fold the n rows of x ([n][T] FP32 sampler snapshots)
+ *   into running per-site (count, mean, M2) (FP64 [T] each; count = rows
+ *   already folded in; mean/M2 are ignored when count = 0).
+ * rsv_welford_target: hbar_out (FP64 [T], may be NULL) = mean; target_out
+ *   (FP32 [T]) = log((count - 1) / M2).  count >= 2.
+ * rsv_mass_features: feat_out [T][20] FP32 = standardised features
+ *   (y^2, lnRV, hbar_{t-4..t+4} zero-padded, phi, mu, xi, s_eta^2, s_u^2,
+ *   edge flag, (1+phi^2)/s_eta^2, 1/s_u^2, (y^2/2) e^{-hbar}); stats_out
+ *   [40] FP32 = per-feature mean and 1/sd (0 for a constant feature).
+ * rsv_mlp_grad: loss (FP32 scalar, may be NULL) and gradient grad_out
+ *   [RSV_MLP_NPARAM] of the minibatch of Adam step `step`: batch sites drawn
+ *   as floor(hi32(w) T / 2^32), w = word k%4 of Philox block k/4 with counter
+ *   {k/4, step, 3, 0}, key {seed, 0}.  batch: multiple of 64.  T < 2^32.
+ * rsv_mlp_train: n_steps Adam steps (steps step0 .. step0+n_steps-1, Adam time
+ *   step+1) on params with state adam_m, adam_v (FP32 [RSV_MLP_NPARAM], zero
+ *   before step 0); loss_out [n_steps] or NULL.
+ * rsv_mlp_mass: minv_out [T] = 1/m_t and, if m_out != NULL, m_out [T] = m_t. */
+#define RSV_MLP_NPARAM 1761
+rsv_status rsv_welford_update(rsv_ctx* ctx, const float* x, int64_t n, int64_t T, int64_t count,
+                              double* mean, double* m2, void* stream);
+rsv_status rsv_welford_target(rsv_ctx* ctx, const double* mean, const double* m2, int64_t T,
+                              int64_t count, double* hbar_out, float* target_out, void* stream);
+rsv_status rsv_mass_features(rsv_ctx* ctx, const double* y, const double* lnrv, const double* hbar,
+                             int64_t T, rsv_theta theta, float* feat_out, float* stats_out,
+                             void* stream);
+rsv_status rsv_mlp_grad(rsv_ctx* ctx, const float* feat, const float* target, int64_t T,
+                        const float* params, uint64_t seed, uint64_t step, int batch,
+                        float* grad_out, float* loss_out, void* stream);
+rsv_status rsv_mlp_train(rsv_ctx* ctx, const float* feat, const float* target, int64_t T,
+                         float* params, float* adam_m, float* adam_v, int64_t step0, int n_steps,
+                         int batch, uint64_t seed, float lr, float* loss_out, void* stream);
+rsv_status rsv_mlp_mass(rsv_ctx* ctx, const float* feat, int64_t T, const float* params,
+                        float* minv_out, float* m_out, void* stream);
+
 /* ---- Philox momenta (exposed for tests of the generator) -----------------
  * p_t exactly as rsv_hmc_trajectory draws them for (seed, series, traj);
  * bits = 53 (FP64 path) or 23 (MIXED path). p_out [T] FP64. */

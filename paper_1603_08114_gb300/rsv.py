@@ -308,3 +308,92 @@ def rsv_hmc_batched(ctx: Context, plan: Plan, h, y, lnrv, theta_dev, dtau: float
         float(dtau), int(seed), int(traj0), int(n_traj), _ptr(log_u, torch.float64, n, "log_u"),
         _ptr(dH_out, torch.float64, n * n_traj, "dH_out"),
         _ptr(accept_out, torch.int32, n * n_traj, "accept_out"), _stream()))
+
+
+RSV_MLP_NPARAM = 1761
+
+
+def _mlp_lib():
+    L = lib()
+    if not getattr(L, "_mlp_ready", False):
+        L.rsv_welford_update.argtypes = [_P, _P, _I64, _I64, _I64, _P, _P, _P]
+        L.rsv_welford_target.argtypes = [_P, _P, _P, _I64, _I64, _P, _P, _P]
+        L.rsv_mass_features.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P, _P]
+        L.rsv_mlp_grad.argtypes = [_P, _P, _P, _I64, _P, _U64, _U64, _INT, _P, _P, _P]
+        L.rsv_mlp_train.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _I64, _INT, _INT, _U64,
+                                    ctypes.c_float, _P, _P]
+        L.rsv_mlp_mass.argtypes = [_P, _P, _I64, _P, _P, _P, _P]
+        for n in ("rsv_welford_update", "rsv_welford_target", "rsv_mass_features",
+                  "rsv_mlp_grad", "rsv_mlp_train", "rsv_mlp_mass"):
+            getattr(L, n).restype = _INT
+        L._mlp_ready = True
+    return L
+
+
+def rsv_welford_update(ctx: Context, x, count: int, mean, m2):
+    """Fold the rows of x ([n, T] FP32) into running (count, mean, M2) FP64."""
+    n, T = x.shape
+    _check(_mlp_lib().rsv_welford_update(ctx.handle, _ptr(x, torch.float32, n * T, "x"), n, T,
+                                         int(count), _ptr(mean, torch.float64, T, "mean"),
+                                         _ptr(m2, torch.float64, T, "m2"), _stream()))
+    return count + n
+
+
+def rsv_welford_target(ctx: Context, mean, m2, count: int, hbar_out=None, target_out=None):
+    T = mean.numel()
+    if target_out is None:
+        target_out = torch.empty(T, dtype=torch.float32, device=mean.device)
+    _check(_mlp_lib().rsv_welford_target(ctx.handle, _ptr(mean, torch.float64, T, "mean"),
+                                         _ptr(m2, torch.float64, T, "m2"), T, int(count),
+                                         _ptr(hbar_out, torch.float64, T, "hbar_out"),
+                                         _ptr(target_out, torch.float32, T, "target_out"),
+                                         _stream()))
+    return target_out
+
+
+def rsv_mass_features(ctx: Context, y, lnrv, hbar, th):
+    T = y.numel()
+    feat = torch.empty(T, 20, dtype=torch.float32, device=y.device)
+    stats = torch.empty(40, dtype=torch.float32, device=y.device)
+    _check(_mlp_lib().rsv_mass_features(ctx.handle, _ptr(y, torch.float64, T, "y"),
+                                        _ptr(lnrv, torch.float64, T, "lnrv"),
+                                        _ptr(hbar, torch.float64, T, "hbar"), T, theta(th),
+                                        _ptr(feat, torch.float32, 20 * T, "feat"),
+                                        _ptr(stats, torch.float32, 40, "stats"), _stream()))
+    return feat, stats
+
+
+def rsv_mlp_grad(ctx: Context, feat, target, params, seed: int, step: int, batch: int):
+    T = target.numel()
+    g = torch.empty(RSV_MLP_NPARAM, dtype=torch.float32, device=feat.device)
+    loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+    _check(_mlp_lib().rsv_mlp_grad(ctx.handle, _ptr(feat, torch.float32, 20 * T, "feat"),
+                                   _ptr(target, torch.float32, T, "target"), T,
+                                   _ptr(params, torch.float32, RSV_MLP_NPARAM, "params"),
+                                   int(seed), int(step), int(batch),
+                                   _ptr(g, torch.float32, RSV_MLP_NPARAM, "grad"),
+                                   _ptr(loss, torch.float32, 1, "loss"), _stream()))
+    return g, loss
+
+
+def rsv_mlp_train(ctx: Context, feat, target, params, adam_m, adam_v, step0: int, n_steps: int,
+                  batch: int, seed: int, lr: float = 1e-3, loss_out=None):
+    T = target.numel()
+    _check(_mlp_lib().rsv_mlp_train(ctx.handle, _ptr(feat, torch.float32, 20 * T, "feat"),
+                                    _ptr(target, torch.float32, T, "target"), T,
+                                    _ptr(params, torch.float32, RSV_MLP_NPARAM, "params"),
+                                    _ptr(adam_m, torch.float32, RSV_MLP_NPARAM, "adam_m"),
+                                    _ptr(adam_v, torch.float32, RSV_MLP_NPARAM, "adam_v"),
+                                    int(step0), int(n_steps), int(batch), int(seed), float(lr),
+                                    _ptr(loss_out, torch.float32, n_steps, "loss_out"),
+                                    _stream()))
+
+
+def rsv_mlp_mass(ctx: Context, feat, params, m_out=None):
+    T = feat.shape[0]
+    minv = torch.empty(T, dtype=torch.float32, device=feat.device)
+    _check(_mlp_lib().rsv_mlp_mass(ctx.handle, _ptr(feat, torch.float32, 20 * T, "feat"), T,
+                                   _ptr(params, torch.float32, RSV_MLP_NPARAM, "params"),
+                                   _ptr(minv, torch.float32, T, "minv"),
+                                   _ptr(m_out, torch.float32, T, "m_out"), _stream()))
+    return minv

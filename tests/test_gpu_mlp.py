@@ -1,0 +1,204 @@
+"""Learned mass on the GPU against the FP64 reference (oracle/mlp.py): moments,
+features, forward, gradients, Adam; and what the trained mass gains."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp, stats
+from paper_1603_08114_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TH = synth.THETA_STD
+
+
+@pytest.fixture(scope="module")
+def rsv():
+    from paper_1603_08114_gb300 import rsv as r
+    return r
+
+
+@pytest.fixture(scope="module")
+def ctx(rsv):
+    c = rsv.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def flat(P):
+    return np.concatenate([P["W1"].ravel(), P["b1"], P["W2"].ravel(), P["b2"], P["W3"],
+                           P["b3"]]).astype(np.float32)
+
+
+def unflat(v):
+    v = np.asarray(v, dtype=np.float64)
+    o = 0
+    P = {}
+    for k, shape in (("W1", (32, 20)), ("b1", (32,)), ("W2", (32, 32)), ("b2", (32,)),
+                     ("W3", (32,)), ("b3", (1,))):
+        n = int(np.prod(shape))
+        P[k] = v[o:o + n].reshape(shape)
+        o += n
+    return P
+
+
+def test_welford_matches_two_pass(rsv, ctx):
+    rng = np.random.default_rng(0)
+    n1, n2, T = 37, 50, 3001
+    X = (rng.standard_normal((n1 + n2, T)) * rng.uniform(0.1, 2, T) + rng.uniform(-1, 1, T))
+    X = X.astype(np.float32)
+    mean = torch.zeros(T, dtype=torch.float64, device="cuda")
+    m2 = torch.zeros_like(mean)
+    c = rsv.rsv_welford_update(ctx, dev(X[:n1], torch.float32), 0, mean, m2)
+    c = rsv.rsv_welford_update(ctx, dev(X[n1:], torch.float32), c, mean, m2)
+    m, v = mlp.welford_reference(X)
+    assert np.allclose(mean.cpu().numpy(), m, rtol=0, atol=1e-12)
+    assert np.allclose(m2.cpu().numpy() / (c - 1), v, rtol=1e-11)
+    hbar = torch.empty_like(mean)
+    tgt = rsv.rsv_welford_target(ctx, mean, m2, c, hbar_out=hbar).cpu().numpy()
+    assert np.allclose(tgt, np.log(1 / v), rtol=0, atol=1e-5)
+    assert np.array_equal(hbar.cpu().numpy(), mean.cpu().numpy())
+
+
+def test_features_match_reference(rsv, ctx):
+    T = 5003
+    s = synth.rsv_series(T, TH, seed=4)
+    hbar = s.h_true + 0.1 * np.cos(np.arange(T))
+    F, st = rsv.rsv_mass_features(ctx, dev(s.y), dev(s.lnrv), dev(hbar), TH)
+    ref, m, inv = mlp.standardize(mlp.features_raw(s.y, s.lnrv, hbar, s.theta))
+    assert np.max(np.abs(F.cpu().numpy() - ref)) < 2e-5
+    assert np.allclose(st.cpu().numpy()[:20], m, rtol=1e-6, atol=1e-6)
+
+
+@pytest.fixture(scope="module")
+def problem(rsv, ctx):
+    T = 20000
+    s = synth.rsv_series(T, TH, seed=5)
+    hbar = s.h_true
+    F, _ = rsv.rsv_mass_features(ctx, dev(s.y), dev(s.lnrv), dev(hbar), TH)
+    target = (-np.log(0.02 + 0.01 * np.cos(np.arange(T) * 0.01) ** 2)).astype(np.float32)
+    P = mlp.init_params(2)
+    return dict(T=T, F=F, Fnp=F.cpu().numpy().astype(np.float64), target=dev(target, torch.float32),
+                target_np=target.astype(np.float64), P=P)
+
+
+def test_forward_matches_reference(rsv, ctx, problem):
+    params = dev(flat(problem["P"]), torch.float32)
+    m_gpu = torch.empty(problem["T"], dtype=torch.float32, device="cuda")
+    minv = rsv.rsv_mlp_mass(ctx, problem["F"], params, m_out=m_gpu).cpu().numpy()
+    ref = mlp.forward(unflat(flat(problem["P"])), problem["Fnp"], bf=True)["m"]
+    rel = np.abs(m_gpu.cpu().numpy() - ref) / ref
+    assert np.median(rel) < 1e-5 and np.max(rel) < 5e-3
+    assert np.allclose(minv, 1 / m_gpu.cpu().numpy(), rtol=1e-6)
+
+
+@pytest.mark.parametrize("batch", [64, 4096])
+def test_gradient_matches_reference(rsv, ctx, problem, batch):
+    params = dev(flat(problem["P"]), torch.float32)
+    g, loss = rsv.rsv_mlp_grad(ctx, problem["F"], problem["target"], params, seed=11, step=3,
+                               batch=batch)
+    idx = mlp.batch_indices(11, 3, problem["T"], batch)
+    L, G = mlp.loss_and_grads(unflat(flat(problem["P"])), problem["Fnp"][idx],
+                              problem["target_np"][idx], bf=True)
+    assert abs(loss.item() - L) <= 1e-4 * L
+    gg = unflat(g.cpu().numpy())
+    for k in G:
+        scale = np.max(np.abs(G[k]))
+        err = np.max(np.abs(gg[k] - G[k])) / scale
+        assert err < 5e-3, (k, err)
+
+
+def test_adam_steps_match_reference(rsv, ctx, problem):
+    """Two GPU Adam steps against the reference Adam fed the GPU's own gradients."""
+    params = dev(flat(problem["P"]), torch.float32)
+    am = torch.zeros_like(params)
+    av = torch.zeros_like(params)
+    P = unflat(flat(problem["P"]))
+    opt = mlp.Adam(P, lr=1e-3)
+    for step in range(2):
+        g, _ = rsv.rsv_mlp_grad(ctx, problem["F"], problem["target"], params, seed=1, step=step,
+                                batch=512)
+        rsv.rsv_mlp_train(ctx, problem["F"], problem["target"], params, am, av, step, 1, 512,
+                          seed=1, lr=1e-3)
+        opt.step(P, unflat(g.cpu().numpy()))
+    got = params.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - flat(P).astype(np.float64))) < 2e-6
+
+
+def test_training_reduces_loss_like_reference(rsv, ctx, problem):
+    params = dev(flat(problem["P"]), torch.float32)
+    am = torch.zeros_like(params)
+    av = torch.zeros_like(params)
+    losses = torch.empty(300, dtype=torch.float32, device="cuda")
+    rsv.rsv_mlp_train(ctx, problem["F"], problem["target"], params, am, av, 0, 300, 1024,
+                      seed=4, lr=3e-3, loss_out=losses)
+    l = losses.cpu().numpy()
+    assert l[-20:].mean() < 0.25 * l[:5].mean()
+    P = unflat(flat(problem["P"]))
+    opt = mlp.Adam(P, lr=3e-3)
+    ref = []
+    for step in range(300):
+        idx = mlp.batch_indices(4, step, problem["T"], 1024)
+        L, G = mlp.loss_and_grads(P, problem["Fnp"][idx], problem["target_np"][idx], bf=True)
+        ref.append(L)
+        opt.step(P, G)
+    assert abs(l[-20:].mean() - np.mean(ref[-20:])) < 0.25 * np.mean(ref[-20:]) + 1e-3
+
+
+def test_learned_mass_gains_over_identity(rsv, ctx):
+    """The learned mass on a 2^14-site series: posterior means of h agree with
+    the identity-mass sampler within MCSE, and ESS per second of h (median
+    over sites) is higher."""
+    from paper_1603_08114_gb300 import learned
+    T = 1 << 14
+    s = synth.rsv_series(T, TH, seed=6)
+    y, lr = dev(s.y), dev(s.lnrv)
+    th = dev(TH)
+    h = dev(s.h_true)
+    mean, m2, cnt = learned.collect_moments(ctx, h, y, lr, th, 2000, 100, 0.005, seed=1)
+    tm = learned.train_mass(ctx, y, lr, TH, mean, m2, cnt, steps=1000, batch=4096, lr=3e-3)
+    losses = tm.losses.cpu().numpy()
+    assert losses[-50:].mean() < losses[:10].mean()
+    dt, n_md = learned.tune_step(ctx, h, y, lr, th, tm.minv, length=1.5)
+    n = 400
+    res = {}
+    for name in ("identity", "mass"):
+        hh = h.clone()
+        snaps = torch.empty(n, T, dtype=torch.float32, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        if name == "identity":
+            rsv.rsv_hmc_chain(ctx, hh, y, lr, th.clone(), 100, 0.005, n, prec="mixed", seed=3,
+                              snaps=snaps, thin=1)
+        else:
+            ms = learned.MassSampler(ctx, tm.minv, dt, n_md, 0.005, 100)
+            ms.run(hh, y, lr, th.clone(), n, seed=3, snaps=snaps, update_theta=False)
+            assert not ms.fell_back
+        b.record()
+        b.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        ess = rsv.rsv_ess(ctx, snaps).cpu().numpy()
+        x = snaps.cpu().numpy().astype(np.float64)
+        res[name] = dict(ess_s=np.median(ess) / sec, mean=x.mean(0),
+                         mcse=x.std(0) / np.sqrt(np.maximum(ess, 1)))
+    z = np.abs(res["mass"]["mean"] - res["identity"]["mean"]) / np.sqrt(
+        res["mass"]["mcse"] ** 2 + res["identity"]["mcse"] ** 2)
+    assert np.mean(z < 3.5) > 0.99
+    assert res["mass"]["ess_s"] > res["identity"]["ess_s"], res
+
+
+def test_fallback_to_identity_when_acceptance_collapses(rsv, ctx):
+    from paper_1603_08114_gb300 import learned
+    T = 4096
+    s = synth.rsv_series(T, TH, seed=7)
+    y, lr = dev(s.y), dev(s.lnrv)
+    h = dev(s.h_true)
+    bad = torch.full((T,), 400.0, dtype=torch.float32, device="cuda")  # step far too large
+    ms = learned.MassSampler(ctx, bad, 0.3, 5, 0.005, 100, window=20)
+    acc = torch.empty(60, dtype=torch.int32, device="cuda")
+    ms.run(h, y, lr, dev(TH), 60, seed=2, accept_out=acc, update_theta=False)
+    assert ms.fell_back
+    assert acc[-20:].float().mean().item() > 0.6
