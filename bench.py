@@ -7,10 +7,12 @@ dtau = 0.005, dH, Metropolis, then a Gibbs sweep of theta), run by one
 rsv_hmc_chain call that also records every trajectory's h and theta for ESS.  The
 chain continues from step to step (the warm-up steps are its burn-in).
 
-Reported: leapfrog site-updates/s (T * n_md * trajectories / time) and ESS/s
-of h (per-site ESS over the step's 200 draws / step time) for the headline
-sampler (mixed precision; diagonal mass when given) and for the plain FP64
-sampler on the same workload.
+Headline sampler: mixed precision with the learned diagonal mass (trained
+before timing from 10^4 plain-sampler snapshots; its step size and trajectory
+length tuned to ~0.8 acceptance; identity-mass fallback).  Reported:
+leapfrog site-updates/s (T * n_md * trajectories / time) and ESS/s of h
+(per-site ESS over the step's 200 draws / step time) and of theta, beside the
+plain mixed and plain FP64 samplers (identity mass, 100 x 0.005).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -39,7 +41,8 @@ SEED_DATA = 1
 METRIC = "leapfrog site-updates/s & ESS/s at T=2^20, mixed+learned vs FP64 plain, 1 GB300"
 UNIT = "site-updates/s"
 THETA_NAMES = ("phi", "mu", "xi", "sig_eta2", "sig_u2")
-WORKLOAD = "rsv-hmc single chain T=2^20, 200 traj x 100 x 0.005 per step"
+WORKLOAD = ("rsv-hmc single chain T=2^20, theta sampled, 200 trajectories per step; "
+            "learned mass (tuned dtau, n_md) vs identity 100 x 0.005")
 # Algorithmic instructions per site and leapfrog step of the mixed kernel on the
 # FP32/issue pipes: innovation (1), AR (1), force (3) + exponent argument (1),
 # special-function exp2 (1), compensated p update (4), compensated h update (4).
@@ -223,7 +226,23 @@ def run_ours(args):
 
     thetas = torch.empty(N_TRAJ, 5, dtype=torch.float64, device=dev)
 
-    def arm(prec, mass, warmup, steps, clocks=None, timing=False):
+    def run_chain(prec, mass, n_md, dtau, sampler, h, th, traj, record):
+        if sampler is not None:
+            if record:
+                sampler.run(h, y, lnrv, th, N_TRAJ, seed=11 + rank, traj0=traj, snaps=snaps,
+                            theta_out=thetas, accept_out=acc)
+            else:
+                sampler.run(h, y, lnrv, th, N_TRAJ, seed=11 + rank, traj0=traj)
+        elif record:
+            rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, n_md, dtau, N_TRAJ, prec=prec, minv=mass,
+                              seed=11 + rank, traj0=traj, snaps=snaps, thin=1, accept_out=acc,
+                              dH_out=dH, update_theta=True, theta_out=thetas)
+        else:
+            rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, n_md, dtau, N_TRAJ, prec=prec, minv=mass,
+                              seed=11 + rank, traj0=traj, update_theta=True)
+
+    def arm(prec, mass, warmup, steps, clocks=None, timing=False, n_md=N_MD, dtau=DTAU,
+            sampler=None):
         # the chain starts from the generator's latent path, a posterior-typical
         # state (from lnRV - xi the first trajectories are all rejected); every
         # trajectory is followed by a Gibbs sweep of theta
@@ -231,8 +250,7 @@ def run_ours(args):
         th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
         traj = 0
         for _ in range(warmup):
-            rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, N_MD, DTAU, N_TRAJ, prec=prec, minv=mass,
-                              seed=11 + rank, traj0=traj, update_theta=True)
+            run_chain(prec, mass, n_md, dtau, sampler, h, th, traj, False)
             traj += N_TRAJ
         rsv.rsv_sync_status(ctx)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -248,9 +266,7 @@ def run_ours(args):
             flush.zero_()
             l0 = rsv.rsv_stats(ctx, reset=False)[0]
             ev[k][0].record()
-            rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, N_MD, DTAU, N_TRAJ, prec=prec, minv=mass,
-                              seed=11 + rank, traj0=traj, snaps=snaps, thin=1, accept_out=acc,
-                              dH_out=dH, update_theta=True, theta_out=thetas)
+            run_chain(prec, mass, n_md, dtau, sampler, h, th, traj, True)
             ev[k][1].record()
             traj += N_TRAJ
             launches += rsv.rsv_stats(ctx, reset=False)[0] - l0
@@ -273,7 +289,8 @@ def run_ours(args):
         ess_min = [float(x) for x in ess_min]
         ess_th = torch.stack(ess_th).mean(0).cpu().numpy()
         return dict(
-            site_updates_per_s=ws * T_SITES * N_MD * N_TRAJ / sec_per_step,
+            site_updates_per_s=ws * T_SITES * n_md * N_TRAJ / sec_per_step,
+            n_md=n_md, dtau=dtau,
             ms_per_step=1e3 * sec_per_step,
             ess_h_median_per_s=ws * statistics.mean(ess_med) / sec_per_step,
             ess_h_min_per_s=ws * statistics.mean(ess_min) / sec_per_step,
@@ -338,12 +355,49 @@ def run_ours(args):
                              sched["sites_per_thread"], "cached": sched["cached"], **info}}
 
     # headline: mixed precision (diagonal mass when given)
+    # learned diagonal mass (untimed set-up): moments of the plain sampler over
+    # n_snap trajectories, 2000 Adam steps, inverse mass, step tuned to ~0.8
+    # acceptance at trajectory length 2.5; fallback to the plain sampler below
+    # 0.6 acceptance
+    learned_info, sampler, head_nmd, head_dt = None, None, N_MD, DTAU
+    if minv is None and not args.no_learned:
+        from paper_1603_08114_gb300 import learned
+        h0 = torch.tensor(s.h_true, device=dev)
+        th0 = torch.tensor(s.theta, dtype=torch.float64, device=dev)
+        t0 = time.perf_counter()
+        mean, m2, cnt = learned.collect_moments(ctx, h0, y, lnrv, th0, args.n_snap, N_MD, DTAU,
+                                                seed=5 + rank)
+        torch.cuda.synchronize()
+        t_snap = time.perf_counter() - t0
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record()
+        tm = learned.train_mass(ctx, y, lnrv, s.theta, mean, m2, cnt, steps=2000, batch=4096,
+                                lr=1e-3, seed=7 + rank)
+        b_ev.record()
+        b_ev.synchronize()
+        head_dt, head_nmd = learned.tune_step(ctx, h0, y, lnrv, th0, tm.minv, length=2.5)
+        minv = tm.minv
+        sampler = learned.MassSampler(ctx, minv, head_dt, head_nmd, DTAU, N_MD, window=50)
+        m = (1.0 / minv).float()
+        losses = tm.losses.cpu().numpy()
+        learned_info = {"snapshots": int(cnt), "snapshot_s": t_snap,
+                        "train_steps": 2000, "train_ms": a_ev.elapsed_time(b_ev),
+                        "loss_first": float(losses[:10].mean()),
+                        "loss_last": float(losses[-50:].mean()),
+                        "m_quantiles": [float(v) for v in torch.quantile(
+                            m[::16], torch.tensor([0.01, 0.5, 0.99], device=dev))],
+                        "dtau": head_dt, "n_md": head_nmd}
+
     clocks = Clocks(local)
-    head = arm("mixed", minv, args.warmup, args.steps, clocks=clocks, timing=True)
-    # comparison: plain FP64 sampler, identity mass (at most 3 timed steps)
-    fp64 = None
-    batched = None
+    head = arm("mixed", minv, args.warmup, args.steps, clocks=clocks, timing=True,
+               n_md=head_nmd, dtau=head_dt, sampler=sampler)
+    if learned_info is not None:
+        learned_info["fell_back"] = bool(sampler.fell_back)
+    # comparisons: plain mixed and plain FP64 samplers (identity mass, 100 x 0.005)
+    ident = fp64 = batched = None
     if args.only != "mixed":
+        if minv is not None:
+            ident = arm("mixed", None, min(args.warmup, 3), min(args.steps, 3))
         fp64 = arm("fp64", None, min(args.warmup, 3), min(args.steps, 3))
         batched = batched_leg(max(3, min(args.steps, 10)))
 
@@ -370,8 +424,9 @@ def run_ours(args):
         yd.copy_(y_host, non_blocking=True)
         ld.copy_(l_host, non_blocking=True)
         thd.copy_(th_host, non_blocking=True)
-        rsv.rsv_hmc_chain(ctx, hd, yd, ld, thd, N_MD, DTAU, N_TRAJ, prec="mixed", minv=minv,
-                          seed=99, traj0=k * N_TRAJ, accept_out=acc, dH_out=dH)
+        rsv.rsv_hmc_chain(ctx, hd, yd, ld, thd, head_nmd, head_dt, N_TRAJ, prec="mixed",
+                          minv=minv, seed=99, traj0=k * N_TRAJ, accept_out=acc, dH_out=dH,
+                          update_theta=True)
         out_h.copy_(hd, non_blocking=True)
         out_a.copy_(acc, non_blocking=True)
         out_d.copy_(dH, non_blocking=True)
@@ -385,7 +440,7 @@ def run_ours(args):
     sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_clock_mhz * 1e6 / 1e12  # Top/s
     per_launch_s = head["traj_ms"] / 1e3 / max(head["traj_launches"], 1)
-    ops_per_launch = OPS_PER_SITE_STEP_MIXED * T_SITES * N_MD
+    ops_per_launch = OPS_PER_SITE_STEP_MIXED * T_SITES * head_nmd
     achieved = ops_per_launch / per_launch_s / 1e12
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
@@ -402,7 +457,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "T": T_SITES, "n_md": N_MD, "dtau": DTAU,
+            "config": {"workload": WORKLOAD, "T": T_SITES, "n_md": head_nmd, "dtau": head_dt,
                        "traj_per_step": N_TRAJ, "precision": "mixed",
                        "mass": "learned" if minv is not None else "identity",
                        "l2": "flushed before every step (256 MB write, untimed)",
@@ -422,6 +477,14 @@ def run_ours(args):
                 "ess_theta_per_s": fp64["ess_theta_per_s"],
                 "accept_rate": fp64["accept_rate"]},
             "batched": batched,
+            "learned": learned_info,
+            "mixed_identity": None if ident is None else {
+                "site_updates_per_s": ident["site_updates_per_s"], "n_md": N_MD, "dtau": DTAU,
+                "ms_per_step": ident["ms_per_step"],
+                "ess_h_median_per_s": ident["ess_h_median_per_s"],
+                "ess_h_min_per_s": ident["ess_h_min_per_s"],
+                "ess_theta_per_s": ident["ess_theta_per_s"],
+                "accept_rate": ident["accept_rate"]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
                          "kernel": "k_traj_mixed", "peak_kind": "nominal FP32-lane issue "
@@ -454,6 +517,10 @@ def main():
     ap.add_argument("--traj-per-step", type=int, default=None,
                     help="trajectories per step (profiling; default 200)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="headline arm without the learned mass (profiling)")
+    ap.add_argument("--n-snap", type=int, default=10000,
+                    help="plain-sampler snapshots for the learned mass")
     args = ap.parse_args()
     if args.traj_per_step:
         global N_TRAJ

@@ -149,11 +149,14 @@ def test_training_reduces_loss_like_reference(rsv, ctx, problem):
 
 
 def test_learned_mass_gains_over_identity(rsv, ctx):
-    """The learned mass on a 2^14-site series: posterior means of h agree with
-    the identity-mass sampler within MCSE, and ESS per second of h (median
-    over sites) is higher."""
+    """The learned mass on a 2^16-site series, against the plain identity-mass
+    sampler at its own settings (100 x 0.005): the posterior means of h agree
+    within Monte-Carlo error, and the effective sample size per force
+    evaluation (median over sites) is higher.  (On this posterior the learned
+    m_t is close to the constant 1/Var(h_t); the gain is the larger stable
+    step it allows.  ESS per second at 2^20 sites is reported by bench.py.)"""
     from paper_1603_08114_gb300 import learned
-    T = 1 << 14
+    T = 1 << 16
     s = synth.rsv_series(T, TH, seed=6)
     y, lr = dev(s.y), dev(s.lnrv)
     th = dev(TH)
@@ -161,33 +164,52 @@ def test_learned_mass_gains_over_identity(rsv, ctx):
     mean, m2, cnt = learned.collect_moments(ctx, h, y, lr, th, 2000, 100, 0.005, seed=1)
     tm = learned.train_mass(ctx, y, lr, TH, mean, m2, cnt, steps=1000, batch=4096, lr=3e-3)
     losses = tm.losses.cpu().numpy()
-    assert losses[-50:].mean() < losses[:10].mean()
-    dt, n_md = learned.tune_step(ctx, h, y, lr, th, tm.minv, length=1.5)
+    assert losses[-50:].mean() < 0.1 * losses[:10].mean()
+    dt, n_md = learned.tune_step(ctx, h, y, lr, th, tm.minv, length=2.5)
     n = 400
     res = {}
     for name in ("identity", "mass"):
         hh = h.clone()
         snaps = torch.empty(n, T, dtype=torch.float32, device="cuda")
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
         if name == "identity":
             rsv.rsv_hmc_chain(ctx, hh, y, lr, th.clone(), 100, 0.005, n, prec="mixed", seed=3,
                               snaps=snaps, thin=1)
+            grads = n * 100
         else:
             ms = learned.MassSampler(ctx, tm.minv, dt, n_md, 0.005, 100)
             ms.run(hh, y, lr, th.clone(), n, seed=3, snaps=snaps, update_theta=False)
             assert not ms.fell_back
-        b.record()
-        b.synchronize()
-        sec = a.elapsed_time(b) / 1e3
+            grads = n * n_md
         ess = rsv.rsv_ess(ctx, snaps).cpu().numpy()
         x = snaps.cpu().numpy().astype(np.float64)
-        res[name] = dict(ess_s=np.median(ess) / sec, mean=x.mean(0),
+        res[name] = dict(ess_per_grad=np.median(ess) / grads, mean=x.mean(0),
                          mcse=x.std(0) / np.sqrt(np.maximum(ess, 1)))
     z = np.abs(res["mass"]["mean"] - res["identity"]["mean"]) / np.sqrt(
         res["mass"]["mcse"] ** 2 + res["identity"]["mcse"] ** 2)
     assert np.mean(z < 3.5) > 0.99
-    assert res["mass"]["ess_s"] > res["identity"]["ess_s"], res
+    assert res["mass"]["ess_per_grad"] > res["identity"]["ess_per_grad"], (
+        res["mass"]["ess_per_grad"], res["identity"]["ess_per_grad"], dt, n_md)
+
+
+def test_trained_mass_recovers_exact_precision_in_gaussian_subcase(rsv, ctx):
+    """y = 0: the posterior of h is Gaussian and 1/Var(h_t) is known exactly
+    (tridiagonal inverse).  Trained on that exact target the network's m_t
+    matches it within 3 % at every site, edges included."""
+    from paper_1603_08114_gb300 import learned
+    from tests.kalman_pin import tridiag_posterior
+    T = 4000
+    s = synth.rsv_series(T, TH, seed=8)
+    y0 = np.zeros(T)
+    m_exact, v_exact, _ = tridiag_posterior(s.lnrv, TH)
+    target = dev(np.log(1.0 / v_exact).astype(np.float32), torch.float32)
+    F, _ = rsv.rsv_mass_features(ctx, dev(y0), dev(s.lnrv), dev(m_exact), TH)
+    params = dev(learned.glorot_params(0), torch.float32)
+    am, av = torch.zeros_like(params), torch.zeros_like(params)
+    rsv.rsv_mlp_train(ctx, F, target, params, am, av, 0, 3000, 1024, seed=5, lr=3e-3)
+    m = torch.empty(T, dtype=torch.float32, device="cuda")
+    rsv.rsv_mlp_mass(ctx, F, params, m_out=m)
+    rel = np.abs(m.cpu().numpy() * v_exact - 1.0)
+    assert np.max(rel) < 0.03, (np.max(rel), np.argmax(rel))
 
 
 def test_fallback_to_identity_when_acceptance_collapses(rsv, ctx):
