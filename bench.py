@@ -252,7 +252,7 @@ def run_ours(args):
         for _ in range(warmup):
             run_chain(prec, mass, n_md, dtau, sampler, h, th, traj, False)
             traj += N_TRAJ
-        rsv.rsv_sync_status(ctx)
+        nonfinite = rsv.rsv_sync_status(ctx, allow_nonfinite=True) == rsv.RSV_ENONFINITE
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
         ess_med, ess_min, ess_th, acc_rate = [], [], [], []
@@ -262,6 +262,7 @@ def run_ours(args):
         if clocks:
             clocks.__enter__()
         launches = 0
+        md0 = sampler.md_steps if sampler is not None else 0
         for k in range(steps):
             flush.zero_()
             l0 = rsv.rsv_stats(ctx, reset=False)[0]
@@ -280,16 +281,22 @@ def run_ours(args):
             clocks.__exit__()
         rsv.rsv_timing(ctx, False)
         _, traj_launches, traj_ms = rsv.rsv_stats(ctx, reset=True)
-        rsv.rsv_sync_status(ctx)
+        # a non-finite dH is a rejected trajectory, not a failure; it is reported
+        nonfinite |= rsv.rsv_sync_status(ctx, allow_nonfinite=True) == rsv.RSV_ENONFINITE
         ms = [a.elapsed_time(b) for a, b in ev]
         total_s = sum(ms) / 1e3
         total_s = _barrier_max(ws, total_s)
         sec_per_step = total_s / steps
+        # leapfrog steps per site actually run per step (the mass sampler may
+        # have fallen back to the plain settings part-way)
+        md_per_step = ((sampler.md_steps - md0) / steps if sampler is not None
+                       else n_md * N_TRAJ)
         ess_med = [float(x) for x in ess_med]
         ess_min = [float(x) for x in ess_min]
         ess_th = torch.stack(ess_th).mean(0).cpu().numpy()
         return dict(
-            site_updates_per_s=ws * T_SITES * n_md * N_TRAJ / sec_per_step,
+            site_updates_per_s=ws * T_SITES * md_per_step / sec_per_step,
+            md_steps_per_step=md_per_step,
             n_md=n_md, dtau=dtau,
             ms_per_step=1e3 * sec_per_step,
             ess_h_median_per_s=ws * statistics.mean(ess_med) / sec_per_step,
@@ -299,7 +306,8 @@ def run_ours(args):
                              for n, v in zip(THETA_NAMES, ess_th)},
             ess_theta_per_step={n: float(v) for n, v in zip(THETA_NAMES, ess_th)},
             accept_rate=float(statistics.mean(float(a) for a in acc_rate)),
-            launches=launches, traj_launches=traj_launches, traj_ms=traj_ms)
+            launches=launches, traj_launches=traj_launches, traj_ms=traj_ms,
+            nonfinite_dH_seen=bool(nonfinite))
 
     def batched_leg(steps):
         """The 4096-series workload: one persistent launch per trajectory of all
@@ -377,7 +385,7 @@ def run_ours(args):
         b_ev.synchronize()
         head_dt, head_nmd = learned.tune_step(ctx, h0, y, lnrv, th0, tm.minv, length=2.5)
         minv = tm.minv
-        sampler = learned.MassSampler(ctx, minv, head_dt, head_nmd, DTAU, N_MD, window=50)
+        sampler = learned.MassSampler(ctx, minv, head_dt, head_nmd, DTAU, N_MD, window=100)
         m = (1.0 / minv).float()
         losses = tm.losses.cpu().numpy()
         learned_info = {"snapshots": int(cnt), "snapshot_s": t_snap,
@@ -393,6 +401,7 @@ def run_ours(args):
                n_md=head_nmd, dtau=head_dt, sampler=sampler)
     if learned_info is not None:
         learned_info["fell_back"] = bool(sampler.fell_back)
+        learned_info["window_accept"] = [round(r, 3) for r in sampler.history]
     # comparisons: plain mixed and plain FP64 samplers (identity mass, 100 x 0.005)
     ident = fp64 = batched = None
     if args.only != "mixed":

@@ -230,7 +230,7 @@ rsv_status rsv_gibbs_theta(rsv_ctx* ctx, const double* h, const double* lnrv, in
 
 /* ---- learned diagonal mass ---------------------------------------------------
  * The paper has no learned part; these calls build the per-site mass m_t used
- * through `minv` above.  m_t = softplus(z_t) + 1e-3, z_t a 20 -> 32 -> 32 -> 1
+ * through `minv` above.  m_t = s (softplus(z_t) + 1e-3), z_t a 20 -> 32 -> 32 -> 1
  * MLP (tanh hidden units) on 20 standardised features of site t computed from
  * a FROZEN posterior mean hbar (never from the current h, so HMC stays exact),
  * trained by Adam (b1 0.9, b2 0.999, eps 1e-8) on the mean squared error of
@@ -243,11 +243,20 @@ rsv_status rsv_gibbs_theta(rsv_ctx* ctx, const double* h, const double* lnrv, in
  *   into running per-site (count, mean, M2) (FP64 [T] each; count = rows
  *   already folded in; mean/M2 are ignored when count = 0).
  * rsv_welford_target: hbar_out (FP64 [T], may be NULL) = mean; target_out
- *   (FP32 [T]) = log((count - 1) / M2).  count >= 2.
+ *   (FP32 [T]) = log((count - 1) / M2); log_scale_out (FP32 scalar, may be
+ *   NULL) = the mean over the sites of target_out, the log of the output
+ *   scale s.  count >= 2.
+ * log_scale (in rsv_mlp_grad, _train, _mass): device FP32 scalar log s, fixed
+ *   during training; NULL means s = 1.  s sets the scale of the network's
+ *   output so that softplus works near unit slope (without it the tanh
+ *   layers saturate to reach precisions of O(30) and the fit goes flat).
  * rsv_mass_features: feat_out [T][20] FP32 = standardised features
  *   (y^2, lnRV, hbar_{t-4..t+4} zero-padded, phi, mu, xi, s_eta^2, s_u^2,
- *   edge flag, (1+phi^2)/s_eta^2, 1/s_u^2, (y^2/2) e^{-hbar}); stats_out
- *   [40] FP32 = per-feature mean and 1/sd (0 for a constant feature).
+ *   edge proximity 2^-d with d the distance to the nearer end,
+ *   (1+phi^2)/s_eta^2, 1/s_u^2, (y^2/2) e^{-hbar}), each standardised over
+ *   the sites except the edge proximity, clipped to [-8, 8]; stats_out [40]
+ *   FP32 = per-feature mean and 1/sd (0 for a constant feature; 0 and 1 for
+ *   the edge proximity).
  * rsv_mlp_grad: loss (FP32 scalar, may be NULL) and gradient grad_out
  *   [RSV_MLP_NPARAM] of the minibatch of Adam step `step`: batch sites drawn
  *   as floor(hi32(w) T / 2^32), w = word k%4 of Philox block k/4 with counter
@@ -255,23 +264,31 @@ rsv_status rsv_gibbs_theta(rsv_ctx* ctx, const double* h, const double* lnrv, in
  * rsv_mlp_train: n_steps Adam steps (steps step0 .. step0+n_steps-1, Adam time
  *   step+1) on params with state adam_m, adam_v (FP32 [RSV_MLP_NPARAM], zero
  *   before step 0); loss_out [n_steps] or NULL.
- * rsv_mlp_mass: minv_out [T] = 1/m_t and, if m_out != NULL, m_out [T] = m_t. */
+ * rsv_mlp_mass: minv_out [T] = 1/m_t and, if m_out != NULL, m_out [T] = m_t,
+ *   with m_t clamped to [1/s_u^2, A_t/s_eta^2 + 1/s_u^2 + (y_t^2/2) e^{-hbar_t}]
+ *   (the observation precision, a floor of the posterior precision, and the
+ *   diagonal of the Hessian of S at hbar; A_t = 1 + phi^2 inside, 1 at the
+ *   ends, 1 - phi^2 if T = 1), so the mass cannot destabilise the leapfrog.
+ *   y, hbar: [T] FP64 (the data and frozen mean the features came from). */
 #define RSV_MLP_NPARAM 1761
 rsv_status rsv_welford_update(rsv_ctx* ctx, const float* x, int64_t n, int64_t T, int64_t count,
                               double* mean, double* m2, void* stream);
 rsv_status rsv_welford_target(rsv_ctx* ctx, const double* mean, const double* m2, int64_t T,
-                              int64_t count, double* hbar_out, float* target_out, void* stream);
+                              int64_t count, double* hbar_out, float* target_out,
+                              float* log_scale_out, void* stream);
 rsv_status rsv_mass_features(rsv_ctx* ctx, const double* y, const double* lnrv, const double* hbar,
                              int64_t T, rsv_theta theta, float* feat_out, float* stats_out,
                              void* stream);
 rsv_status rsv_mlp_grad(rsv_ctx* ctx, const float* feat, const float* target, int64_t T,
-                        const float* params, uint64_t seed, uint64_t step, int batch,
-                        float* grad_out, float* loss_out, void* stream);
+                        const float* params, const float* log_scale, uint64_t seed, uint64_t step,
+                        int batch, float* grad_out, float* loss_out, void* stream);
 rsv_status rsv_mlp_train(rsv_ctx* ctx, const float* feat, const float* target, int64_t T,
-                         float* params, float* adam_m, float* adam_v, int64_t step0, int n_steps,
-                         int batch, uint64_t seed, float lr, float* loss_out, void* stream);
+                         float* params, const float* log_scale, float* adam_m, float* adam_v,
+                         int64_t step0, int n_steps, int batch, uint64_t seed, float lr,
+                         float* loss_out, void* stream);
 rsv_status rsv_mlp_mass(rsv_ctx* ctx, const float* feat, int64_t T, const float* params,
-                        float* minv_out, float* m_out, void* stream);
+                        const float* log_scale, const double* y, const double* hbar,
+                        rsv_theta theta, float* minv_out, float* m_out, void* stream);
 
 /* ---- Philox momenta (exposed for tests of the generator) -----------------
  * p_t exactly as rsv_hmc_trajectory draws them for (seed, series, traj);

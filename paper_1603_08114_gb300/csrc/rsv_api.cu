@@ -166,6 +166,8 @@ rsv_status rsv_reserve(rsv_ctx* c, int64_t max_T, int64_t max_series)
     if ((st = c->ser_cnt.ensure(n * sizeof(unsigned))) != RSV_OK) return st;
     if ((st = c->ser_dh.ensure(n * sizeof(double))) != RSV_OK) return st;
     if ((st = c->ser_acc.ensure(n * sizeof(int))) != RSV_OK) return st;
+    if ((st = c->theta_f.ensure(n * sizeof(MixedTheta))) != RSV_OK) return st;
+    if ((st = c->gibbs.ensure((size_t)gibbs_grid(max_T) * 8 * sizeof(double))) != RSV_OK) return st;
     return RSV_OK;
 }
 

@@ -88,6 +88,7 @@ rsv_status ensure_plan_ws(rsv_ctx* c, const Plan& p, bool mixed, bool need_p)
         if ((st = c->fbuf1.ensure(N * 8)) != RSV_OK) return st;
         if ((st = c->a_f.ensure(N * 4)) != RSV_OK) return st;
         if ((st = c->lr_f.ensure(N * 8)) != RSV_OK) return st;
+        if ((st = c->theta_f.ensure(n * sizeof(MixedTheta))) != RSV_OK) return st;
     } else {
         if ((st = c->dbuf0.ensure(N * 8)) != RSV_OK) return st;
     }
@@ -168,6 +169,10 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
         a.lr_f = c->lr_f.as<float2>();
         a.h0f = c->fbuf0.as<float2>();
         a.h1f = c->fbuf1.as<float2>();
+        a.theta_f = c->theta_f.as<MixedTheta>();
+        if ((e = counted(c, launch_theta_prep, o.theta, o.th_inline, (int)n,
+                         c->theta_f.as<MixedTheta>(), s)) != cudaSuccess)
+            return cuda_fail(e, "theta prep kernel");
         if ((e = counted(c, launch_prep_mixed, o.y, o.lnrv, c->a_f.as<float>(),
                          c->lr_f.as<float2>(), P.total, s)) != cudaSuccess)
             return cuda_fail(e, "prep kernel");
@@ -202,6 +207,7 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
             g.mask = 31;
             g.partials = c->gibbs.as<double>();
             g.counter = reinterpret_cast<unsigned*>(ints + kGibbsCounter);
+            g.theta_f = mixed ? c->theta_f.as<MixedTheta>() : nullptr;
             if ((e = counted(c, launch_gibbs, g, mixed, s)) != cudaSuccess)
                 return cuda_fail(e, "theta kernel");
         } else if (o.theta_out) {

@@ -22,14 +22,16 @@ rsv_status rsv_welford_update(rsv_ctx* c, const float* x, int64_t n, int64_t T, 
 }
 
 rsv_status rsv_welford_target(rsv_ctx* c, const double* mean, const double* m2, int64_t T,
-                              int64_t count, double* hbar_out, float* target_out, void* stream)
+                              int64_t count, double* hbar_out, float* target_out,
+                              float* log_scale_out, void* stream)
 {
     rsv_status st = ctx_begin(c, stream);
     if (st != RSV_OK) return st;
     if (!mean || !m2 || !target_out) return fail(RSV_EINVAL, "null argument");
     if (T < 1 || count < 2) return fail(RSV_EINVAL, "need T >= 1 and count >= 2");
     cudaError_t e = counted(c, launch_welford_target, mean, m2, T, count, hbar_out, target_out,
-                            (cudaStream_t)stream);
+                            log_scale_out, (cudaStream_t)stream);
+    if (log_scale_out) ++c->launches;
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "welford target kernel");
 }
 
@@ -65,8 +67,8 @@ static rsv_status mlp_common(rsv_ctx* c, const float* feat, const float* target,
 }
 
 rsv_status rsv_mlp_grad(rsv_ctx* c, const float* feat, const float* target, int64_t T,
-                        const float* params, uint64_t seed, uint64_t step, int batch,
-                        float* grad_out, float* loss_out, void* stream)
+                        const float* params, const float* log_scale, uint64_t seed, uint64_t step,
+                        int batch, float* grad_out, float* loss_out, void* stream)
 {
     rsv_status st = ctx_begin(c, stream);
     if (st != RSV_OK) return st;
@@ -76,13 +78,14 @@ rsv_status rsv_mlp_grad(rsv_ctx* c, const float* feat, const float* target, int6
                             (float*)nullptr, (float*)nullptr, grad_out, c->extra.as<float>(),
                             reinterpret_cast<unsigned*>(c->ints.as<int>() + kBatchCounter),
                             seed, step, (int64_t)1, 0.f, 0.f, 0.f, 0.f, batch, 0, loss_out,
-                            (cudaStream_t)stream);
+                            log_scale, (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "mlp gradient kernel");
 }
 
 rsv_status rsv_mlp_train(rsv_ctx* c, const float* feat, const float* target, int64_t T,
-                         float* params, float* adam_m, float* adam_v, int64_t step0, int n_steps,
-                         int batch, uint64_t seed, float lr, float* loss_out, void* stream)
+                         float* params, const float* log_scale, float* adam_m, float* adam_v,
+                         int64_t step0, int n_steps, int batch, uint64_t seed, float lr,
+                         float* loss_out, void* stream)
 {
     rsv_status st = ctx_begin(c, stream);
     if (st != RSV_OK) return st;
@@ -96,21 +99,24 @@ rsv_status rsv_mlp_train(rsv_ctx* c, const float* feat, const float* target, int
                                 (float*)nullptr, c->extra.as<float>(),
                                 reinterpret_cast<unsigned*>(c->ints.as<int>() + kBatchCounter),
                                 seed, step, (int64_t)(step + 1), lr, 0.9f, 0.999f, 1e-8f, batch, 1,
-                                loss_out ? loss_out + i : (float*)nullptr, (cudaStream_t)stream);
+                                loss_out ? loss_out + i : (float*)nullptr, log_scale,
+                                (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "mlp step kernel");
     }
     return RSV_OK;
 }
 
 rsv_status rsv_mlp_mass(rsv_ctx* c, const float* feat, int64_t T, const float* params,
-                        float* minv_out, float* m_out, void* stream)
+                        const float* log_scale, const double* y, const double* hbar,
+                        rsv_theta theta, float* minv_out, float* m_out, void* stream)
 {
     rsv_status st = ctx_begin(c, stream);
     if (st != RSV_OK) return st;
-    if (!feat || !params || !minv_out) return fail(RSV_EINVAL, "null argument");
+    if (!feat || !params || !y || !hbar || !minv_out) return fail(RSV_EINVAL, "null argument");
     if (T < 1) return fail(RSV_EINVAL, "T must be >= 1");
-    cudaError_t e = counted(c, launch_mlp_mass, feat, T, params, minv_out, m_out,
-                            (cudaStream_t)stream);
+    if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
+    cudaError_t e = counted(c, launch_mlp_mass, feat, T, params, y, hbar, to_dev(theta), log_scale,
+                            minv_out, m_out, (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "mlp mass kernel");
 }
 

@@ -58,10 +58,14 @@ __device__ __forceinline__ double u01_53(uint64_t w)
 {
     return ((double)(w >> 11) + 0.5) * 0x1.0p-53;
 }
-// Uniform in (0,1) exactly representable in FP32: (k + 1/2) 2^-23, top 23 bits.
+// Uniform in (0,1) exactly representable in FP32: (k + 1/2) 2^-23, k = top 23
+// bits.  Built from the bits (1 + k 2^-23 has k as its mantissa) so that no
+// integer-to-float conversion runs: conversions share this GPU's slow FP64
+// pipe.  Every step is exact: (1 + k 2^-23) - 1 = k 2^-23, + 2^-24 fits 24 bits.
 __device__ __forceinline__ float u01_23(uint64_t w)
 {
-    return ((float)(uint32_t)(w >> 41) + 0.5f) * 0x1.0p-23f;
+    const uint32_t k = (uint32_t)(w >> 41);
+    return (__uint_as_float(0x3F800000u | k) - 1.0f) + 0x1.0p-24f;
 }
 
 // Box-Muller: r = sqrt(-2 ln u1); (r cos 2 pi u2, r sin 2 pi u2).
@@ -155,11 +159,15 @@ __device__ __forceinline__ void ff_exp_table(float2* tab)
 // q = r^2 (1/2 + r/6 + r^2/24 + r^3/120) in FP32 (|q| < 6e-5, so its FP32
 // rounding is below 1e-11 of the result).  ln2/32 is split into a 24-bit
 // head and a tail so that k * head is exact through two_prod.
+// k = rint(32 t / ln2) is taken by adding 1.5 2^23 (the FP32 sum then holds k
+// in its low mantissa bits, rounded to nearest even, for |k| < 2^22), which
+// needs no float-to-integer conversion.
 __device__ __forceinline__ ff ff_exp(ff t, const float2* tab)
 {
     const float C_hi = 0x1.62e43p-6f, C_lo = -0x1.05c61p-34f;  // ln2/32
-    const float kf = rintf(t.hi * 46.166241308446828f);       // 32/ln2
-    const int k = (int)kf;
+    const float kr = __fmaf_rn(t.hi, 46.166241308446828f, 0x1.8p23f);  // 32/ln2
+    const int k = __float_as_int(kr) - 0x4B400000;
+    const float kf = kr - 0x1.8p23f;
     ff kc = two_prod(kf, C_hi);
     kc.lo = fmaf(kf, C_lo, kc.lo);
     const ff r = ff_sub(t, kc);

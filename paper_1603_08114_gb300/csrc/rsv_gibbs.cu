@@ -187,38 +187,71 @@ __device__ void gibbs_draws(const double (&S)[NSTAT], double x0, int64_t T, doub
     if (phi_acc) *phi_acc = acc;
 }
 
-// Statistics pass + last-block draws.  `cur` selects the state buffer.
+// Block sum of NSTAT double-float values in a fixed order (butterfly in each
+// warp, then warp 0 over the warps in order); the result is valid in thread 0.
+__device__ __forceinline__ void block_sum_ff(ff (&s)[NSTAT], float2 (*red)[NSTAT])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NSTAT; ++i) {
+        const ff w = warp_sum_ff(s[i]);
+        if (lane == 0) red[warp][i] = make_float2(w.hi, w.lo);
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NSTAT; ++i) {
+            const float2 v = lane < nw ? red[lane][i] : make_float2(0.f, 0.f);
+            s[i] = warp_sum_ff(ff{v.x, v.y});
+        }
+    }
+    __syncthreads();
+}
+
+// Statistics pass + last-block draws.  `cur` selects the state buffer.  The
+// mixed path keeps every per-site and cross-block sum in double-float (FP32
+// arithmetic; the FP64 pipe of this GPU is slow) and converts the totals to
+// FP64 once for the scalar draws.
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_gibbs(GibbsArgs A)
 {
     __shared__ double red[32];
+    __shared__ float2 redf[32][NSTAT];
+    __shared__ ff s_c[3];
     __shared__ int s_last;
     const int* curp = A.cur;
     const int cur = curp ? *(volatile int*)curp : 0;
-    const ThetaD th = load_theta(A.theta);
-    double S[NSTAT];
-    for (int i = 0; i < NSTAT; ++i) S[i] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (MIXED) {
+        if (threadIdx.x == 0) {
+            const ThetaD th = load_theta(A.theta);
+            s_c[0] = ff_from_double(th.xi);
+            s_c[1] = ff_from_double(th.mu);
+            s_c[2] = ff_from_double(th.phi);
+        }
+        __syncthreads();
+        const ff xi = s_c[0], mu = s_c[1], phi = s_c[2];
         const float2* h = cur ? A.h1f : A.h0f;
-        const ff xi = ff_from_double(th.xi), mu = ff_from_double(th.mu),
-                 phi = ff_from_double(th.phi);
         ff s[NSTAT];
         for (int i = 0; i < NSTAT; ++i) s[i] = ff{0.f, 0.f};
         for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
             site_stats_f(h, A.lr_f, t, A.T, xi, mu, phi, s);
-        for (int i = 0; i < NSTAT; ++i) {
-            const ff w = warp_sum_ff(s[i]);
-            S[i] = (threadIdx.x & 31) == 0 ? ff_to_double(w) : 0.0;
-        }
+        block_sum_ff(s, redf);
+        float2* pf = reinterpret_cast<float2*>(A.partials);
+        if (threadIdx.x == 0)
+            for (int i = 0; i < NSTAT; ++i)
+                pf[(int64_t)blockIdx.x * NSTAT + i] = make_float2(s[i].hi, s[i].lo);
     } else {
+        const ThetaD th = load_theta(A.theta);
+        double S[NSTAT];
+        for (int i = 0; i < NSTAT; ++i) S[i] = 0.0;
         const double* h = cur ? A.h1d : A.h0d;
         for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
             site_stats_d(h, A.lnrv, t, A.T, th, S);
-    }
-    for (int i = 0; i < NSTAT; ++i) {
-        const double b = block_sum(S[i], red);
-        if (threadIdx.x == 0) A.partials[(int64_t)blockIdx.x * NSTAT + i] = b;
+        for (int i = 0; i < NSTAT; ++i) {
+            const double b = block_sum(S[i], red);
+            if (threadIdx.x == 0) A.partials[(int64_t)blockIdx.x * NSTAT + i] = b;
+        }
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -228,14 +261,29 @@ __global__ void __launch_bounds__(256) k_gibbs(GibbsArgs A)
     if (!s_last) return;
     __threadfence();
     double tot[NSTAT];
-    for (int i = 0; i < NSTAT; ++i) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-            v += __ldcg(A.partials + (int64_t)b * NSTAT + i);
-        tot[i] = block_sum(v, red);
+    if (MIXED) {
+        const float2* pf = reinterpret_cast<const float2*>(A.partials);
+        ff s[NSTAT];
+        for (int i = 0; i < NSTAT; ++i) {
+            s[i] = ff{0.f, 0.f};
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+                const float2 v = __ldcg(pf + (int64_t)b * NSTAT + i);
+                s[i] = ff_add(s[i], ff{v.x, v.y});
+            }
+        }
+        block_sum_ff(s, redf);
+        for (int i = 0; i < NSTAT; ++i) tot[i] = ff_to_double(s[i]);
+    } else {
+        for (int i = 0; i < NSTAT; ++i) {
+            double v = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+                v += __ldcg(A.partials + (int64_t)b * NSTAT + i);
+            tot[i] = block_sum(v, red);
+        }
     }
     if (threadIdx.x == 0) {
         *A.counter = 0u;
+        const ThetaD th = load_theta(A.theta);
         double x0;
         if (MIXED) {
             const float2 v = (cur ? A.h1f : A.h0f)[0];
@@ -245,16 +293,19 @@ __global__ void __launch_bounds__(256) k_gibbs(GibbsArgs A)
         }
         gibbs_draws(tot, x0, A.T, A.theta, A.theta_out, A.seed, A.series, A.traj, A.mask,
                     A.phi_acc);
+        if (A.theta_f) *A.theta_f = mixed_theta(load_theta(A.theta));
         __threadfence();
     }
 }
 
 }  // namespace
 
+// About 4 sites per thread, up to 8 blocks of 256 per SM: the statistics pass
+// is bound by load latency, so it wants many threads in flight.
 int gibbs_grid(int64_t T)
 {
-    int64_t g = (T + 255) / 256;
-    if (g > 152) g = 152;
+    int64_t g = (T + 1023) / 1024;
+    if (g > 152 * 8) g = 152 * 8;
     if (g < 1) g = 1;
     return (int)g;
 }

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "rsv_traj.cuh"
+
 namespace rsv {
 
 struct GibbsArgs {
@@ -22,6 +24,7 @@ struct GibbsArgs {
     double* partials;    // [grid * 8]
     unsigned* counter;
     int* phi_acc;        // optional
+    MixedTheta* theta_f; // optional: refreshed from the new theta (mixed path)
 };
 
 int gibbs_grid(int64_t T);

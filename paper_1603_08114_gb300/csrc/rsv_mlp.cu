@@ -2,11 +2,14 @@
 // MLP trained by Adam, and mass inference.
 //
 // Not part of the paper (which has no learned component): the task adds a
-// per-site mass m_t = softplus(z_t) + eps for HMC, where z_t is a 20 -> 32 ->
+// per-site mass m_t = s (softplus(z_t) + eps) for HMC, where z_t is a 20 -> 32 ->
 // 32 -> 1 MLP (tanh hidden units) on 20 features of site t computed from a
 // FROZEN state (the posterior mean hbar of a plain sampler), so the mass never
 // depends on the current h and HMC stays exact.  The network is trained on
-// log(1 / Var(h_t)) with the squared error in log space.
+// log(1 / Var(h_t)) with the squared error in log space.  s is a fixed output
+// scale, the geometric mean of the target precisions: it keeps softplus near
+// its unit-slope range so that the tanh layers need not saturate to reach
+// precisions of O(30).
 //
 // Tensor cores: the matmuls (layer 1 and 2 forward, the back-propagation
 // through layer 2 and the weight gradients of layers 1 and 2) run as
@@ -32,6 +35,8 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NF, OFF_W2 = OFF_B1 + NH,
               NPARAM = OFF_B3 + 1;
 static_assert(NPARAM == 1761, "parameter layout");
 constexpr float EPS_M = 1e-3f;
+constexpr int EDGE = 16;       // the edge proximity 2^-d is not standardised
+constexpr float CLIP = 8.0f;   // standardised features are clipped to [-8, 8]
 constexpr int SITES_PER_BLOCK = 64;  // 4 warps x 16 sites
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -219,6 +224,7 @@ struct StepArgs {
     int batch;
     int update;
     float* loss_out;      // optional
+    const float* log_scale;  // optional device scalar: log s
 };
 
 __global__ void __launch_bounds__(128) k_mlp_step(const StepArgs A)
@@ -250,8 +256,9 @@ __global__ void __launch_bounds__(128) k_mlp_step(const StepArgs A)
         yg = A.target[sg];
         yg8 = A.target[sg8];
     }
+    const float ls = A.log_scale ? *A.log_scale : 0.f;
     const float mg = softplus_f(z3g) + EPS_M, mg8 = softplus_f(z3g8) + EPS_M;
-    const float lg = logf(mg) - yg, lg8 = logf(mg8) - yg8;
+    const float lg = logf(mg) + ls - yg, lg8 = logf(mg8) + ls - yg8;
     const float invB = 1.f / (float)A.batch;
     const float g3g = 2.f * lg * invB * sigmoid_f(z3g) / mg;
     const float g3g8 = 2.f * lg8 * invB * sigmoid_f(z3g8) / mg8;
@@ -439,14 +446,31 @@ __global__ void __launch_bounds__(128) k_mlp_step(const StepArgs A)
     if (tid == 0) *A.counter = 0u;
 }
 
-// m_t for every site; writes 1/m_t (and m_t if m_out).
+// Clamp interval of the mass at site t: [1/s_u^2, diagonal of the Hessian of
+// S at hbar] = [1/s_u^2, A_t/s_eta^2 + 1/s_u^2 + (y_t^2/2) e^{-hbar_t}], A_t =
+// 1 + phi^2 inside, 1 at the ends, 1 - phi^2 when T = 1.
+__device__ __forceinline__ float clamp_mass(float m, int64_t t, int64_t T, const double* y,
+                                            const double* hbar, const ThetaD& th)
+{
+    const double A = T == 1 ? 1.0 - th.phi * th.phi
+                   : (t == 0 || t == T - 1) ? 1.0 : 1.0 + th.phi * th.phi;
+    const double lo = 1.0 / th.su2;
+    const double hi = A / th.se2 + lo + 0.5 * y[t] * y[t] * exp(-hbar[t]);
+    return fminf(fmaxf(m, (float)lo), (float)hi);
+}
+
+// m_t for every site, clamped; writes 1/m_t (and m_t if m_out).
 __global__ void __launch_bounds__(128) k_mlp_mass(const float* __restrict__ feat, int64_t T,
                                                   const float* __restrict__ P,
+                                                  const double* __restrict__ y,
+                                                  const double* __restrict__ hbar, ThetaD th,
+                                                  const float* __restrict__ log_scale,
                                                   float* __restrict__ minv, float* __restrict__ m_out)
 {
     __shared__ SParams sp;
     __shared__ float fs[4][16][KP];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const float scale = log_scale ? expf(*log_scale) : 1.f;
     load_params(P, sp);
     __syncthreads();
     for (int64_t base = ((int64_t)blockIdx.x * 4 + warp) * 16; base < T;
@@ -461,7 +485,9 @@ __global__ void __launch_bounds__(128) k_mlp_mass(const float* __restrict__ feat
         mlp_forward(sp, &fs[warp][0][0], a1, a2, z3g, z3g8);
         if (t == 0) {
             const int64_t s0 = base + g, s1 = base + g + 8;
-            const float m0 = softplus_f(z3g) + EPS_M, m1 = softplus_f(z3g8) + EPS_M;
+            float m0 = scale * (softplus_f(z3g) + EPS_M), m1 = scale * (softplus_f(z3g8) + EPS_M);
+            if (s0 < T) m0 = clamp_mass(m0, s0, T, y, hbar, th);
+            if (s1 < T) m1 = clamp_mass(m1, s1, T, y, hbar, th);
             if (s0 < T) {
                 minv[s0] = 1.f / m0;
                 if (m_out) m_out[s0] = m0;
@@ -506,6 +532,17 @@ __global__ void k_welford_target(const double* __restrict__ mean, const double* 
     }
 }
 
+// log s = mean over the sites of the target (one block, FP64, fixed order).
+__global__ void __launch_bounds__(1024) k_target_mean(const float* __restrict__ target, int64_t T,
+                                                      float* __restrict__ out)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t t = threadIdx.x; t < T; t += blockDim.x) s += (double)target[t];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *out = (float)(s / (double)T);
+}
+
 // Raw features of each site (see the header of oracle/mlp.py for the list).
 __global__ void k_feat_raw(const double* __restrict__ y, const double* __restrict__ lnrv,
                            const double* __restrict__ hbar, int64_t T, ThetaD th,
@@ -526,7 +563,8 @@ __global__ void k_feat_raw(const double* __restrict__ y, const double* __restric
         f[13] = (float)th.xi;
         f[14] = (float)th.se2;
         f[15] = (float)th.su2;
-        f[16] = (t == 0 || t == T - 1) ? 1.f : 0.f;
+        const int64_t d = t < T - 1 - t ? t : T - 1 - t;   // distance to the nearer end
+        f[16] = ldexpf(1.f, -(int)(d < 64 ? d : 64));
         f[17] = (float)((1.0 + th.phi * th.phi) / th.se2);
         f[18] = (float)(1.0 / th.su2);
         f[19] = (float)(0.5 * yt * yt * exp(-hbar[t]));
@@ -573,11 +611,12 @@ __global__ void __launch_bounds__(256) k_feat_stats(const float* __restrict__ F,
         for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + (int64_t)b * NF + f);
         if (pass == 0) {
             acc[f] = s / (double)T;
-            stats[f] = (float)acc[f];
+            stats[f] = f == EDGE ? 0.f : (float)acc[f];
         } else {
             const double sd = sqrt(s / (double)T);
             const double m = acc[f];
-            stats[NF + f] = (sd > 1e-12 * fmax(1.0, fabs(m))) ? (float)(1.0 / sd) : 0.f;
+            stats[NF + f] = f == EDGE ? 1.f
+                          : (sd > 1e-12 * fmax(1.0, fabs(m))) ? (float)(1.0 / sd) : 0.f;
         }
     }
     if (threadIdx.x == 0) *counter = 0u;
@@ -588,7 +627,7 @@ __global__ void k_feat_norm(float* __restrict__ F, int64_t T, const float* __res
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T * NF;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int f = (int)(i % NF);
-        F[i] = (F[i] - stats[f]) * stats[NF + f];
+        F[i] = fminf(fmaxf((F[i] - stats[f]) * stats[NF + f], -CLIP), CLIP);
     }
 }
 
@@ -608,21 +647,23 @@ cudaError_t launch_mlp_step(const float* feat, const float* target, int64_t T, f
                             float* adam_m, float* adam_v, float* grad_out, float* partials,
                             unsigned* counter, uint64_t seed, uint64_t step, int64_t adam_t,
                             float lr, float b1, float b2, float eps, int batch, int update,
-                            float* loss_out, cudaStream_t st)
+                            float* loss_out, const float* log_scale, cudaStream_t st)
 {
     StepArgs a{feat,  target,  T,    params, adam_m, adam_v, grad_out, partials, counter,
                seed,  step,    adam_t, lr,   b1,     b2,     eps,      batch,    update,
-               loss_out};
+               loss_out, log_scale};
     k_mlp_step<<<batch / SITES_PER_BLOCK, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_mass(const float* feat, int64_t T, const float* params, float* minv,
+cudaError_t launch_mlp_mass(const float* feat, int64_t T, const float* params, const double* y,
+                            const double* hbar, ThetaD th, const float* log_scale, float* minv,
                             float* m_out, cudaStream_t st)
 {
     int64_t g = (T + 63) / 64;
     if (g > 152 * 16) g = 152 * 16;
-    k_mlp_mass<<<(int)(g < 1 ? 1 : g), 128, 0, st>>>(feat, T, params, minv, m_out);
+    k_mlp_mass<<<(int)(g < 1 ? 1 : g), 128, 0, st>>>(feat, T, params, y, hbar, th, log_scale,
+                                                      minv, m_out);
     return cudaGetLastError();
 }
 
@@ -634,9 +675,10 @@ cudaError_t launch_welford(const float* x, int64_t n, int64_t T, int64_t count, 
 }
 
 cudaError_t launch_welford_target(const double* mean, const double* m2, int64_t T, int64_t count,
-                                  double* hbar, float* target, cudaStream_t st)
+                                  double* hbar, float* target, float* log_scale, cudaStream_t st)
 {
     k_welford_target<<<grid1(T), 256, 0, st>>>(mean, m2, T, count, hbar, target);
+    if (log_scale) k_target_mean<<<1, 1024, 0, st>>>(target, T, log_scale);
     return cudaGetLastError();
 }
 

@@ -22,23 +22,28 @@ namespace rsv {
 namespace {
 
 const int kJ_fp64[] = {4, 8, 16, 28};
-const int kJ_mixed[] = {4, 8, 16, 20};
+const int kJ_mixed[] = {4, 8, 12, 16, 20};
+const int kNJ_fp64 = 4, kNJ_mixed = 5;
 
+// mixed: (a, k) float2 + x0 (hi, lo) + p0 per site (+ dtau/m with a mass);
+// FP64: a', kc (+ 1/m) per site
 size_t smem_for(bool mixed, bool mass, int nt, int j)
 {
     const size_t W = (size_t)nt * (size_t)j;
-    return mixed ? 3 * W * sizeof(float) : (2 + (mass ? 1 : 0)) * W * sizeof(double);
+    return mixed ? (5 + (mass ? 1 : 0)) * W * sizeof(float)
+                 : (2 + (mass ? 1 : 0)) * W * sizeof(double);
 }
 
 bool valid_j(bool mixed, int j)
 {
     const int* js = mixed ? kJ_mixed : kJ_fp64;
-    for (int i = 0; i < 4; ++i)
+    const int n = mixed ? kNJ_mixed : kNJ_fp64;
+    for (int i = 0; i < n; ++i)
         if (js[i] == j) return true;
     return false;
 }
 
-int ntmax(bool mixed) { return mixed ? 384 : 256; }
+int ntmax(bool mixed, int j) { return mixed ? mixed_max_threads(j) : 256; }
 
 }  // namespace
 
@@ -74,7 +79,7 @@ bool make_plan(const int64_t* off, int n, int n_md, bool mixed, bool mass, int n
     int nt = 0, j = 0;
     int64_t tile = 0;
     if (sched_nt > 0) {
-        if (!valid_j(mixed, sched_j) || sched_nt % 32 || sched_nt > ntmax(mixed) ||
+        if (!valid_j(mixed, sched_j) || sched_nt % 32 || sched_nt > ntmax(mixed, sched_j) ||
             sched_tile < 1 || sched_tile + 2 * K + 3 > (int64_t)sched_nt * sched_j ||
             smem_for(mixed, mass, sched_nt, sched_j) > smem_cap) {
             *why = "the fixed schedule does not fit this call";
@@ -89,8 +94,10 @@ bool make_plan(const int64_t* off, int n, int n_md, bool mixed, bool mass, int n
         const int64_t T = Tmax;
         double best = 1e300;
         const int* js = mixed ? kJ_mixed : kJ_fp64;
-        for (int ji = 0; ji < 4; ++ji) {
-            for (int t = 32; t <= ntmax(mixed); t += 32) {
+        const int nj = mixed ? kNJ_mixed : kNJ_fp64;
+        for (int ji = 0; ji < nj; ++ji) {
+            const int tmax = ntmax(mixed, js[ji]);
+            for (int t = 32; t <= tmax; t += 32) {
                 const int64_t cap = (int64_t)t * js[ji];
                 if (smem_for(mixed, mass, t, js[ji]) > smem_cap) continue;
                 const int64_t tl = cap - 2 * K - 3;
@@ -121,7 +128,7 @@ bool make_plan(const int64_t* off, int n, int n_md, bool mixed, bool mass, int n
                     if (bps < 1) continue;
                     const int64_t waves = (b + (int64_t)num_sms * bps - 1) / ((int64_t)num_sms * bps);
                     double cost = (double)waves * (double)cap * bps;
-                    cost *= 1.0 + 1e-3 * (double)(ntmax(mixed) - t) / ntmax(mixed);
+                    cost *= 1.0 + 1e-3 * (double)(tmax - t) / tmax;
                     if (cost < best) {
                         best = cost;
                         nt = t;
@@ -138,7 +145,7 @@ bool make_plan(const int64_t* off, int n, int n_md, bool mixed, bool mass, int n
     } else {
         // many series: the largest window, so that most series are whole
         j = mixed ? 20 : 28;
-        nt = ntmax(mixed);
+        nt = ntmax(mixed, j);
         tile = (int64_t)nt * j - 2 * K - 3;
         if (tile < 1) {
             *why = "n_md too large for an on-chip window";

@@ -33,7 +33,7 @@ namespace rsv {
 
 namespace {
 
-constexpr int NWMAX = 16;  // warps per block at most
+constexpr int NWMAX = 32;  // warps per block at most
 constexpr float kLog2e = 1.4426950408889634f;
 
 // 2^x on the special-function unit (ex2.approx.ftz.f32, relative error about
@@ -48,18 +48,23 @@ __device__ __forceinline__ float ex2_approx(float x)
 // left_last = last value of thread tid-1, right_first = first value of thread
 // tid+1 (garbage across a segment boundary; callers never use it there).
 // `edge` is one of two alternating buffers of 2*nw values.
+// Branch-free: every lane loads the two neighbouring warps' edge values (one
+// address per warp and load, a broadcast) and selects.
 template <typename V>
 __device__ __forceinline__ void exchange(V first, V last, V& left_last, V& right_first, V* edge,
                                          int nw)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    left_last = __shfl_up_sync(0xffffffffu, last, 1);
-    right_first = __shfl_down_sync(0xffffffffu, first, 1);
+    const V up = __shfl_up_sync(0xffffffffu, last, 1);
+    const V dn = __shfl_down_sync(0xffffffffu, first, 1);
     if (lane == 0) edge[2 * warp] = first;
     if (lane == 31) edge[2 * warp + 1] = last;
     __syncthreads();
-    if (lane == 0) left_last = warp > 0 ? edge[2 * (warp - 1) + 1] : first;
-    if (lane == 31) right_first = warp + 1 < nw ? edge[2 * (warp + 1)] : last;
+    const bool has_l = warp > 0, has_r = warp + 1 < nw;
+    const V el = edge[2 * (has_l ? warp - 1 : warp) + 1];
+    const V er = edge[2 * (has_r ? warp + 1 : warp)];
+    left_last = lane == 0 ? (has_l ? el : first) : up;
+    right_first = lane == 31 ? (has_r ? er : last) : dn;
 }
 
 // Innovations e_j = x_{j+1} - phi x_j of one thread's run (xR = first x of the
@@ -87,23 +92,12 @@ struct View {
     int cur;     // buffer holding the series' current state
 };
 
-__device__ __forceinline__ void load_bin(const TrajArgs& A, int b, int* s_wseg, int* s_wacc,
-                                         View& v)
+// This warp's view, from the segment ids already placed in s_wseg (no
+// barrier; a kernel may call it again after its step loop instead of keeping
+// the view in registers through the loop).
+__device__ __forceinline__ void view_of(const TrajArgs& A, const int* s_wseg, View& v)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    __syncthreads();
-    if (tid < NWMAX) {
-        s_wseg[tid] = -1;
-        s_wacc[tid] = 0;
-    }
-    __syncthreads();
-    const int f0 = A.bin_first[b], f1 = A.bin_first[b + 1];
-    for (int i = f0 + tid; i < f1; i += blockDim.x) {
-        const int id = A.bin_seg[i];
-        const Seg g = A.segs[id];
-        for (int w = g.warp0; w < g.warp0 + g.nwarp && w < NWMAX; ++w) s_wseg[w] = id;
-    }
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v.sid = s_wseg[warp];
     if (v.sid >= 0) {
         v.g = A.segs[v.sid];
@@ -121,6 +115,26 @@ __device__ __forceinline__ void load_bin(const TrajArgs& A, int b, int* s_wseg, 
     v.n = (int)(v.g.whi - v.g.wlo);
     v.base = ts;  // the caller scales it by J
     v.first = (ts == 0);
+}
+
+__device__ __forceinline__ void load_bin(const TrajArgs& A, int b, int* s_wseg, int* s_wacc,
+                                         View& v)
+{
+    const int tid = threadIdx.x;
+    __syncthreads();
+    if (tid < NWMAX) {
+        s_wseg[tid] = -1;
+        s_wacc[tid] = 0;
+    }
+    __syncthreads();
+    const int f0 = A.bin_first[b], f1 = A.bin_first[b + 1];
+    for (int i = f0 + tid; i < f1; i += blockDim.x) {
+        const int id = A.bin_seg[i];
+        const Seg g = A.segs[id];
+        for (int w = g.warp0; w < g.warp0 + g.nwarp && w < NWMAX; ++w) s_wseg[w] = id;
+    }
+    __syncthreads();
+    view_of(A, s_wseg, v);
 }
 
 // Metropolis decision of one series (Sec. 3): accept iff ln u < -dH; a
@@ -191,6 +205,47 @@ __device__ __forceinline__ void segment_decisions(const TrajArgs& A, const View&
         for (int w = v.g.warp0; w < v.g.warp0 + v.g.nwarp; ++w) d += s_wpart[w];
         if (!v.g.split) s_wacc[v.g.warp0] = decide(A, v.g.series, d, v.cur, false);
         else *split_part = d;
+    }
+}
+
+// The same two steps with the partial dH as double-float (mixed path): sums
+// in FP32 arithmetic by one warp, one FP64 conversion for the decision.
+__device__ void finish_split_ff(const TrajArgs& A, const View& v, float2 part, int* s_flag)
+{
+    float2* pf = reinterpret_cast<float2*>(A.partials);
+    if (threadIdx.x == 0) {
+        pf[v.sid] = part;
+        __threadfence();
+        const unsigned prev = atomicAdd(A.ser_cnt + v.g.series, 1u);
+        *s_flag = (prev == (unsigned)v.si.nseg - 1u);
+    }
+    __syncthreads();
+    const int last = *s_flag;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    ff s = {0.f, 0.f};
+    for (int i = threadIdx.x; i < v.si.nseg; i += 32) {
+        const float2 w = __ldcg(pf + v.si.seg0 + i);
+        s = ff_add(s, ff{w.x, w.y});
+    }
+    s = warp_sum_ff(s);
+    if (threadIdx.x == 0) {
+        A.ser_cnt[v.g.series] = 0u;
+        decide(A, v.g.series, ff_to_double(s), v.cur, true);
+        __threadfence();
+    }
+}
+__device__ __forceinline__ void segment_decisions_ff(const TrajArgs& A, const View& v,
+                                                     const float2* s_wpf, int* s_wacc,
+                                                     float2* split_part)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (v.sid >= 0 && warp == v.g.warp0 && lane == 0) {
+        ff d = {0.f, 0.f};
+        for (int w = v.g.warp0; w < v.g.warp0 + v.g.nwarp; ++w) d = ff_add(d, ff{s_wpf[w].x, s_wpf[w].y});
+        if (!v.g.split) s_wacc[v.g.warp0] = decide(A, v.g.series, ff_to_double(d), v.cur, false);
+        else *split_part = make_float2(d.hi, d.lo);
     }
 }
 
@@ -339,209 +394,367 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
 // position and the momentum (a random walk of their FP32 roundings over n_md
 // steps would otherwise dominate dH at 2^22 sites); dH from double-float
 // per-site differences, accumulated in FP64 across threads.
-// Dynamic shared memory (slot-major): x0 hi/lo and p0 [W each] (p0 enters
-// every trajectory with lo = 0: drawn in FP32, or rounded from p_in).
+//
+// Registers hold only the evolving state (x and p as (hi, lo), 4 J floats), so
+// that a block can run up to 32 warps; the per-site constants of the force sit
+// in shared memory and are read as float4.  Dynamic shared memory (slot-major:
+// slot j of thread tid at [j][tid]):
+//   s_ak  float4 [J/2][NT]  (a_j, k_j, a_{j+1}, k_{j+1}): a = y^2/2,
+//                           k = 1/2 - c'/s_u^2
+//   s_dm  float4 [J/4][NT]  dtau/m of 4 consecutive slots (with a mass only)
+//   s_x0h, s_x0l, s_p0h  float [J][NT]  start of the trajectory, for dH (p0
+//                           enters with lo = 0: drawn in FP32 or rounded from p_in)
 // ---------------------------------------------------------------------------
-template <int J, bool MASS>
-__global__ void __launch_bounds__(384, 1) k_traj_mixed(const TrajArgs A)
+template <int J>
+constexpr int mixed_ntmax()
 {
+    return J <= 4 ? 1024 : J <= 8 ? 768 : J <= 12 ? 640 : J <= 16 ? 512 : 384;
+}
+
+// 2^(j/32), j = 0..31, as double-float pairs, written by the theta prep kernel
+// (FP64, 32 lanes, once per call) and copied to shared memory by each block.
+__device__ float2 g_exptab[32];
+
+// Per-block constants of the leapfrog of one segment.
+struct MixedConst {
+    float phi, st0, iu, ie, cmu, dt;
+    int la;        // slot of the series' last site in this thread (or out of [0, J))
+    bool first;    // this thread holds the series' first site in slot 0
+};
+
+// Packed FP32 pair arithmetic (FFMA2/FADD2: two independent FP32 lanes per
+// instruction, each rounded exactly as its scalar counterpart).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as a + (-1) b: one rounding, the same value as a scalar subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
+
+// Compensated v += c*u on (hi, lo) pairs (lo carries what hi lost), lane by lane.
+__device__ __forceinline__ void cupd2(float2& hi, float2& lo, float2 c, float2 u)
+{
+    const float2 y = fma2(c, u, lo);
+    const float2 t = add2(hi, y);
+    lo = sub2(y, sub2(t, hi));
+    hi = t;
+}
+
+// n_md leapfrog steps (eqs. (6)-(8)) with the two half steps of consecutive
+// steps merged: x += dt/2 p;  n_md times { p -= dt F(x); x += (dt, or dt/2 at
+// the end) p }.  A thread's run of J sites is held as P = J/2 pairs
+// (j, j + P): the two halves of the run advance side by side in the two lanes
+// of packed FP32 instructions.  Site by site the innovation
+// e_j = x_{j+1} - phi x_j, the force and both updates are fused: a site's
+// update feeds no later site's force of the same step (that needs only e_j,
+// already taken).  The seams: the lower half's last site takes x_P from before
+// the step, and the upper half's chain starts from e_{P-1}.
+// EDGE: some thread of the warp ends a series before its last slot; e = 0 at
+// that slot (the series' end condition e_{T-1} = 0) by a select.
+// s_ak: float4 [P][NT] = (-a_p, -a_{p+P}, k_p, k_{p+P}); s_dm: float2 [P][NT].
+template <int J, bool MASS, bool EDGE>
+__device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J / 2],
+                                            float2 (&PH)[J / 2], float2 (&PL)[J / 2],
+                                            const float4* __restrict__ s_ak,
+                                            const float2* __restrict__ s_dm, float* s_edge,
+                                            int& par, int nw, int n_md, const MixedConst& c)
+{
+    constexpr int P = J / 2;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    const float2 nphi = f2(-c.phi, -c.phi), iu = f2(c.iu, c.iu), ie = f2(c.ie, c.ie);
+    const float2 nl2e = f2(-kLog2e, -kLog2e), cmu = f2(c.cmu, c.cmu);
+    const float2 ndt = f2(-c.dt, -c.dt);
+    for (int k = 0; k < n_md; ++k) {
+        float xL, xR;
+        exchange(X[0].x, X[P - 1].y, xL, xR, s_edge + par * 2 * nw, nw);
+        par ^= 1;
+        const float xP = X[0].y;  // x_P before the step
+        float2 eprev;
+        eprev.x = c.first ? c.st0 * X[0].x : fmaf(-c.phi, xL, X[0].x);
+        eprev.y = fmaf(-c.phi, X[P - 1].x, xP);  // e_{P-1}
+        const float hs = (k + 1 < n_md) ? 1.0f : 0.5f;
+        const float2 cx = f2(hs * c.dt, hs * c.dt);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const float4 ak = s_ak[q * NT + tid];
+            const float2 nxt = (q + 1 < P) ? X[q + 1] : f2(xP, xR);
+            float2 e = fma2(nphi, X[q], nxt);
+            if (EDGE) {
+                if (q == c.la) e.x = 0.0f;
+                if (q + P == c.la) e.y = 0.0f;
+            } else if (q == P - 1) {
+                if (c.la == J - 1) e.y = 0.0f;
+            }
+            const float2 ar = fma2(nphi, e, eprev);
+            eprev = e;
+            float2 f = fma2(iu, X[q], f2(ak.z, ak.w));
+            f = fma2(ie, ar, f);
+            // (y^2/2) e^{-h} = a 2^{-(x + mu) log2 e}: a small exponent argument
+            const float2 t = fma2(nl2e, X[q], cmu);
+            f = fma2(f2(ak.x, ak.y), f2(ex2_approx(t.x), ex2_approx(t.y)), f);
+            cupd2(PH[q], PL[q], ndt, f);
+            float2 cq = cx;
+            if (MASS) {
+                const float2 dm = s_dm[q * NT + tid];
+                cq = f2(hs * dm.x, hs * dm.y);
+            }
+            cupd2(X[q], XL[q], cq, PH[q]);
+        }
+    }
+}
+
+// Energy of one owned site in double-float, without the site-independent
+// constants (mu/2 per site, which cancel in dH): the parts accumulate
+// separately and are weighted once per thread,
+//   H = K/2 + L/2 + R/(2 s_u^2) + Q/(2 s_eta^2) + E  (+ the stationary term),
+//   K = p^2/m, L = x, R = (x - c')^2, Q = (x_{t+1} - phi x_t)^2 (t < T-1),
+//   E = (y^2/2) e^{-h}.
+struct HParts {
+    ff K, L, R, Q, E;
+};
+__device__ __forceinline__ void hparts_zero(HParts& a)
+{
+    a.K = a.L = a.R = a.Q = a.E = ff{0.f, 0.f};
+}
+__device__ __forceinline__ ff hparts_total(const HParts& a, const MixedTheta& mt)
+{
+    ff tot = ff_add(ff_mul_f(a.K, 0.5f), ff_mul_f(a.L, 0.5f));
+    tot = ff_add(tot, a.E);
+    tot = ff_add(tot, ff_mul(a.R, mt.hu));
+    return ff_add(tot, ff_mul(a.Q, mt.he));
+}
+// x: h - mu; p: momentum (hi, lo); mi: 1/m; cp: c' = lnRV - xi - mu; a: y^2/2;
+// xn: next site's x (used only if has_next).
+__device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, float mi, ff cp, float a,
+                                            ff xn, bool has_next, const MixedTheta& mt,
+                                            const float2* tab)
+{
+    ff p2 = two_prod(p.hi, p.hi);  // (hi + lo)^2 to ~2^-48
+    p2.lo = fmaf(2.0f * p.hi, p.lo, p2.lo);
+    ff_acc(acc.K, mi == 1.0f ? p2 : ff_mul_f(p2, mi));
+    ff_acc(acc.L, x);
+    const ff r = ff_sub(x, cp);
+    ff_acc(acc.R, ff_mul(r, r));
+    if (has_next) {
+        const ff e = ff_sub(xn, ff_mul(mt.phi_ff, x));
+        ff_acc(acc.Q, ff_mul(e, e));
+    }
+    const ff E = ff_exp(ff_sub(ff{-mt.mu.hi, -mt.mu.lo}, x), tab);
+    ff_acc(acc.E, ff_mul_f(E, a));
+}
+
+// Per-site work outside the leapfrog (loading, momenta, both ends of dH)
+// runs in rolled loops over the thread's slots through shared memory: fully
+// unrolled over J slots it is thousands of instructions per thread, more than
+// the instruction caches hold.
+template <int J, bool MASS>
+__global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajArgs A)
+{
+    static_assert(J % 4 == 0, "J must be a multiple of 4");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_wseg[NWMAX], s_wacc[NWMAX], s_flag;
-    __shared__ double s_wpart[NWMAX], s_red[32], s_edge_d[4 * NWMAX], s_split;
+    __shared__ double s_edge_d[4 * NWMAX];
     __shared__ float2 s_exptab[32];
+    __shared__ MixedTheta s_mt[NWMAX];
+    __shared__ float2 s_wpf[NWMAX], s_splitf;
     const int NT = blockDim.x, W = NT * J, nw = NT >> 5, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     float* s_edge = reinterpret_cast<float*>(s_edge_d);
-    ff_exp_table(s_exptab);
-    float* s_x0h = reinterpret_cast<float*>(smem_raw);
-    float* s_x0l = s_x0h + W;
-    float* s_p0h = s_x0l + W;
+    if (tid < 32) s_exptab[tid] = g_exptab[tid];
+    constexpr int P = J / 2;
+    float4* s_ak = reinterpret_cast<float4*>(smem_raw);  // [P][NT] (-a, -a', k, k') of (p, p+P)
+    float* s_ak1 = reinterpret_cast<float*>(smem_raw);
+    float2* s_dm = reinterpret_cast<float2*>(s_ak + P * NT);  // [P][NT] dtau/m of (p, p+P)
+    float* s_dm1 = reinterpret_cast<float*>(s_dm);
+    float* s_xh = reinterpret_cast<float*>(s_dm + (MASS ? P * NT : 0));  // [J][NT]
+    float* s_xl = s_xh + W;
+    float* s_ph = s_xl + W;
     const bool mass_on = MASS && (A.mass_on == nullptr || *A.mass_on != 0);
     const float dt = (float)A.dtau;
+    // slot j is lane j / P of pair j % P
+    auto na_at = [&](int j) -> float& { return s_ak1[((j % P) * NT + tid) * 4 + j / P]; };
+    auto k_at = [&](int j) -> float& { return s_ak1[((j % P) * NT + tid) * 4 + 2 + j / P]; };
+    auto dm_at = [&](int j) -> float& { return s_dm1[((j % P) * NT + tid) * 2 + j / P]; };
 
     for (int b = blockIdx.x; b < A.nbins; b += gridDim.x) {
-        View v;
-        load_bin(A, b, s_wseg, s_wacc, v);
-        const int base = v.base * J;
-        const int la = v.n - 1 - base;
-        const bool edge_thread = (la >= 0 && la < J);
-        const ThetaD th = v.th;
-        const float phif = (float)th.phi;
-        const float ief = (float)(1.0 / th.se2), iuf = (float)(1.0 / th.su2);
-        const ff mu_ff = ff_from_double(th.mu);
-        const ff ximu_ff = ff_from_double(th.xi + th.mu);
-        const float cmu = (float)(-th.mu * 1.4426950408889634);  // exponent of e^{-mu}
-        const int64_t off = v.si.off, wlo = v.g.wlo;
-        float2* hin = v.cur ? A.h1f : A.h0f;
-        float2* hout = v.g.split ? (v.cur ? A.h0f : A.h1f) : hin;
-
-        float xh[J], xl[J], ph[J], pl[J], af[J], kf[J];
-        float dtm[MASS ? J : 1];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int i = base + j;
-            const int64_t s = off + wlo + i;
-            const bool act = i < v.n;
-            const float2 hv = act ? hin[s] : make_float2(mu_ff.hi, mu_ff.lo);
-            ff x = two_sum(hv.x, -mu_ff.hi);  // x = h - mu in double-float
-            x.lo += hv.y - mu_ff.lo;
-            x = fast_two_sum(x.hi, x.lo);
-            xh[j] = x.hi;
-            xl[j] = x.lo;
-            af[j] = act ? A.a_f[s] : 0.0f;  // y^2/2
-            const float2 lr = act ? A.lr_f[s] : make_float2(ximu_ff.hi, ximu_ff.lo);
-            ff cp = two_sum(lr.x, -ximu_ff.hi);  // c' = lnRV - xi - mu
-            cp.lo += lr.y - ximu_ff.lo;
-            kf[j] = fmaf(-iuf, cp.hi + cp.lo, 0.5f);
-            if (MASS) dtm[MASS ? j : 0] = (act && mass_on) ? A.minv[s] : 1.0f;
-        }
-        if (A.p_in) {
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const int i = base + j;
-                const double pv = i < v.n ? A.p_in[off + wlo + i] : 0.0;
-                ph[j] = (float)pv;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < J / 4; ++q) {
-                const int64_t s0 = wlo + base + 4 * q;
-                const u64x4 r = philox_block(A.seed, (uint64_t)v.g.series, A.traj, STREAM_MOM,
-                                             (uint64_t)(s0 >> 2));
-                box_muller_f(u01_23(r.w[0]), u01_23(r.w[1]), ph[4 * q + 0], ph[4 * q + 1]);
-                box_muller_f(u01_23(r.w[2]), u01_23(r.w[3]), ph[4 * q + 2], ph[4 * q + 3]);
-            }
-#pragma unroll
-            for (int j = 0; j < J; ++j)
-                if (MASS) ph[j] = ph[j] / sqrtf(dtm[MASS ? j : 0]);
-        }
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            pl[j] = 0.0f;
-            s_x0h[j * NT + tid] = xh[j];
-            s_x0l[j * NT + tid] = xl[j];
-            s_p0h[j * NT + tid] = ph[j];
-            if (MASS) dtm[MASS ? j : 0] *= dt;  // dtau / m_t
-        }
-        int par = 0;
-
-        // Compensated v += c*u on a (hi, lo) pair: lo carries what hi lost.
-        auto cupd = [](float& hi, float& lo, float c, float u) {
-            const float y = fmaf(c, u, lo);
-            const float t = hi + y;
-            lo = y - (t - hi);
-            hi = t;
-        };
-
-        // Leapfrog with the two half steps of consecutive steps merged:
-        // x += dt/2 p;  n_md times { p -= dt F(x); x += (dt, or dt/2 at the end) p }.
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-            cupd(xh[j], xl[j], MASS ? 0.5f * dtm[MASS ? j : 0] : 0.5f * dt, ph[j]);
-        for (int k = 0; k < A.n_md; ++k) {
-            float xL, xR, e[J];
-            exchange(xh[0], xh[J - 1], xL, xR, s_edge + par * 2 * nw, nw);
-            par ^= 1;
-            if (edge_thread) innovations<J, float, true>(xh, xR, phif, la, e);
-            else innovations<J, float, false>(xh, xR, phif, la, e);
-            float eprev = v.first ? (1.0f - phif * phif) * xh[0] : fmaf(-phif, xL, xh[0]);
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const float ar = fmaf(-phif, e[j], eprev);
-                eprev = e[j];
-                float f = fmaf(iuf, xh[j], kf[j]);
-                f = fmaf(ief, ar, f);
-                // (y^2/2) e^{-h} = a 2^{-(x + mu) log2 e}: a small exponent argument
-                f = fmaf(-af[j], ex2_approx(fmaf(-kLog2e, xh[j], cmu)), f);
-                cupd(ph[j], pl[j], -dt, f);
-            }
-            const float hs = (k + 1 < A.n_md) ? 1.0f : 0.5f;
-#pragma unroll
-            for (int j = 0; j < J; ++j)
-                cupd(xh[j], xl[j], MASS ? hs * dtm[MASS ? j : 0] : hs * dt, ph[j]);
-        }
-
-        // ---- dH from per-site differences in double-float ------------------
-        // K = sum (p'^2 - p^2)/m, L = sum (x' - x), R = sum (x'-c')^2 - (x-c')^2,
-        // Q = sum e'^2 - e^2, E = sum a (e^{-h'} - e^{-h});
-        // dH = K/2 + L/2 + R/(2 s_u^2) + Q/(2 s_eta^2) + E + stationary term.
-        ff accK = {0.f, 0.f}, accL = {0.f, 0.f}, accR = {0.f, 0.f}, accQ = {0.f, 0.f},
-           accE = {0.f, 0.f};
-        double stat = 0.0;
-        const ff phi_ff = ff_from_double(th.phi);
+        float2 X[P], XL[P], PH[P], PL[P];
+        MixedConst mc;
+        ff h0;             // this thread's owned-site H at the start
+        double stat0 = 0.0;
+        bool has_stat = false;
         {
-            float xLh, xRh, xLl, xRl;
-            exchange(xh[0], xh[J - 1], xLh, xRh, s_edge + par * 2 * nw, nw);
-            par ^= 1;
-            exchange(xl[0], xl[J - 1], xLl, xRl, s_edge + par * 2 * nw, nw);
-            par ^= 1;
+            View v;
+            load_bin(A, b, s_wseg, s_wacc, v);
+            const int base = v.base * J;
+            if (lane < 16)
+                reinterpret_cast<float*>(&s_mt[warp])[lane] =
+                    reinterpret_cast<const float*>(A.theta_f + v.g.series)[lane];
+            __syncwarp();
+            const MixedTheta& mt = s_mt[warp];
+            mc.phi = mt.phi;
+            mc.st0 = mt.st0;
+            mc.ie = mt.ie;
+            mc.iu = mt.iu;
+            mc.cmu = mt.cmu;
+            mc.dt = dt;
+            mc.la = v.n - 1 - base;
+            mc.first = v.first;
+            const int64_t off = v.si.off, wlo = v.g.wlo;
+            const float2* hin = v.cur ? A.h1f : A.h0f;
+            // pass 1: site constants, x, p -> shared memory
+#pragma unroll 1
+            for (int q = 0; q < J / 4; ++q) {
+                float z[4];
+                if (A.p_in) {
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const int64_t s = wlo + base + j;
-                if (v.sid < 0 || s < v.g.lo || s >= v.g.hi) continue;
-                const ff x1 = {xh[j], xl[j]};
-                const ff x0 = {s_x0h[j * NT + tid], s_x0l[j * NT + tid]};
-                const ff d = ff_sub(x1, x0);
-                ff_acc(accL, d);
-                const float p0h = s_p0h[j * NT + tid];
-                ff q1 = two_prod(ph[j], ph[j]);  // p'^2 = (hi + lo)^2 to ~2^-48
-                q1.lo = fmaf(2.0f * ph[j], pl[j], q1.lo);
-                ff dk = ff_sub(q1, two_prod(p0h, p0h));
-                if (MASS) dk = ff_mul_f(dk, dtm[MASS ? j : 0] / dt);
-                ff_acc(accK, dk);
-                const float2 lr = A.lr_f[off + s];
-                ff cp = two_sum(lr.x, -ximu_ff.hi);
-                cp.lo += lr.y - ximu_ff.lo;
-                ff sgm = ff_add(x1, x0);
-                sgm = ff_sub(sgm, ff{2.0f * cp.hi, 2.0f * cp.lo});
-                ff_acc(accR, ff_mul(d, sgm));
-                if (s + 1 < v.si.T) {
-                    ff n1, n0;
-                    if (j + 1 < J) {
-                        n1 = {xh[j + 1], xl[j + 1]};
-                        n0 = {s_x0h[(j + 1) * NT + tid], s_x0l[(j + 1) * NT + tid]};
-                    } else {
-                        n1 = {xRh, xRl};
-                        n0 = {s_x0h[tid + 1], s_x0l[tid + 1]};
+                    for (int i = 0; i < 4; ++i) {
+                        const int ii = base + 4 * q + i;
+                        z[i] = ii < v.n ? (float)A.p_in[off + wlo + ii] : 0.0f;
                     }
-                    const ff e1 = ff_sub(n1, ff_mul(phi_ff, x1));
-                    const ff e0 = ff_sub(n0, ff_mul(phi_ff, x0));
-                    ff_acc(accQ, ff_mul(ff_sub(e1, e0), ff_add(e1, e0)));
+                } else {
+                    const int64_t s0 = wlo + base + 4 * q;
+                    const u64x4 r = philox_block(A.seed, (uint64_t)v.g.series, A.traj, STREAM_MOM,
+                                                 (uint64_t)(s0 >> 2));
+                    box_muller_f(u01_23(r.w[0]), u01_23(r.w[1]), z[0], z[1]);
+                    box_muller_f(u01_23(r.w[2]), u01_23(r.w[3]), z[2], z[3]);
                 }
-                if (s == 0) {
-                    const double a1 = ff_to_double(x1), a0 = ff_to_double(x0);
-                    stat = 0.5 * (1.0 - th.phi * th.phi) / th.se2 * (a1 * a1 - a0 * a0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int j = 4 * q + i;
+                    const int ii = base + j;
+                    const int64_t s = off + wlo + ii;
+                    const bool act = ii < v.n;
+                    const float2 hv = act ? hin[s] : make_float2(mt.mu.hi, mt.mu.lo);
+                    ff x = two_sum(hv.x, -mt.mu.hi);  // x = h - mu in double-float
+                    x.lo += hv.y - mt.mu.lo;
+                    x = fast_two_sum(x.hi, x.lo);
+                    const float a = act ? A.a_f[s] : 0.0f;  // y^2/2
+                    const float2 lr = act ? A.lr_f[s] : make_float2(mt.ximu.hi, mt.ximu.lo);
+                    ff cp = two_sum(lr.x, -mt.ximu.hi);  // c' = lnRV - xi - mu
+                    cp.lo += lr.y - mt.ximu.lo;
+                    na_at(j) = -a;
+                    k_at(j) = fmaf(-mt.iu, cp.hi + cp.lo, 0.5f);
+                    float pz = z[i];
+                    if (MASS) {
+                        const float mi = (act && mass_on) ? A.minv[s] : 1.0f;
+                        dm_at(j) = dt * mi;
+                        if (!A.p_in) pz = pz / sqrtf(mi);
+                    }
+                    s_xh[j * NT + tid] = x.hi;
+                    s_xl[j * NT + tid] = x.lo;
+                    s_ph[j * NT + tid] = pz;
                 }
-                // a (e^{-h'} - e^{-h}) with both exponentials in double-float
-                const ff E1 = ff_exp(ff_sub(ff{-mu_ff.hi, -mu_ff.lo}, x1), s_exptab);
-                const ff E0 = ff_exp(ff_sub(ff{-mu_ff.hi, -mu_ff.lo}, x0), s_exptab);
-                ff_acc(accE, ff_mul_f(ff_sub(E1, E0), af[j]));
+            }
+            __syncthreads();
+            // pass 2: H at the start over the owned sites (needs the next x)
+            HParts acc;
+            hparts_zero(acc);
+#pragma unroll 1
+            for (int j = 0; j < J; ++j) {
+                const int64_t sg = wlo + base + j;
+                if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
+                const ff x = {s_xh[j * NT + tid], s_xl[j * NT + tid]};
+                const int nidx = j + 1 < J ? (j + 1) * NT + tid : tid + 1;
+                const ff xn = {s_xh[nidx], s_xl[nidx]};
+                const float2 lr = A.lr_f[off + sg];
+                ff cp = two_sum(lr.x, -mt.ximu.hi);
+                cp.lo += lr.y - mt.ximu.lo;
+                const float mi = MASS ? dm_at(j) / dt : 1.0f;
+                hparts_site(acc, x, ff{s_ph[j * NT + tid], 0.f}, mi, cp, -na_at(j), xn,
+                            sg + 1 < v.si.T, mt, s_exptab);
+                if (sg == 0) {  // one thread per series
+                    const double a0 = ff_to_double(x);
+                    stat0 = 0.5 * (1.0 - v.th.phi * v.th.phi) / v.th.se2 * a0 * a0;
+                    has_stat = true;
+                }
+            }
+            h0 = hparts_total(acc, mt);
+            // registers <- shared memory, then the first half step of eq. (6)
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                X[q] = f2(s_xh[q * NT + tid], s_xh[(q + P) * NT + tid]);
+                XL[q] = f2(s_xl[q * NT + tid], s_xl[(q + P) * NT + tid]);
+                PH[q] = f2(s_ph[q * NT + tid], s_ph[(q + P) * NT + tid]);
+                PL[q] = f2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const float2 c0 = MASS ? f2(0.5f * dm_at(q), 0.5f * dm_at(q + P))
+                                       : f2(0.5f * dt, 0.5f * dt);
+                cupd2(X[q], XL[q], c0, PH[q]);
             }
         }
-        ff tot = ff_add(ff_add(ff_mul_f(accK, 0.5f), ff_mul_f(accL, 0.5f)), accE);
-        tot = ff_add(tot, ff_mul(accR, ff_from_double(0.5 / th.su2)));
-        tot = ff_add(tot, ff_mul(accQ, ff_from_double(0.5 / th.se2)));
-        tot = warp_sum_ff(tot);
-        double mine = (tid & 31) == 0 ? ff_to_double(tot) : 0.0;
-        mine = warp_sum(mine + stat);
-        if ((tid & 31) == 0) s_wpart[tid >> 5] = mine;
+
+        int par = 0;
+        const bool mid_end = mc.la >= 0 && mc.la < J - 1;
+        if (__any_sync(0xffffffffu, mid_end))
+            mixed_steps<J, MASS, true>(X, XL, PH, PL, s_ak, s_dm, s_edge, par, nw, A.n_md, mc);
+        else
+            mixed_steps<J, MASS, false>(X, XL, PH, PL, s_ak, s_dm, s_edge, par, nw, A.n_md, mc);
+
+        // ---- the end of the trajectory: state -> shared memory (x over the
+        // start's slots, p lo over k, which the leapfrog no longer needs) ----
+        __syncthreads();  // every warp is done reading k and the start state
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            s_xh[q * NT + tid] = X[q].x;
+            s_xh[(q + P) * NT + tid] = X[q].y;
+            s_xl[q * NT + tid] = XL[q].x;
+            s_xl[(q + P) * NT + tid] = XL[q].y;
+            s_ph[q * NT + tid] = PH[q].x;
+            s_ph[(q + P) * NT + tid] = PH[q].y;
+            k_at(q) = PL[q].x;
+            k_at(q + P) = PL[q].y;
+        }
         __syncthreads();
-        segment_decisions(A, v, s_wpart, s_wacc, &s_split);
+        View v;
+        view_of(A, s_wseg, v);
+        const int base = v.base * J;
+        const MixedTheta& mt = s_mt[warp];
+        const int64_t off = v.si.off, wlo = v.g.wlo;
+        HParts acc;
+        hparts_zero(acc);
+        double stat1 = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < J; ++j) {
+            const int64_t sg = wlo + base + j;
+            if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
+            const ff x = {s_xh[j * NT + tid], s_xl[j * NT + tid]};
+            const int nidx = j + 1 < J ? (j + 1) * NT + tid : tid + 1;
+            const ff xn = {s_xh[nidx], s_xl[nidx]};
+            const float2 lr = A.lr_f[off + sg];
+            ff cp = two_sum(lr.x, -mt.ximu.hi);
+            cp.lo += lr.y - mt.ximu.lo;
+            const float mi = MASS ? dm_at(j) / dt : 1.0f;
+            hparts_site(acc, x, ff{s_ph[j * NT + tid], k_at(j)}, mi, cp, -na_at(j), xn,
+                        sg + 1 < v.si.T, mt, s_exptab);
+            if (sg == 0) {
+                const double a1 = ff_to_double(x);
+                stat1 = 0.5 * (1.0 - v.th.phi * v.th.phi) / v.th.se2 * a1 * a1;
+            }
+        }
+        ff dh = ff_sub(hparts_total(acc, mt), h0);
+        if (has_stat) dh = ff_add(dh, ff_from_double(stat1 - stat0));
+        dh = warp_sum_ff(dh);
+        if (lane == 0) s_wpf[warp] = make_float2(dh.hi, dh.lo);
+        __syncthreads();
+        segment_decisions_ff(A, v, s_wpf, s_wacc, &s_splitf);
         __syncthreads();
         const bool write_h = v.sid >= 0 && (v.g.split || s_wacc[v.g.warp0]);
-#pragma unroll
+        float2* hout = v.g.split ? (v.cur ? A.h0f : A.h1f) : (v.cur ? A.h1f : A.h0f);
+#pragma unroll 1
         for (int j = 0; j < J; ++j) {
-            const int64_t s = wlo + base + j;
-            if (v.sid >= 0 && s >= v.g.lo && s < v.g.hi) {
+            const int64_t sg = wlo + base + j;
+            if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
                 if (write_h) {
-                    ff hh = two_sum(xh[j], mu_ff.hi);
-                    hh.lo += xl[j] + mu_ff.lo;
+                    ff hh = two_sum(s_xh[j * NT + tid], mt.mu.hi);
+                    hh.lo += s_xl[j * NT + tid] + mt.mu.lo;
                     hh = fast_two_sum(hh.hi, hh.lo);
-                    hout[off + s] = make_float2(hh.hi, hh.lo);
+                    hout[off + sg] = make_float2(hh.hi, hh.lo);
                 }
-                if (A.p_out) A.p_out[off + s] = (double)ph[j] + (double)pl[j];
+                if (A.p_out) A.p_out[off + sg] = (double)s_ph[j * NT + tid] + (double)k_at(j);
             }
         }
-        if (v.g.split) finish_split(A, v, s_split, s_red, &s_flag);
+        if (v.g.split) finish_split_ff(A, v, s_splitf, &s_flag);
     }
 }
 
@@ -659,7 +872,38 @@ cudaError_t launch_mixed(const TrajArgs& a, const Plan& p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+__global__ void k_theta_prep(const double* __restrict__ theta, ThetaD th_inline, int n,
+                             MixedTheta* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const ff v = ff_from_double(exp2((double)threadIdx.x / 32.0));
+        g_exptab[threadIdx.x] = make_float2(v.hi, v.lo);
+    }
+    if (i < n) out[i] = mixed_theta(theta ? load_theta(theta + 5 * (int64_t)i) : th_inline);
+}
+
 }  // namespace
+
+cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, MixedTheta* theta_f,
+                              cudaStream_t st)
+{
+    const int g = (n + 127) / 128;
+    k_theta_prep<<<g < 1 ? 1 : g, 128, 0, st>>>(theta, th_inline, n, theta_f);
+    return cudaGetLastError();
+}
+
+int mixed_max_threads(int j)
+{
+    switch (j) {
+        case 4: return mixed_ntmax<4>();
+        case 8: return mixed_ntmax<8>();
+        case 12: return mixed_ntmax<12>();
+        case 16: return mixed_ntmax<16>();
+        case 20: return mixed_ntmax<20>();
+        default: return 0;
+    }
+}
 
 int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem)
 {
@@ -683,7 +927,7 @@ int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem)
         else RSV_OCC((k_traj_fp64<JJ, false>));                            \
         break;
     if (mixed) {
-        switch (j) { RSV_JM(4) RSV_JM(8) RSV_JM(16) RSV_JM(20) default: return 0; }
+        switch (j) { RSV_JM(4) RSV_JM(8) RSV_JM(12) RSV_JM(16) RSV_JM(20) default: return 0; }
     } else {
         switch (j) { RSV_JD(4) RSV_JD(8) RSV_JD(16) RSV_JD(28) default: return 0; }
     }
@@ -705,6 +949,7 @@ cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st)
         switch (p.j) {
             RSV_CASE(launch_mixed, 4)
             RSV_CASE(launch_mixed, 8)
+            RSV_CASE(launch_mixed, 12)
             RSV_CASE(launch_mixed, 16)
             RSV_CASE(launch_mixed, 20)
             default: return cudaErrorInvalidValue;

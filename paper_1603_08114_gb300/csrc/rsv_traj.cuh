@@ -50,6 +50,34 @@ struct Plan {
     bool mixed = false, mass = false;
 };
 
+// theta-derived constants of one series in FP32 / double-float for the mixed
+// path, 16 floats per series.  The FP64 pipe of this GPU runs at 1/64 of the
+// FP32 rate and every FP64 instruction occupies it for the whole warp, even
+// with one lane active, so these are derived once per series (mixed_theta, by
+// a small kernel or the theta update) instead of inside the trajectory kernel.
+struct MixedTheta {
+    float phi, st0, iu, ie, cmu;  // leapfrog: phi, 1 - phi^2, 1/s_u^2, 1/s_eta^2, -mu log2 e
+    ff mu, ximu, phi_ff, hu, he;  // dH: mu, xi + mu, phi, 1/(2 s_u^2), 1/(2 s_eta^2)
+    float pad;
+};
+static_assert(sizeof(MixedTheta) == 64, "MixedTheta is 16 floats");
+__device__ __forceinline__ MixedTheta mixed_theta(const ThetaD& th)
+{
+    MixedTheta m;
+    m.phi = (float)th.phi;
+    m.st0 = 1.0f - m.phi * m.phi;
+    m.iu = (float)(1.0 / th.su2);
+    m.ie = (float)(1.0 / th.se2);
+    m.cmu = (float)(-th.mu * 1.4426950408889634);  // exponent of e^{-mu}
+    m.mu = ff_from_double(th.mu);
+    m.ximu = ff_from_double(th.xi + th.mu);
+    m.phi_ff = ff_from_double(th.phi);
+    m.hu = ff_from_double(0.5 / th.su2);
+    m.he = ff_from_double(0.5 / th.se2);
+    m.pad = 0.0f;
+    return m;
+}
+
 struct TrajArgs {
     const Seg* segs;
     const int* bin_first;
@@ -76,6 +104,7 @@ struct TrajArgs {
     const double* lnrv;
     const float* a_f;    // mixed path: y^2/2 and lnRV as (hi, lo)
     const float2* lr_f;
+    const MixedTheta* theta_f;  // mixed path: per-series constants (launch_theta_prep)
     const float* minv;   // optional inverse mass (FP32, packed)
     const int* mass_on;  // optional flag; 0 = use m = 1
     int n_md;
@@ -94,6 +123,13 @@ bool make_plan(const int64_t* offsets, int n, int n_md, bool mixed, bool mass, i
 void free_plan(Plan& plan);
 
 cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st);
+// theta_f[s] = mixed_theta(theta of series s) for n series (theta: device
+// [n][5], or NULL for th_inline); also fills the device table of 2^(j/32).
+cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, MixedTheta* theta_f,
+                              cudaStream_t st);
+// Largest block (threads) of the mixed kernel with `j` sites per thread (0 if
+// j is not instantiated).
+int mixed_max_threads(int j);
 // Resident blocks per SM of a trajectory kernel configuration (0 if invalid).
 int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem);
 

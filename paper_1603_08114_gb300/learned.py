@@ -3,10 +3,12 @@
 Control flow only - every arithmetic step runs in librsv's kernels:
   1. run the plain (identity-mass) sampler and fold its h snapshots into
      per-site Welford moments (rsv_hmc_chain + rsv_welford_update);
-  2. target log(1/Var(h_t)) and frozen posterior mean hbar (rsv_welford_target);
+  2. target log(1/Var(h_t)), its mean over the sites (the log of the output
+     scale s) and the frozen posterior mean hbar (rsv_welford_target);
   3. standardised features from hbar, y, lnRV, theta (rsv_mass_features);
   4. Adam training of the BF16 MLP (rsv_mlp_train);
-  5. inverse mass 1/m_t for every site (rsv_mlp_mass).
+  5. inverse mass 1/m_t for every site (rsv_mlp_mass), m_t clamped to
+     [1/s_u^2, diagonal of the Hessian of S at hbar].
 The mass is a function of the frozen hbar only, so HMC with it stays exact.
 
 The sampler that uses it (`MassSampler`) runs the chain in windows of
@@ -62,6 +64,7 @@ def collect_moments(ctx, h, y, lnrv, theta_dev, n_snap: int, n_md: int, dtau: fl
 class TrainedMass:
     minv: torch.Tensor
     params: torch.Tensor
+    log_scale: torch.Tensor
     losses: torch.Tensor
     target: torch.Tensor
     hbar: torch.Tensor
@@ -73,22 +76,27 @@ def train_mass(ctx, y, lnrv, theta, mean, m2, count: int, steps: int = 2000, bat
     """Steps 2-5: target, features, Adam training, inverse mass."""
     T = y.numel()
     hbar = torch.empty(T, dtype=torch.float64, device=y.device)
-    target = rsv.rsv_welford_target(ctx, mean, m2, count, hbar_out=hbar)
+    log_s = torch.empty(1, dtype=torch.float32, device=y.device)
+    target = rsv.rsv_welford_target(ctx, mean, m2, count, hbar_out=hbar, log_scale_out=log_s)
     feat, _ = rsv.rsv_mass_features(ctx, y, lnrv, hbar, theta)
     params = torch.tensor(glorot_params(init_seed), device=y.device)
     am = torch.zeros_like(params)
     av = torch.zeros_like(params)
     losses = torch.empty(max(steps, 1), dtype=torch.float32, device=y.device)
     rsv.rsv_mlp_train(ctx, feat, target, params, am, av, 0, steps, batch, seed, lr,
-                      loss_out=losses if steps else None)
-    minv = rsv.rsv_mlp_mass(ctx, feat, params)
-    return TrainedMass(minv=minv, params=params, losses=losses[:steps], target=target,
+                      loss_out=losses if steps else None, log_scale=log_s)
+    minv = rsv.rsv_mlp_mass(ctx, feat, params, y, hbar, theta, log_scale=log_s)
+    return TrainedMass(minv=minv, params=params, log_scale=log_s, losses=losses[:steps],
+                       target=target,
                        hbar=hbar, features=feat)
 
 
+LADDER = (0.5, 0.4, 0.3, 0.25, 0.2, 0.15, 0.12, 0.1, 0.08, 0.07, 0.06, 0.05, 0.045, 0.04,
+          0.035, 0.03, 0.025, 0.02, 0.015, 0.01)
+
+
 def tune_step(ctx, h, y, lnrv, theta_dev, minv, length: float, prec="mixed",
-              ladder=(0.5, 0.4, 0.3, 0.25, 0.2, 0.15, 0.1, 0.05), n_try: int = 10,
-              target_acc: float = 0.8, seed: int = 99):
+              ladder=LADDER, n_try: int = 40, target_acc: float = 0.8, seed: int = 99):
     """Largest step of the ladder whose acceptance over n_try trajectories (of
     length ~ `length`) reaches target_acc; returns (dtau, n_md).  h is not
     modified."""
@@ -114,10 +122,11 @@ class MassSampler:
     n_md: int
     plain_dtau: float
     plain_n_md: int
-    window: int = 50
+    window: int = 100
     prec: str = "mixed"
     fell_back: bool = False
     history: list = field(default_factory=list)
+    md_steps: int = 0   # leapfrog steps run so far (per site)
 
     def run(self, h, y, lnrv, theta_dev, n_traj: int, seed: int, traj0: int = 0, snaps=None,
             theta_out=None, accept_out=None, update_theta: bool = True):
@@ -134,11 +143,13 @@ class MassSampler:
                                   self.plain_dtau, k, prec=self.prec, seed=seed,
                                   traj0=traj0 + done, snaps=sn, thin=1, theta_out=tho,
                                   accept_out=acc, update_theta=update_theta)
+                self.md_steps += k * self.plain_n_md
             else:
                 rsv.rsv_hmc_chain(self.ctx, h, y, lnrv, theta_dev, self.n_md, self.dtau, k,
                                   prec=self.prec, minv=self.minv, seed=seed, traj0=traj0 + done,
                                   snaps=sn, thin=1, theta_out=tho, accept_out=acc,
                                   update_theta=update_theta)
+                self.md_steps += k * self.n_md
                 rate = float(acc.float().mean())
                 self.history.append(rate)
                 if rate < 0.6:

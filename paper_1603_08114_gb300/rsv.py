@@ -146,9 +146,16 @@ def rsv_set_schedule(ctx: Context, threads: int = 0, sites_per_thread: int = 0, 
     _check(lib().rsv_set_schedule(ctx.handle, int(threads), int(sites_per_thread), int(tile)))
 
 
-def rsv_sync_status(ctx: Context):
-    """Synchronise the current stream; raise on a device-side condition."""
-    _check(lib().rsv_sync_status(ctx.handle, _stream()))
+def rsv_sync_status(ctx: Context, allow_nonfinite: bool = False) -> int:
+    """Synchronise the current stream and clear the device status word; raise on
+    a device-side condition.  With allow_nonfinite, RSV_ENONFINITE (a trajectory
+    whose dH was not finite, rejected by the Metropolis test) is returned
+    instead of raised."""
+    st = lib().rsv_sync_status(ctx.handle, _stream())
+    if allow_nonfinite and st == RSV_ENONFINITE:
+        return st
+    _check(st)
+    return st
 
 
 def rsv_action(ctx: Context, h, y, lnrv, th, S_out=None):
@@ -317,12 +324,12 @@ def _mlp_lib():
     L = lib()
     if not getattr(L, "_mlp_ready", False):
         L.rsv_welford_update.argtypes = [_P, _P, _I64, _I64, _I64, _P, _P, _P]
-        L.rsv_welford_target.argtypes = [_P, _P, _P, _I64, _I64, _P, _P, _P]
+        L.rsv_welford_target.argtypes = [_P, _P, _P, _I64, _I64, _P, _P, _P, _P]
         L.rsv_mass_features.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P, _P]
-        L.rsv_mlp_grad.argtypes = [_P, _P, _P, _I64, _P, _U64, _U64, _INT, _P, _P, _P]
-        L.rsv_mlp_train.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _I64, _INT, _INT, _U64,
+        L.rsv_mlp_grad.argtypes = [_P, _P, _P, _I64, _P, _P, _U64, _U64, _INT, _P, _P, _P]
+        L.rsv_mlp_train.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _P, _I64, _INT, _INT, _U64,
                                     ctypes.c_float, _P, _P]
-        L.rsv_mlp_mass.argtypes = [_P, _P, _I64, _P, _P, _P, _P]
+        L.rsv_mlp_mass.argtypes = [_P, _P, _I64, _P, _P, _P, _P, Theta, _P, _P, _P]
         for n in ("rsv_welford_update", "rsv_welford_target", "rsv_mass_features",
                   "rsv_mlp_grad", "rsv_mlp_train", "rsv_mlp_mass"):
             getattr(L, n).restype = _INT
@@ -339,7 +346,8 @@ def rsv_welford_update(ctx: Context, x, count: int, mean, m2):
     return count + n
 
 
-def rsv_welford_target(ctx: Context, mean, m2, count: int, hbar_out=None, target_out=None):
+def rsv_welford_target(ctx: Context, mean, m2, count: int, hbar_out=None, target_out=None,
+                       log_scale_out=None):
     T = mean.numel()
     if target_out is None:
         target_out = torch.empty(T, dtype=torch.float32, device=mean.device)
@@ -347,6 +355,7 @@ def rsv_welford_target(ctx: Context, mean, m2, count: int, hbar_out=None, target
                                          _ptr(m2, torch.float64, T, "m2"), T, int(count),
                                          _ptr(hbar_out, torch.float64, T, "hbar_out"),
                                          _ptr(target_out, torch.float32, T, "target_out"),
+                                         _ptr(log_scale_out, torch.float32, 1, "log_scale_out"),
                                          _stream()))
     return target_out
 
@@ -363,13 +372,15 @@ def rsv_mass_features(ctx: Context, y, lnrv, hbar, th):
     return feat, stats
 
 
-def rsv_mlp_grad(ctx: Context, feat, target, params, seed: int, step: int, batch: int):
+def rsv_mlp_grad(ctx: Context, feat, target, params, seed: int, step: int, batch: int,
+                 log_scale=None):
     T = target.numel()
     g = torch.empty(RSV_MLP_NPARAM, dtype=torch.float32, device=feat.device)
     loss = torch.empty(1, dtype=torch.float32, device=feat.device)
     _check(_mlp_lib().rsv_mlp_grad(ctx.handle, _ptr(feat, torch.float32, 20 * T, "feat"),
                                    _ptr(target, torch.float32, T, "target"), T,
                                    _ptr(params, torch.float32, RSV_MLP_NPARAM, "params"),
+                                   _ptr(log_scale, torch.float32, 1, "log_scale"),
                                    int(seed), int(step), int(batch),
                                    _ptr(g, torch.float32, RSV_MLP_NPARAM, "grad"),
                                    _ptr(loss, torch.float32, 1, "loss"), _stream()))
@@ -377,11 +388,12 @@ def rsv_mlp_grad(ctx: Context, feat, target, params, seed: int, step: int, batch
 
 
 def rsv_mlp_train(ctx: Context, feat, target, params, adam_m, adam_v, step0: int, n_steps: int,
-                  batch: int, seed: int, lr: float = 1e-3, loss_out=None):
+                  batch: int, seed: int, lr: float = 1e-3, loss_out=None, log_scale=None):
     T = target.numel()
     _check(_mlp_lib().rsv_mlp_train(ctx.handle, _ptr(feat, torch.float32, 20 * T, "feat"),
                                     _ptr(target, torch.float32, T, "target"), T,
                                     _ptr(params, torch.float32, RSV_MLP_NPARAM, "params"),
+                                    _ptr(log_scale, torch.float32, 1, "log_scale"),
                                     _ptr(adam_m, torch.float32, RSV_MLP_NPARAM, "adam_m"),
                                     _ptr(adam_v, torch.float32, RSV_MLP_NPARAM, "adam_v"),
                                     int(step0), int(n_steps), int(batch), int(seed), float(lr),
@@ -389,11 +401,14 @@ def rsv_mlp_train(ctx: Context, feat, target, params, adam_m, adam_v, step0: int
                                     _stream()))
 
 
-def rsv_mlp_mass(ctx: Context, feat, params, m_out=None):
+def rsv_mlp_mass(ctx: Context, feat, params, y, hbar, th, m_out=None, log_scale=None):
     T = feat.shape[0]
     minv = torch.empty(T, dtype=torch.float32, device=feat.device)
     _check(_mlp_lib().rsv_mlp_mass(ctx.handle, _ptr(feat, torch.float32, 20 * T, "feat"), T,
                                    _ptr(params, torch.float32, RSV_MLP_NPARAM, "params"),
+                                   _ptr(log_scale, torch.float32, 1, "log_scale"),
+                                   _ptr(y, torch.float64, T, "y"),
+                                   _ptr(hbar, torch.float64, T, "hbar"), theta(th),
                                    _ptr(minv, torch.float32, T, "minv"),
                                    _ptr(m_out, torch.float32, T, "m_out"), _stream()))
     return minv

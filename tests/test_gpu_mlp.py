@@ -58,8 +58,10 @@ def test_welford_matches_two_pass(rsv, ctx):
     assert np.allclose(mean.cpu().numpy(), m, rtol=0, atol=1e-12)
     assert np.allclose(m2.cpu().numpy() / (c - 1), v, rtol=1e-11)
     hbar = torch.empty_like(mean)
-    tgt = rsv.rsv_welford_target(ctx, mean, m2, c, hbar_out=hbar).cpu().numpy()
+    ls = torch.empty(1, dtype=torch.float32, device="cuda")
+    tgt = rsv.rsv_welford_target(ctx, mean, m2, c, hbar_out=hbar, log_scale_out=ls).cpu().numpy()
     assert np.allclose(tgt, np.log(1 / v), rtol=0, atol=1e-5)
+    assert abs(ls.item() - np.log(1 / v).mean()) < 1e-5
     assert np.array_equal(hbar.cpu().numpy(), mean.cpu().numpy())
 
 
@@ -81,28 +83,37 @@ def problem(rsv, ctx):
     F, _ = rsv.rsv_mass_features(ctx, dev(s.y), dev(s.lnrv), dev(hbar), TH)
     target = (-np.log(0.02 + 0.01 * np.cos(np.arange(T) * 0.01) ** 2)).astype(np.float32)
     P = mlp.init_params(2)
+    log_s = float(np.float32(target.mean()))
     return dict(T=T, F=F, Fnp=F.cpu().numpy().astype(np.float64), target=dev(target, torch.float32),
-                target_np=target.astype(np.float64), P=P)
+                target_np=target.astype(np.float64), P=P, series=s, log_s=log_s,
+                log_s_dev=dev([log_s], torch.float32))
 
 
-def test_forward_matches_reference(rsv, ctx, problem):
+@pytest.mark.parametrize("scaled", [False, True])
+def test_forward_matches_reference(rsv, ctx, problem, scaled):
     params = dev(flat(problem["P"]), torch.float32)
     m_gpu = torch.empty(problem["T"], dtype=torch.float32, device="cuda")
-    minv = rsv.rsv_mlp_mass(ctx, problem["F"], params, m_out=m_gpu).cpu().numpy()
-    ref = mlp.forward(unflat(flat(problem["P"])), problem["Fnp"], bf=True)["m"]
+    s = problem["series"]
+    ls = problem["log_s"] if scaled else 0.0
+    minv = rsv.rsv_mlp_mass(ctx, problem["F"], params, dev(s.y), dev(s.h_true), TH, m_out=m_gpu,
+                            log_scale=problem["log_s_dev"] if scaled else None).cpu().numpy()
+    ref = mlp.forward(unflat(flat(problem["P"])), problem["Fnp"], bf=True, log_s=ls)["m"]
+    lo, hi = mlp.mass_bounds(s.y, s.h_true, TH)
+    ref = np.clip(ref, lo, hi)
     rel = np.abs(m_gpu.cpu().numpy() - ref) / ref
     assert np.median(rel) < 1e-5 and np.max(rel) < 5e-3
     assert np.allclose(minv, 1 / m_gpu.cpu().numpy(), rtol=1e-6)
 
 
-@pytest.mark.parametrize("batch", [64, 4096])
-def test_gradient_matches_reference(rsv, ctx, problem, batch):
+@pytest.mark.parametrize("batch,scaled", [(64, False), (4096, False), (4096, True)])
+def test_gradient_matches_reference(rsv, ctx, problem, batch, scaled):
     params = dev(flat(problem["P"]), torch.float32)
     g, loss = rsv.rsv_mlp_grad(ctx, problem["F"], problem["target"], params, seed=11, step=3,
-                               batch=batch)
+                               batch=batch, log_scale=problem["log_s_dev"] if scaled else None)
     idx = mlp.batch_indices(11, 3, problem["T"], batch)
     L, G = mlp.loss_and_grads(unflat(flat(problem["P"])), problem["Fnp"][idx],
-                              problem["target_np"][idx], bf=True)
+                              problem["target_np"][idx], bf=True,
+                              log_s=problem["log_s"] if scaled else 0.0)
     assert abs(loss.item() - L) <= 1e-4 * L
     gg = unflat(g.cpu().numpy())
     for k in G:
@@ -193,8 +204,9 @@ def test_learned_mass_gains_over_identity(rsv, ctx):
 
 def test_trained_mass_recovers_exact_precision_in_gaussian_subcase(rsv, ctx):
     """y = 0: the posterior of h is Gaussian and 1/Var(h_t) is known exactly
-    (tridiagonal inverse).  Trained on that exact target the network's m_t
-    matches it within 3 % at every site, edges included."""
+    (tridiagonal inverse).  Trained on that exact target (output scale = its
+    geometric mean) the network's m_t matches it within 3 % at every site,
+    edges included."""
     from paper_1603_08114_gb300 import learned
     from tests.kalman_pin import tridiag_posterior
     T = 4000
@@ -202,12 +214,14 @@ def test_trained_mass_recovers_exact_precision_in_gaussian_subcase(rsv, ctx):
     y0 = np.zeros(T)
     m_exact, v_exact, _ = tridiag_posterior(s.lnrv, TH)
     target = dev(np.log(1.0 / v_exact).astype(np.float32), torch.float32)
+    ls = dev([np.log(1.0 / v_exact).mean()], torch.float32)
     F, _ = rsv.rsv_mass_features(ctx, dev(y0), dev(s.lnrv), dev(m_exact), TH)
     params = dev(learned.glorot_params(0), torch.float32)
     am, av = torch.zeros_like(params), torch.zeros_like(params)
-    rsv.rsv_mlp_train(ctx, F, target, params, am, av, 0, 3000, 1024, seed=5, lr=3e-3)
+    rsv.rsv_mlp_train(ctx, F, target, params, am, av, 0, 3000, 1024, seed=5, lr=3e-3,
+                      log_scale=ls)
     m = torch.empty(T, dtype=torch.float32, device="cuda")
-    rsv.rsv_mlp_mass(ctx, F, params, m_out=m)
+    rsv.rsv_mlp_mass(ctx, F, params, dev(y0), dev(m_exact), TH, m_out=m, log_scale=ls)
     rel = np.abs(m.cpu().numpy() * v_exact - 1.0)
     assert np.max(rel) < 0.03, (np.max(rel), np.argmax(rel))
 
