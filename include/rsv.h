@@ -223,10 +223,14 @@ rsv_status rsv_hmc_batched(rsv_ctx* ctx, rsv_plan* plan, double* h, double* p, c
  * this order from Philox counter {block, traj, 2, series}, key {seed, 0}.
  *  h [T] FP64, lnrv [T] FP64, theta device FP64 [5] in/out.
  *  mask: bit 0 xi, 1 s_u^2, 2 mu, 3 s_eta^2, 4 phi (31 = all).
+ *  prec: RSV_FP64 -- statistics and draws in FP64 (53-bit uniforms);
+ *        RSV_MIXED -- the sweep the mixed chain runs: h and lnRV as (hi, lo)
+ *        FP32 pairs, statistics in double-float, the draws in FP32 from 23-bit
+ *        uniforms of the same stream positions; theta comes out FP32-valued.
  *  phi_acc_out: device int32 scalar (1 if the phi proposal was accepted) or NULL. */
 rsv_status rsv_gibbs_theta(rsv_ctx* ctx, const double* h, const double* lnrv, int64_t T,
                            double* theta, uint64_t seed, uint64_t series, uint64_t traj,
-                           int mask, int32_t* phi_acc_out, void* stream);
+                           int mask, rsv_precision prec, int32_t* phi_acc_out, void* stream);
 
 /* ---- learned diagonal mass ---------------------------------------------------
  * The paper has no learned part; these calls build the per-site mass m_t used

@@ -19,8 +19,14 @@ import torch
 
 from . import rsv
 
+# bumped whenever the trajectory kernels change, so cached choices are redone
+KERNEL_REV = 2
+
 CANDIDATES = {
-    "mixed": [(nt, j) for j in (8, 16, 20) for nt in (128, 192, 256, 320, 384)],
+    "mixed": ([(nt, 20) for nt in (128, 192, 256, 320, 384)]
+              + [(nt, 16) for nt in (128, 256, 384, 512)]
+              + [(nt, 12) for nt in (192, 320, 448, 640)]
+              + [(nt, 8) for nt in (256, 384, 512, 768)]),
     "fp64": [(nt, j) for j in (8, 16, 28) for nt in (64, 128, 192, 256)],
 }
 
@@ -37,7 +43,8 @@ def _key(prec, n_md, mass, offsets) -> str:
     name = torch.cuda.get_device_name()
     b_total = int(math.log2(max(int(T.sum()), 1)))
     b_max = int(math.log2(max(int(T.max()), 1)))
-    return f"{name}|{prec}|{n_md}|{int(bool(mass))}|n{len(T)}|tot2^{b_total}|max2^{b_max}"
+    return (f"{name}|k{KERNEL_REV}|{prec}|{n_md}|{int(bool(mass))}|n{len(T)}|tot2^{b_total}"
+            f"|max2^{b_max}")
 
 
 def tune_plan(ctx: rsv.Context, offsets, n_md: int, prec: str, y, lnrv, theta_dev, dtau: float,

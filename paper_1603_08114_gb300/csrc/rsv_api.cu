@@ -246,18 +246,39 @@ rsv_status rsv_draw_momenta(rsv_ctx* c, uint64_t seed, uint64_t series, uint64_t
 
 rsv_status rsv_gibbs_theta(rsv_ctx* c, const double* h, const double* lnrv, int64_t T,
                            double* theta, uint64_t seed, uint64_t series, uint64_t traj,
-                           int mask, int32_t* phi_acc_out, void* stream)
+                           int mask, rsv_precision prec, int32_t* phi_acc_out, void* stream)
 {
     rsv_status st = ctx_begin(c, stream);
     if (st != RSV_OK) return st;
     if (!h || !lnrv || !theta) return fail(RSV_EINVAL, "null argument");
     if (T < 1) return fail(RSV_EINVAL, "T must be >= 1");
     if (mask < 0 || mask > 31) return fail(RSV_EINVAL, "mask must be in 0..31");
+    if (prec != RSV_FP64 && prec != RSV_MIXED) return fail(RSV_EINVAL, "bad precision");
+    const bool mixed = prec == RSV_MIXED;
     if ((st = c->gibbs.ensure((size_t)gibbs_grid(T) * 8 * sizeof(double))) != RSV_OK) return st;
+    if (mixed && ((st = c->fbuf0.ensure((size_t)T * 8)) != RSV_OK ||
+                  (st = c->lr_f.ensure((size_t)T * 8)) != RSV_OK ||
+                  (st = c->theta_f.ensure(sizeof(MixedTheta))) != RSV_OK))
+        return st;
     GibbsArgs g;
     memset(&g, 0, sizeof(g));
-    g.h0d = h;
-    g.lnrv = lnrv;
+    cudaError_t e;
+    if (mixed) {
+        // the state and lnRV as (hi, lo) FP32 pairs, theta's constants
+        if ((e = counted(c, launch_h_to_ff, h, c->fbuf0.as<float2>(), T,
+                         (cudaStream_t)stream)) != cudaSuccess ||
+            (e = counted(c, launch_h_to_ff, lnrv, c->lr_f.as<float2>(), T,
+                         (cudaStream_t)stream)) != cudaSuccess ||
+            (e = counted(c, launch_theta_prep, (const double*)theta, ThetaD{}, 1,
+                         c->theta_f.as<MixedTheta>(), (cudaStream_t)stream)) != cudaSuccess)
+            return cuda_fail(e, "theta update set-up");
+        g.h0f = c->fbuf0.as<float2>();
+        g.lr_f = c->lr_f.as<float2>();
+        g.theta_f = c->theta_f.as<MixedTheta>();
+    } else {
+        g.h0d = h;
+        g.lnrv = lnrv;
+    }
     g.T = T;
     g.theta = theta;
     g.seed = seed;
@@ -267,7 +288,7 @@ rsv_status rsv_gibbs_theta(rsv_ctx* c, const double* h, const double* lnrv, int6
     g.partials = c->gibbs.as<double>();
     g.counter = reinterpret_cast<unsigned*>(c->ints.as<int>() + kGibbsCounter);
     g.phi_acc = phi_acc_out;
-    cudaError_t e = counted(c, launch_gibbs, g, false, (cudaStream_t)stream);
+    e = counted(c, launch_gibbs, g, mixed, (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "theta kernel");
 }
 

@@ -26,51 +26,329 @@ namespace {
 
 constexpr int NSTAT = 8;  // sum q, sum q^2, X_a, X_b, XX_m, XY, sum e, sum e^2
 
-// Sequential uniforms of Philox stream 2 for one trajectory (block 0, 1, ...).
-struct Stream {
-    uint64_t seed, series, traj, blk;
-    u64x4 w;
+// ---------------------------------------------------------------------------
+// The draws with their variates precomputed in parallel.  The FP64 pipe of
+// this GPU takes about 64 cycles per warp instruction whether one lane or 32
+// are active, so a single thread walking the draws spends most of its time
+// there.  Every random variate the sweep uses is a function of stream 2 alone
+// (uniforms, their logs, Box-Muller normals, and the Marsaglia-Tsang
+// candidates v = (1 + c z)^3 with their logs, c fixed by T), so all of them
+// are computed for stream positions 0..NPRE-1 at once, one position per lane,
+// with the transcendental steps spread over four warps (four FP64 units);
+// so are the few quantities that need only the current theta.  One warp then
+// walks the sweep consuming stream 2 in order (block k of Philox stream 2
+// gives positions 4k..4k+3), with the same FP64 expressions, and evaluates
+// directly past the precomputed positions.
+// ---------------------------------------------------------------------------
+constexpr int NPRE = 32;
+
+struct PreDraws {
+    double u[NPRE + 1], lu[NPRE], sq[NPRE], cs[NPRE], bm[NPRE], v[NPRE], v3[NPRE], lv3[NPRE];
+    double gc, gd;                  // Marsaglia-Tsang c, d of the sweep's gamma shape
+    double sxi, mmu, smu, lphi;     // sqrt(s_u^2/T); mean and precision root of mu; log(1-phi^2)
+};
+
+// Variates in stream order: u01 takes one position; normal() two, the cosine
+// branch of Box-Muller sqrt(-2 ln u1) cospi(2 u2); gamma(alpha) by Marsaglia &
+// Tsang (ACM TOMS 26, 2000) for alpha >= 1 (NaN after 1000 rejections), and
+// as Gamma(alpha + 1) u^(1/alpha) for alpha < 1.
+struct WalkStream {
+    const PreDraws* P;
+    uint64_t seed, series, traj;
     int pos;
-    __device__ double u01()
+    double alpha_pre;
+    __device__ double direct_u(int i) const
     {
-        if (pos == 4) {
-            w = philox_block(seed, series, traj, STREAM_THETA, blk++);
-            pos = 0;
-        }
-        return u01_53(w.w[pos++]);
+        const u64x4 w = philox_block(seed, series, traj, STREAM_THETA, (uint64_t)(i >> 2));
+        return u01_53(w.w[i & 3]);
     }
-    // cosine branch of Box-Muller: one normal per two uniforms
+    __device__ double uni(int i) const { return i <= NPRE ? P->u[i] : direct_u(i); }
+    __device__ double loguni(int i) const { return i < NPRE ? P->lu[i] : log(uni(i)); }
+    __device__ double normal_at(int i) const
+    {
+        return i < NPRE ? P->bm[i] : sqrt(-2.0 * loguni(i)) * cospi(2.0 * uni(i + 1));
+    }
+    __device__ double u01() { return uni(pos++); }
     __device__ double normal()
     {
-        const double u1 = u01(), u2 = u01();
-        return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        const double z = normal_at(pos);
+        pos += 2;
+        return z;
     }
-    // Gamma(alpha, 1): Marsaglia & Tsang (ACM TOMS 26, 2000) for alpha >= 1;
-    // alpha < 1 as Gamma(alpha + 1) u^(1/alpha).  NaN after 1000 rejections.
     __device__ double gamma(double alpha)
     {
-        double scale = 1.0;
         if (alpha < 1.0) {
             const double g = gamma1(alpha + 1.0);
             const double u = u01();
             return g * pow(u, 1.0 / alpha);
         }
-        return scale * gamma1(alpha);
+        return gamma1(alpha);
     }
     __device__ double gamma1(double alpha)
     {
-        const double d = alpha - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+        const bool pre = alpha == alpha_pre;
+        const double d = pre ? P->gd : alpha - 1.0 / 3.0;
+        const double c = pre ? P->gc : 1.0 / sqrt(9.0 * d);
         for (int it = 0; it < 1000; ++it) {
+            const int i = pos;
+            const bool hit = pre && i < NPRE;
             const double z = normal();
-            double v = 1.0 + c * z;
+            double v = hit ? P->v[i] : 1.0 + c * z;
             if (v <= 0.0) continue;
-            v = v * v * v;
-            const double u = u01();
-            if (log(u) < 0.5 * z * z + d - d * v + d * log(v)) return d * v;
+            v = hit ? P->v3[i] : v * v * v;
+            const double lu = loguni(pos++);
+            const double lv = hit ? P->lv3[i] : log(v);
+            if (lu < 0.5 * z * z + d - d * v + d * lv) return d * v;
         }
         return NAN;
     }
 };
+
+// Fill P (all threads of the block call it; result valid after it returns).
+__device__ void predraw(PreDraws* P, const ThetaD& th, int64_t T, uint64_t seed, uint64_t series,
+                        uint64_t traj)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double Td = (double)T;
+    const double alpha = 0.5 * Td < 1.0 ? 0.5 * Td + 1.0 : 0.5 * Td;
+    if (warp == 0) {
+        const u64x4 w = philox_block(seed, series, traj, STREAM_THETA, (uint64_t)(lane >> 2));
+        P->u[lane] = u01_53(w.w[lane & 3]);
+    } else if (warp == 1 && lane == 0) {
+        const u64x4 w = philox_block(seed, series, traj, STREAM_THETA, (uint64_t)(NPRE >> 2));
+        P->u[NPRE] = u01_53(w.w[0]);
+    } else if (warp == 2 && lane == 0) {
+        P->gd = alpha - 1.0 / 3.0;
+        P->gc = 1.0 / sqrt(9.0 * P->gd);
+    } else if (warp == 3 && lane == 0) {
+        P->sxi = sqrt(th.su2 / Td);
+        P->lphi = log(1.0 - th.phi * th.phi);
+    } else if (warp == 4 && lane == 0) {
+        const double phi = th.phi;
+        const double w0 = 1.0 - phi * phi, w1 = (1.0 - phi) * (1.0 - phi);
+        const double den = w0 + (Td - 1.0) * w1;
+        P->smu = sqrt(den / th.se2);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const double lu = log(P->u[lane]);
+        P->lu[lane] = lu;
+        P->sq[lane] = sqrt(-2.0 * lu);
+    } else if (warp == 1) {
+        P->cs[lane] = cospi(2.0 * P->u[lane + 1]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const double z = P->sq[lane] * P->cs[lane];
+        const double v = 1.0 + P->gc * z;
+        P->bm[lane] = z;
+        P->v[lane] = v;
+        P->v3[lane] = v * v * v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const double v3 = P->v3[lane];
+        P->lv3[lane] = P->v[lane] > 0.0 ? log(v3) : 0.0;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Mixed path: the same sweep in FP32.  Stream positions are consumed in the
+// same order, with 23-bit uniforms (k + 1/2) 2^-23 of the same Philox words;
+// theta is kept FP32-valued, so that the mixed trajectory kernel's constants
+// follow from it in FP32 / double-float arithmetic.  A rounding of theta to
+// FP32 after each draw moves it by ~1e-7 relative, far below its posterior
+// spread.  Marsaglia & Tsang's acceptance value
+//   r = z^2/2 + d (1 - v + ln v),  v = (1 + x)^3,  x = c z,  c^2 = 1/(9 d),
+// is taken for |x| < 1/4 from its expansion: with ln v = 3 ln(1 + x) the
+// terms of order x^2 cancel against z^2/2 exactly and
+//   r = 3 d sum_{k>=4} (-1)^(k+1) x^k / k
+// (in FP32 the direct form loses everything to cancellation when d ~ T/2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float mt_accept_value(float z, float c, float d)
+{
+    const float x = c * z;
+    if (fabsf(x) < 0.25f) {
+        // Horner over k = 20 .. 4 of (-1)^(k+1) x^(k-4) / k
+        float sacc = 0.0f;
+#pragma unroll
+        for (int k = 20; k >= 4; --k) sacc = fmaf(sacc, x, ((k & 1) ? 1.0f : -1.0f) / (float)k);
+        const float x2 = x * x;
+        return 3.0f * d * (x2 * x2) * sacc;
+    }
+    const float v = (1.0f + x) * (1.0f + x) * (1.0f + x);
+    return 0.5f * z * z + d - d * v + d * (3.0f * log1pf(x));
+}
+
+__device__ __forceinline__ float u01_23_at(uint64_t seed, uint64_t series, uint64_t traj, int i)
+{
+    const u64x4 w = philox_block(seed, series, traj, STREAM_THETA, (uint64_t)(i >> 2));
+    return u01_23(w.w[i & 3]);
+}
+
+// The variates of stream positions 0..31 in the registers of one warp (lane
+// i holds position i) and the walk over them: a position the warp holds is
+// read by a shuffle (the position is the same in every lane), any other is
+// computed directly.
+struct WarpDrawsF {
+    uint64_t seed, series, traj;
+    float u, lu, z, v, g;   // this lane's position: uniform, log, normal, candidate
+    int acc;                // candidate at this position accepted
+    float gc, gd;           // Marsaglia-Tsang c, d of the sweep's gamma shape
+    float alpha_pre;
+    int pos;
+    __device__ void fill(int64_t T)
+    {
+        const int lane = threadIdx.x & 31;
+        const float Tf = (float)T;
+        alpha_pre = 0.5f * Tf < 1.0f ? 0.5f * Tf + 1.0f : 0.5f * Tf;
+        gd = alpha_pre - 1.0f / 3.0f;
+        gc = 1.0f / sqrtf(9.0f * gd);
+        u = u01_23_at(seed, series, traj, lane);
+        lu = logf(u);
+        const float un = __shfl_down_sync(0xffffffffu, u, 1);  // position i+1 (lane 31: unused)
+        z = sqrtf(-2.0f * lu) * cospif(2.0f * un);
+        v = 1.0f + gc * z;
+        g = gd * (v * v * v);
+        const float lu2 = __shfl_down_sync(0xffffffffu, lu, 2);  // position i+2
+        acc = (lane < 30 && v > 0.0f && lu2 < mt_accept_value(z, gc, gd)) ? 1 : 0;
+        pos = 0;
+    }
+    __device__ float uni(int i) const
+    {
+        const float r = __shfl_sync(0xffffffffu, u, i & 31);
+        return i < 32 ? r : u01_23_at(seed, series, traj, i);
+    }
+    __device__ float loguni(int i) const
+    {
+        const float r = __shfl_sync(0xffffffffu, lu, i & 31);
+        return i < 32 ? r : logf(uni(i));
+    }
+    __device__ float normal()
+    {
+        const int i = pos;
+        pos += 2;
+        const float r = __shfl_sync(0xffffffffu, z, i & 31);
+        return i < 31 ? r : sqrtf(-2.0f * loguni(i)) * cospif(2.0f * uni(i + 1));
+    }
+    __device__ float gamma(float alpha)
+    {
+        if (alpha < 1.0f) {
+            const float gg = gamma1(alpha + 1.0f);
+            const float uu = uni(pos++);
+            return gg * powf(uu, 1.0f / alpha);
+        }
+        return gamma1(alpha);
+    }
+    __device__ float gamma1(float alpha)
+    {
+        const bool pre = alpha == alpha_pre;
+        const float d = pre ? gd : alpha - 1.0f / 3.0f;
+        const float c = pre ? gc : 1.0f / sqrtf(9.0f * d);
+        for (int it = 0; it < 1000; ++it) {
+            const int i = pos;
+            if (pre && i < 30) {
+                const float vi = __shfl_sync(0xffffffffu, v, i);
+                const int ai = __shfl_sync(0xffffffffu, acc, i);
+                const float gi = __shfl_sync(0xffffffffu, g, i);
+                pos += vi > 0.0f ? 3 : 2;
+                if (ai) return gi;
+                continue;
+            }
+            const float zz = normal();
+            const float vv = 1.0f + c * zz;
+            if (vv <= 0.0f) continue;
+            const float l = loguni(pos++);
+            if (l < mt_accept_value(zz, c, d)) return d * vv * vv * vv;
+        }
+        return NAN;
+    }
+};
+
+// One sweep in FP32 (every lane of one warp calls it uniformly); theta as
+// floats in/out; x0 = h_1 - mu; S the statistics.
+__device__ void gibbs_draws_f(const float (&S)[NSTAT], float x0, int64_t T, float (&th)[5],
+                              WarpDrawsF& st, int mask, int* acc_out)
+{
+    const float Tf = (float)T;
+    const float phi = th[0], mu0 = th[1], xi0 = th[2];
+    float se2 = th[3], su2 = th[4];
+    float xi = xi0, mu = mu0, ph = phi;
+    if (mask & 1) xi = xi0 + S[0] / Tf + sqrtf(su2 / Tf) * st.normal();
+    if (mask & 2) {
+        const float dxi = xi - xi0;
+        const float ss = S[1] - 2.0f * dxi * S[0] + Tf * dxi * dxi;
+        const float g = st.gamma(0.5f * Tf);
+        if (g > 0.0f && ss > 0.0f) su2 = 0.5f * ss / g;
+    }
+    if (mask & 4) {
+        const float w0 = 1.0f - phi * phi, w1 = (1.0f - phi) * (1.0f - phi);
+        const float den = w0 + (Tf - 1.0f) * w1;
+        const float m = mu0 + (w0 * x0 + (1.0f - phi) * S[6]) / den;
+        mu = m + st.normal() / sqrtf(den / se2);
+    }
+    const float dmu = mu - mu0;
+    if (mask & 8) {
+        const float a = x0 - dmu, om = 1.0f - phi;
+        const float Q = (1.0f - phi * phi) * a * a + S[7] - 2.0f * om * dmu * S[6] +
+                        (Tf - 1.0f) * om * om * dmu * dmu;
+        const float g = st.gamma(0.5f * Tf);
+        if (g > 0.0f && Q > 0.0f) se2 = 0.5f * Q / g;
+    }
+    int acc = 0;
+    if (mask & 16) {
+        const float num = S[5] - dmu * (S[2] + S[3]) + (Tf - 1.0f) * dmu * dmu;
+        const float Xm = S[2] - x0;
+        const float D = S[4] - 2.0f * dmu * Xm + (Tf - 2.0f) * dmu * dmu;
+        if (T >= 3 && D > 0.0f) {
+            const float m = num / D, sd = sqrtf(se2 / D);
+            float prop = NAN;
+            for (int it = 0; it < 1000; ++it) {
+                const float c = m + sd * st.normal();
+                if (c > -1.0f && c < 1.0f) {
+                    prop = c;
+                    break;
+                }
+            }
+            const float lu = st.loguni(st.pos++);
+            if (prop == prop) {
+                const float lr = 0.5f * logf(1.0f - prop * prop) - 0.5f * logf(1.0f - phi * phi);
+                if (lu < lr) {
+                    ph = prop;
+                    acc = 1;
+                }
+            }
+        }
+    }
+    th[0] = ph;
+    th[1] = mu;
+    th[2] = xi;
+    th[3] = se2;
+    th[4] = su2;
+    *acc_out = acc;
+}
+
+// MixedTheta of an FP32-valued theta in FP32 / double-float arithmetic.
+__device__ MixedTheta mixed_theta_f(const float (&t)[5])
+{
+    const float phi = t[0], mu = t[1], xi = t[2], se2 = t[3], su2 = t[4];
+    MixedTheta m;
+    m.phi = phi;
+    m.iu = 1.0f / su2;
+    m.ie = 1.0f / se2;
+    m.c0 = m.iu + (1.0f + phi * phi) * m.ie;
+    m.c1 = -phi * m.ie;
+    m.cmu = -mu * 1.4426950408889634f;
+    m.mu = ff{mu, 0.0f};
+    m.ximu = two_sum(xi, mu);
+    m.phi_ff = ff{phi, 0.0f};
+    // 1/(2 s^2) in double-float: quotient and its exact FMA residual
+    const float hu = 0.5f / su2, he = 0.5f / se2;
+    m.hu = ff{hu, fmaf(-hu, su2, 0.5f) / su2};
+    m.he = ff{he, fmaf(-he, se2, 0.5f) / se2};
+    return m;
+}
 
 // Per-site contributions, FP64 state.
 __device__ __forceinline__ void site_stats_d(const double* h, const double* lnrv, int64_t t,
@@ -117,17 +395,17 @@ __device__ __forceinline__ void site_stats_f(const float2* h, const float2* lr, 
     if (t >= 1 && t + 1 < T) ff_acc(s[4], ff_mul(x, x));
 }
 
-__device__ void gibbs_draws(const double (&S)[NSTAT], double x0, int64_t T, double* theta,
-                            double* theta_out, uint64_t seed, uint64_t series, uint64_t traj,
-                            int mask, int* phi_acc)
+// The sweep itself (called by every lane of one warp, uniformly).
+__device__ void gibbs_draws(const double (&S)[NSTAT], double x0, int64_t T, const ThetaD& th,
+                            double* theta, double* theta_out, const PreDraws* P, uint64_t seed,
+                            uint64_t series, uint64_t traj, int mask, int* phi_acc)
 {
-    ThetaD th = load_theta(theta);
-    Stream st{seed, series, traj, 0, {}, 4};
     const double Td = (double)T;
+    WalkStream st{P, seed, series, traj, 0, 0.5 * Td < 1.0 ? 0.5 * Td + 1.0 : 0.5 * Td};
     const double xi0 = th.xi, mu0 = th.mu, phi = th.phi;
     double xi = xi0, su2 = th.su2, mu = mu0, se2 = th.se2, ph = phi;
     // xi
-    if (mask & 1) xi = xi0 + S[0] / Td + sqrt(su2 / Td) * st.normal();
+    if (mask & 1) xi = xi0 + S[0] / Td + P->sxi * st.normal();
     // s_u^2: sum (q - dxi)^2
     if (mask & 2) {
         const double dxi = xi - xi0;
@@ -140,7 +418,7 @@ __device__ void gibbs_draws(const double (&S)[NSTAT], double x0, int64_t T, doub
         const double w0 = 1.0 - phi * phi, w1 = (1.0 - phi) * (1.0 - phi);
         const double den = w0 + (Td - 1.0) * w1;
         const double m = mu0 + (w0 * x0 + (1.0 - phi) * S[6]) / den;
-        mu = m + st.normal() / sqrt(den / se2);
+        mu = m + st.normal() / P->smu;
     }
     const double dmu = mu - mu0;
     // s_eta^2
@@ -169,7 +447,7 @@ __device__ void gibbs_draws(const double (&S)[NSTAT], double x0, int64_t T, doub
             }
             const double u = st.u01();
             if (prop == prop) {
-                const double lr = 0.5 * log(1.0 - prop * prop) - 0.5 * log(1.0 - phi * phi);
+                const double lr = 0.5 * log(1.0 - prop * prop) - 0.5 * P->lphi;
                 if (log(u) < lr) {
                     ph = prop;
                     acc = 1;
@@ -177,14 +455,16 @@ __device__ void gibbs_draws(const double (&S)[NSTAT], double x0, int64_t T, doub
             }
         }
     }
-    theta[0] = ph;
-    theta[1] = mu;
-    theta[2] = xi;
-    theta[3] = se2;
-    theta[4] = su2;
-    if (theta_out)
-        for (int i = 0; i < 5; ++i) theta_out[i] = theta[i];
-    if (phi_acc) *phi_acc = acc;
+    if ((threadIdx.x & 31) == 0) {
+        theta[0] = ph;
+        theta[1] = mu;
+        theta[2] = xi;
+        theta[3] = se2;
+        theta[4] = su2;
+        if (theta_out)
+            for (int i = 0; i < 5; ++i) theta_out[i] = theta[i];
+        if (phi_acc) *phi_acc = acc;
+    }
 }
 
 // Block sum of NSTAT double-float values in a fixed order (butterfly in each
@@ -208,40 +488,16 @@ __device__ __forceinline__ void block_sum_ff(ff (&s)[NSTAT], float2 (*red)[NSTAT
     __syncthreads();
 }
 
-// Statistics pass + last-block draws.  `cur` selects the state buffer.  The
-// mixed path keeps every per-site and cross-block sum in double-float (FP32
-// arithmetic; the FP64 pipe of this GPU is slow) and converts the totals to
-// FP64 once for the scalar draws.
-template <bool MIXED>
+// FP64 path: statistics pass + last-block draws.  `cur` selects the state
+// buffer.
 __global__ void __launch_bounds__(256) k_gibbs(GibbsArgs A)
 {
     __shared__ double red[32];
-    __shared__ float2 redf[32][NSTAT];
-    __shared__ ff s_c[3];
     __shared__ int s_last;
     const int* curp = A.cur;
     const int cur = curp ? *(volatile int*)curp : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (MIXED) {
-        if (threadIdx.x == 0) {
-            const ThetaD th = load_theta(A.theta);
-            s_c[0] = ff_from_double(th.xi);
-            s_c[1] = ff_from_double(th.mu);
-            s_c[2] = ff_from_double(th.phi);
-        }
-        __syncthreads();
-        const ff xi = s_c[0], mu = s_c[1], phi = s_c[2];
-        const float2* h = cur ? A.h1f : A.h0f;
-        ff s[NSTAT];
-        for (int i = 0; i < NSTAT; ++i) s[i] = ff{0.f, 0.f};
-        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
-            site_stats_f(h, A.lr_f, t, A.T, xi, mu, phi, s);
-        block_sum_ff(s, redf);
-        float2* pf = reinterpret_cast<float2*>(A.partials);
-        if (threadIdx.x == 0)
-            for (int i = 0; i < NSTAT; ++i)
-                pf[(int64_t)blockIdx.x * NSTAT + i] = make_float2(s[i].hi, s[i].lo);
-    } else {
+    {
         const ThetaD th = load_theta(A.theta);
         double S[NSTAT];
         for (int i = 0; i < NSTAT; ++i) S[i] = 0.0;
@@ -260,48 +516,118 @@ __global__ void __launch_bounds__(256) k_gibbs(GibbsArgs A)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double tot[NSTAT];
-    if (MIXED) {
-        const float2* pf = reinterpret_cast<const float2*>(A.partials);
+    // FP64 totals, the FP64 sweep with its variates precomputed
+    __shared__ PreDraws s_pre;
+    __shared__ double s_tot[NSTAT];
+    const ThetaD th = load_theta(A.theta);
+    for (int i = 0; i < NSTAT; ++i) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            v += __ldcg(A.partials + (int64_t)b * NSTAT + i);
+        const double t = block_sum(v, red);
+        if (threadIdx.x == 0) s_tot[i] = t;
+    }
+    predraw(&s_pre, th, A.T, A.seed, A.series, A.traj);  // ends with a barrier
+    if (threadIdx.x < 32) {
+        double tot[NSTAT];
+        for (int i = 0; i < NSTAT; ++i) tot[i] = s_tot[i];
+        const double x0 = (cur ? A.h1d : A.h0d)[0] - th.mu;
+        gibbs_draws(tot, x0, A.T, th, A.theta, A.theta_out, &s_pre, A.seed, A.series, A.traj,
+                    A.mask, A.phi_acc);
+        if (threadIdx.x == 0) *A.counter = 0u;
+    }
+    __threadfence();
+}
+
+// Mixed path: the statistics in double-float (FP32 arithmetic; the FP64 pipe
+// of this GPU is slow) from (hi, lo) state, centred on the constants of
+// theta_f; the last block combines them, one warp per statistic, and warp 0
+// takes the sweep in FP32 (variates in registers, no block barriers), writes
+// theta (FP32-valued) and refreshes theta_f.
+constexpr int kGibbsMixedBlock = 256;
+__global__ void __launch_bounds__(kGibbsMixedBlock, 2) k_gibbs_mixed(GibbsArgs A)
+{
+    __shared__ float2 redf[kGibbsMixedBlock / 32][NSTAT];
+    __shared__ float2 s_tot[NSTAT];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cur = A.cur ? *(volatile int*)A.cur : 0;
+    const float2* h = cur ? A.h1f : A.h0f;
+    const MixedTheta& m0 = *A.theta_f;
+    const ff xi = ff_sub(m0.ximu, m0.mu), mu = m0.mu, phi = m0.phi_ff;
+    {
         ff s[NSTAT];
-        for (int i = 0; i < NSTAT; ++i) {
-            s[i] = ff{0.f, 0.f};
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-                const float2 v = __ldcg(pf + (int64_t)b * NSTAT + i);
-                s[i] = ff_add(s[i], ff{v.x, v.y});
-            }
-        }
+        for (int i = 0; i < NSTAT; ++i) s[i] = ff{0.f, 0.f};
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 4
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
+            site_stats_f(h, A.lr_f, t, A.T, xi, mu, phi, s);
         block_sum_ff(s, redf);
-        for (int i = 0; i < NSTAT; ++i) tot[i] = ff_to_double(s[i]);
-    } else {
-        for (int i = 0; i < NSTAT; ++i) {
-            double v = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-                v += __ldcg(A.partials + (int64_t)b * NSTAT + i);
-            tot[i] = block_sum(v, red);
-        }
+        float2* pf = reinterpret_cast<float2*>(A.partials);
+        if (threadIdx.x == 0)
+            for (int i = 0; i < NSTAT; ++i)
+                pf[(int64_t)blockIdx.x * NSTAT + i] = make_float2(s[i].hi, s[i].lo);
     }
     if (threadIdx.x == 0) {
-        *A.counter = 0u;
-        const ThetaD th = load_theta(A.theta);
-        double x0;
-        if (MIXED) {
-            const float2 v = (cur ? A.h1f : A.h0f)[0];
-            x0 = ((double)v.x + (double)v.y) - th.mu;
-        } else {
-            x0 = (cur ? A.h1d : A.h0d)[0] - th.mu;
-        }
-        gibbs_draws(tot, x0, A.T, A.theta, A.theta_out, A.seed, A.series, A.traj, A.mask,
-                    A.phi_acc);
-        if (A.theta_f) *A.theta_f = mixed_theta(load_theta(A.theta));
         __threadfence();
+        s_last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // warp w sums statistic w over the blocks (NSTAT == warps per block)
+    static_assert(NSTAT == kGibbsMixedBlock / 32, "one warp per statistic");
+    {
+        const float2* pf = reinterpret_cast<const float2*>(A.partials);
+        ff acc = {0.f, 0.f};
+        const int nb = (int)gridDim.x;
+#pragma unroll 4
+        for (int b = lane; b < nb; b += 32) {
+            const float2 v = __ldcg(pf + (int64_t)b * NSTAT + warp);
+            acc = ff_add(acc, ff{v.x, v.y});
+        }
+        acc = warp_sum_ff(acc);
+        if (lane == 0) s_tot[warp] = make_float2(acc.hi, acc.lo);
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    float tot[NSTAT];
+    for (int i = 0; i < NSTAT; ++i) tot[i] = s_tot[i].x + s_tot[i].y;
+    // theta rounded to FP32 (exact after the first sweep): one conversion per
+    // lane, then shared across the warp
+    const float mine = lane < 5 ? (float)A.theta[lane] : 0.0f;
+    float th[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) th[k] = __shfl_sync(0xffffffffu, mine, k);
+    const float2 hv = h[0];
+    const ff x0 = ff_sub(ff{hv.x, hv.y}, mu);
+    WarpDrawsF st;
+    st.seed = A.seed;
+    st.series = A.series;
+    st.traj = A.traj;
+    st.fill(A.T);
+    int acc = 0;
+    gibbs_draws_f(tot, x0.hi + x0.lo, A.T, th, st, A.mask, &acc);
+    if (lane < 5) {
+        float v = th[0];
+#pragma unroll
+        for (int k = 1; k < 5; ++k)
+            if (lane == k) v = th[k];
+        A.theta[lane] = (double)v;
+        if (A.theta_out) A.theta_out[lane] = (double)v;
+    }
+    if (lane == 0) {
+        if (A.phi_acc) *A.phi_acc = acc;
+        *A.theta_f = mixed_theta_f(th);
+        *A.counter = 0u;
+    }
+    __threadfence();
 }
 
 }  // namespace
 
-// About 4 sites per thread, up to 8 blocks of 256 per SM: the statistics pass
-// is bound by load latency, so it wants many threads in flight.
+// FP64 path: about 4 sites per thread, up to 8 blocks of 256 per SM.  Mixed
+// path: one wave of two blocks of 256 per SM (loads of four sites in flight).
 int gibbs_grid(int64_t T)
 {
     int64_t g = (T + 1023) / 1024;
@@ -309,12 +635,18 @@ int gibbs_grid(int64_t T)
     if (g < 1) g = 1;
     return (int)g;
 }
+static int gibbs_grid_mixed(int64_t T)
+{
+    int64_t g = (T + 2047) / 2048;
+    if (g > 152 * 2) g = 152 * 2;
+    if (g < 1) g = 1;
+    return (int)g;
+}
 
 cudaError_t launch_gibbs(const GibbsArgs& a, bool mixed, cudaStream_t st)
 {
-    const int g = gibbs_grid(a.T);
-    if (mixed) k_gibbs<true><<<g, 256, 0, st>>>(a);
-    else k_gibbs<false><<<g, 256, 0, st>>>(a);
+    if (mixed) k_gibbs_mixed<<<gibbs_grid_mixed(a.T), kGibbsMixedBlock, 0, st>>>(a);
+    else k_gibbs<<<gibbs_grid(a.T), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ struct GibbsArgs {
     double* partials;    // [grid * 8]
     unsigned* counter;
     int* phi_acc;        // optional
-    MixedTheta* theta_f; // optional: refreshed from the new theta (mixed path)
+    MixedTheta* theta_f; // mixed path: the current theta's constants, read and refreshed
 };
 
 int gibbs_grid(int64_t T);

@@ -23,7 +23,9 @@
 //   AR_t = e_{t-1} - phi e_t,  e_t = x_{t+1} - phi x_t  (e_{T-1} = 0,
 //   e_{-1} = (1 - phi^2) x_0),  a' = y^2/2 e^{-mu},  c' = lnRV - xi - mu,
 // the gradient of S written with the AR innovations e_t (equal to eq. (7)'s
-// stencil (1+phi^2) x_t - phi (x_{t-1} + x_{t+1}) inside the series).
+// stencil (1+phi^2) x_t - phi (x_{t-1} + x_{t+1}) inside the series).  The
+// FP64 kernel uses this innovation form; the mixed kernel the equivalent
+// three-point form with ghost neighbours (see mixed_steps).
 #include <cmath>
 
 #include "rsv_device.cuh"
@@ -417,7 +419,7 @@ __device__ float2 g_exptab[32];
 
 // Per-block constants of the leapfrog of one segment.
 struct MixedConst {
-    float phi, st0, iu, ie, cmu, dt;
+    float phi, c0, c1, cmu, dt;
     int la;        // slot of the series' last site in this thread (or out of [0, J))
     bool first;    // this thread holds the series' first site in slot 0
 };
@@ -441,15 +443,19 @@ __device__ __forceinline__ void cupd2(float2& hi, float2& lo, float2 c, float2 u
 
 // n_md leapfrog steps (eqs. (6)-(8)) with the two half steps of consecutive
 // steps merged: x += dt/2 p;  n_md times { p -= dt F(x); x += (dt, or dt/2 at
-// the end) p }.  A thread's run of J sites is held as P = J/2 pairs
-// (j, j + P): the two halves of the run advance side by side in the two lanes
-// of packed FP32 instructions.  Site by site the innovation
-// e_j = x_{j+1} - phi x_j, the force and both updates are fused: a site's
-// update feeds no later site's force of the same step (that needs only e_j,
-// already taken).  The seams: the lower half's last site takes x_P from before
-// the step, and the upper half's chain starts from e_{P-1}.
-// EDGE: some thread of the warp ends a series before its last slot; e = 0 at
-// that slot (the series' end condition e_{T-1} = 0) by a select.
+// the end) p }.  The force of eq. (7) is taken in its three-point form
+//   F_t = c0 x_t + c1 (x_{t-1} + x_{t+1}) + k_t - a_t e^{-h_t},
+//   c0 = 1/s_u^2 + (1+phi^2)/s_eta^2,  c1 = -phi/s_eta^2,
+// with a ghost neighbour phi x_t beyond either end of a series, which gives
+// the end rows (x_0 - phi x_1)/s_eta^2, (x_{T-1} - phi x_{T-2})/s_eta^2 and,
+// for T = 1, (1 - phi^2) x_0/s_eta^2.
+// A thread's run of J sites is held as P = J/2 pairs (j, j + P): the two
+// halves of the run advance side by side in the two lanes of packed FP32
+// instructions.  Site by site the force and both updates are fused; the left
+// neighbour's value from before the step is carried, the upper half's last
+// site takes x_P from before the step.
+// EDGE: some thread of the warp ends a series before its last slot; the ghost
+// replaces the right neighbour there by a select.
 // s_ak: float4 [P][NT] = (-a_p, -a_{p+P}, k_p, k_{p+P}); s_dm: float2 [P][NT].
 template <int J, bool MASS, bool EDGE>
 __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J / 2],
@@ -460,37 +466,34 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
 {
     constexpr int P = J / 2;
     const int NT = blockDim.x, tid = threadIdx.x;
-    const float2 nphi = f2(-c.phi, -c.phi), iu = f2(c.iu, c.iu), ie = f2(c.ie, c.ie);
+    const float2 c0 = f2(c.c0, c.c0), c1 = f2(c.c1, c.c1);
     const float2 nl2e = f2(-kLog2e, -kLog2e), cmu = f2(c.cmu, c.cmu);
     const float2 ndt = f2(-c.dt, -c.dt);
     for (int k = 0; k < n_md; ++k) {
         float xL, xR;
         exchange(X[0].x, X[P - 1].y, xL, xR, s_edge + par * 2 * nw, nw);
         par ^= 1;
+        if (c.first) xL = c.phi * X[0].x;
+        if (!EDGE && c.la == J - 1) xR = c.phi * X[P - 1].y;
         const float xP = X[0].y;  // x_P before the step
-        float2 eprev;
-        eprev.x = c.first ? c.st0 * X[0].x : fmaf(-c.phi, xL, X[0].x);
-        eprev.y = fmaf(-c.phi, X[P - 1].x, xP);  // e_{P-1}
+        float2 prev = f2(xL, X[P - 1].x);  // left neighbours of pair 0, before the step
         const float hs = (k + 1 < n_md) ? 1.0f : 0.5f;
         const float2 cx = f2(hs * c.dt, hs * c.dt);
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const float4 ak = s_ak[q * NT + tid];
-            const float2 nxt = (q + 1 < P) ? X[q + 1] : f2(xP, xR);
-            float2 e = fma2(nphi, X[q], nxt);
+            const float2 xq = X[q];
+            float2 nxt = (q + 1 < P) ? X[q + 1] : f2(xP, xR);
             if (EDGE) {
-                if (q == c.la) e.x = 0.0f;
-                if (q + P == c.la) e.y = 0.0f;
-            } else if (q == P - 1) {
-                if (c.la == J - 1) e.y = 0.0f;
+                if (q == c.la) nxt.x = c.phi * xq.x;
+                if (q + P == c.la) nxt.y = c.phi * xq.y;
             }
-            const float2 ar = fma2(nphi, e, eprev);
-            eprev = e;
-            float2 f = fma2(iu, X[q], f2(ak.z, ak.w));
-            f = fma2(ie, ar, f);
+            float2 f = fma2(c0, xq, f2(ak.z, ak.w));
+            f = fma2(c1, add2(prev, nxt), f);
             // (y^2/2) e^{-h} = a 2^{-(x + mu) log2 e}: a small exponent argument
-            const float2 t = fma2(nl2e, X[q], cmu);
+            const float2 t = fma2(nl2e, xq, cmu);
             f = fma2(f2(ak.x, ak.y), f2(ex2_approx(t.x), ex2_approx(t.y)), f);
+            prev = xq;
             cupd2(PH[q], PL[q], ndt, f);
             float2 cq = cx;
             if (MASS) {
@@ -591,17 +594,16 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             __syncwarp();
             const MixedTheta& mt = s_mt[warp];
             mc.phi = mt.phi;
-            mc.st0 = mt.st0;
-            mc.ie = mt.ie;
-            mc.iu = mt.iu;
+            mc.c0 = mt.c0;
+            mc.c1 = mt.c1;
             mc.cmu = mt.cmu;
             mc.dt = dt;
             mc.la = v.n - 1 - base;
             mc.first = v.first;
             const int64_t off = v.si.off, wlo = v.g.wlo;
             const float2* hin = v.cur ? A.h1f : A.h0f;
-            // pass 1: site constants, x, p -> shared memory
-#pragma unroll 1
+            // pass 1: site constants, x, p -> shared memory (two quads in flight)
+#pragma unroll 2
             for (int q = 0; q < J / 4; ++q) {
                 float z[4];
                 if (A.p_in) {
@@ -645,11 +647,14 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                 }
             }
             __syncthreads();
-            // pass 2: H at the start over the owned sites (needs the next x)
-            HParts acc;
-            hparts_zero(acc);
-#pragma unroll 1
+            // pass 2: H at the start over the owned sites (needs the next x);
+            // even and odd slots in separate accumulators, two sites in flight
+            HParts acc2[2];
+            hparts_zero(acc2[0]);
+            hparts_zero(acc2[1]);
+#pragma unroll 2
             for (int j = 0; j < J; ++j) {
+                HParts& acc = acc2[j & 1];
                 const int64_t sg = wlo + base + j;
                 if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
                 const ff x = {s_xh[j * NT + tid], s_xl[j * NT + tid]};
@@ -667,7 +672,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     has_stat = true;
                 }
             }
-            h0 = hparts_total(acc, mt);
+            h0 = ff_add(hparts_total(acc2[0], mt), hparts_total(acc2[1], mt));
             // registers <- shared memory, then the first half step of eq. (6)
 #pragma unroll
             for (int q = 0; q < P; ++q) {
@@ -711,11 +716,13 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
         const int base = v.base * J;
         const MixedTheta& mt = s_mt[warp];
         const int64_t off = v.si.off, wlo = v.g.wlo;
-        HParts acc;
-        hparts_zero(acc);
+        HParts acc2[2];
+        hparts_zero(acc2[0]);
+        hparts_zero(acc2[1]);
         double stat1 = 0.0;
-#pragma unroll 1
+#pragma unroll 2
         for (int j = 0; j < J; ++j) {
+            HParts& acc = acc2[j & 1];
             const int64_t sg = wlo + base + j;
             if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
             const ff x = {s_xh[j * NT + tid], s_xl[j * NT + tid]};
@@ -732,7 +739,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                 stat1 = 0.5 * (1.0 - v.th.phi * v.th.phi) / v.th.se2 * a1 * a1;
             }
         }
-        ff dh = ff_sub(hparts_total(acc, mt), h0);
+        ff dh = ff_sub(ff_add(hparts_total(acc2[0], mt), hparts_total(acc2[1], mt)), h0);
         if (has_stat) dh = ff_add(dh, ff_from_double(stat1 - stat0));
         dh = warp_sum_ff(dh);
         if (lane == 0) s_wpf[warp] = make_float2(dh.hi, dh.lo);

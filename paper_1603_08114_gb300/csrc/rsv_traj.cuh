@@ -56,16 +56,19 @@ struct Plan {
 // with one lane active, so these are derived once per series (mixed_theta, by
 // a small kernel or the theta update) instead of inside the trajectory kernel.
 struct MixedTheta {
-    float phi, st0, iu, ie, cmu;  // leapfrog: phi, 1 - phi^2, 1/s_u^2, 1/s_eta^2, -mu log2 e
+    // leapfrog: phi, c0 = 1/s_u^2 + (1+phi^2)/s_eta^2, 1/s_u^2, 1/s_eta^2,
+    // -mu log2 e; c1 = -phi/s_eta^2 (the force's stencil weights)
+    float phi, c0, iu, ie, cmu;
     ff mu, ximu, phi_ff, hu, he;  // dH: mu, xi + mu, phi, 1/(2 s_u^2), 1/(2 s_eta^2)
-    float pad;
+    float c1;
 };
 static_assert(sizeof(MixedTheta) == 64, "MixedTheta is 16 floats");
 __device__ __forceinline__ MixedTheta mixed_theta(const ThetaD& th)
 {
     MixedTheta m;
     m.phi = (float)th.phi;
-    m.st0 = 1.0f - m.phi * m.phi;
+    m.c0 = (float)(1.0 / th.su2 + (1.0 + th.phi * th.phi) / th.se2);
+    m.c1 = (float)(-th.phi / th.se2);
     m.iu = (float)(1.0 / th.su2);
     m.ie = (float)(1.0 / th.se2);
     m.cmu = (float)(-th.mu * 1.4426950408889634);  // exponent of e^{-mu}
@@ -74,7 +77,6 @@ __device__ __forceinline__ MixedTheta mixed_theta(const ThetaD& th)
     m.phi_ff = ff_from_double(th.phi);
     m.hu = ff_from_double(0.5 / th.su2);
     m.he = ff_from_double(0.5 / th.se2);
-    m.pad = 0.0f;
     return m;
 }
 

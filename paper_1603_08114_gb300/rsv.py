@@ -69,7 +69,7 @@ def lib():
                                     _U64, _U64, _I64, _INT, _P, _P, _P, _P, _I64, _INT, _P, _P]
         L.rsv_draw_momenta.argtypes = [_P, _U64, _U64, _U64, _I64, _P, _INT, _P, _P]
         L.rsv_ess.argtypes = [_P, _P, _I64, _I64, _P, _P]
-        L.rsv_gibbs_theta.argtypes = [_P, _P, _P, _I64, _P, _U64, _U64, _U64, _INT, _P, _P]
+        L.rsv_gibbs_theta.argtypes = [_P, _P, _P, _I64, _P, _U64, _U64, _U64, _INT, _INT, _P, _P]
         L.rsv_plan_create.argtypes = [_P, _P, _I64, _INT, _INT, _INT, ctypes.POINTER(_P)]
         L.rsv_plan_destroy.argtypes = [_P]
         L.rsv_plan_destroy.restype = None
@@ -256,13 +256,13 @@ def rsv_stats(ctx: Context, reset: bool = True):
 
 
 def rsv_gibbs_theta(ctx: Context, h, lnrv, theta_dev, seed: int, series: int = 0, traj: int = 0,
-                    mask: int = 31, phi_acc_out=None):
+                    mask: int = 31, phi_acc_out=None, prec: str = "fp64"):
     """One theta Gibbs sweep in place on theta_dev (device FP64 [5]) given h."""
     T = h.numel()
     _check(lib().rsv_gibbs_theta(ctx.handle, _ptr(h, torch.float64, T, "h"),
                                  _ptr(lnrv, torch.float64, T, "lnrv"), T,
                                  _ptr(theta_dev, torch.float64, 5, "theta"), int(seed),
-                                 int(series), int(traj), int(mask),
+                                 int(series), int(traj), int(mask), _prec(prec),
                                  _ptr(phi_acc_out, torch.int32, 1, "phi_acc_out"), _stream()))
 
 
