@@ -43,10 +43,16 @@ UNIT = "site-updates/s"
 THETA_NAMES = ("phi", "mu", "xi", "sig_eta2", "sig_u2")
 WORKLOAD = ("rsv-hmc single chain T=2^20, theta sampled, 200 trajectories per step; "
             "learned mass (tuned dtau, n_md) vs identity 100 x 0.005")
-# Algorithmic instructions per site and leapfrog step of the mixed kernel on the
-# FP32/issue pipes: innovation (1), AR (1), force (3) + exponent argument (1),
-# special-function exp2 (1), compensated p update (4), compensated h update (4).
-OPS_PER_SITE_STEP_MIXED = 15
+# Algorithmic FP32 operations per site and leapfrog step of the mixed kernel:
+# the three-point force (neighbour sum 1, two stencil FMAs 2, exponent argument
+# 1, the y^2/2 e^-h term 1), the compensated p update (4) and the compensated
+# h update (4).  The exp2 itself runs on the special-function unit.
+OPS_PER_SITE_STEP_MIXED = 13
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_traj_mixed launch of
+# the headline workload (learned mass, T = 2^20), from the capture summarised in
+# profiles/k_traj_mixed_T2p20.md (the inputs are read once per launch, so the
+# figure does not depend on n_md); valid for the kernel revision it was taken on.
+TRAFFIC = {"kernel_rev": 3, "bytes": 25256448 + 256}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -261,6 +267,8 @@ def run_ours(args):
         _barrier(ws)
         if clocks:
             clocks.__enter__()
+        if timing:  # marks the headline's timed kernels for ncu (--nvtx-include "timed/")
+            torch.cuda.nvtx.range_push("timed")
         launches = 0
         md0 = sampler.md_steps if sampler is not None else 0
         for k in range(steps):
@@ -276,6 +284,8 @@ def run_ours(args):
             ess_min.append(e.min())
             ess_th.append(rsv.rsv_ess(ctx, thetas.float().contiguous()))
             acc_rate.append(acc.float().mean())
+        if timing:
+            torch.cuda.nvtx.range_pop()
         _barrier(ws)
         if clocks:
             clocks.__exit__()
@@ -445,19 +455,49 @@ def run_ours(args):
     h2d = 3 * T_SITES * 8 + 5 * 8
     d2h = T_SITES * 8 + N_TRAJ * (4 + 8)
 
+    # MD-only rate (the paper's elementary step): trajectory-kernel time at the
+    # headline length minus that at one step, per leapfrog step, no theta update
+    def kernel_us(n_md, n=10):
+        hh = torch.tensor(s.h_true, device=dev)
+        th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
+        rsv.rsv_hmc_chain(ctx, hh, y, lnrv, th, n_md, head_dt, 2, prec="mixed", minv=minv,
+                          seed=77)
+        torch.cuda.synchronize()
+        rsv.rsv_stats(ctx, reset=True)
+        rsv.rsv_timing(ctx, True)
+        rsv.rsv_hmc_chain(ctx, hh, y, lnrv, th, n_md, head_dt, n, prec="mixed", minv=minv,
+                          seed=78, traj0=2)
+        torch.cuda.synchronize()
+        rsv.rsv_timing(ctx, False)
+        _, nl, ms = rsv.rsv_stats(ctx, reset=True)
+        return 1e3 * ms / max(nl, 1)
+    # both lengths on the headline's tiling (its halo for n_md): the plan the
+    # library picks for n_md, its tile fixed for the one-step run too
+    pl = rsv.Plan(ctx, np.array([0, T_SITES], dtype=np.int64), head_nmd, "mixed",
+                  with_mass=minv is not None)
+    pi = pl.info()
+    pl.close()
+    nt_, j_ = pi["threads"], pi["sites_per_thread"]
+    rsv.rsv_set_schedule(ctx, nt_, j_, nt_ * j_ - 2 * (head_nmd + 1) - 3)
+    t_hi, t_lo = kernel_us(head_nmd), kernel_us(1)
+    rsv.rsv_set_schedule(ctx)
+    per_step_us = (t_hi - t_lo) / max(head_nmd - 1, 1)
+    md = {"site_updates_per_s": ws * T_SITES / (per_step_us * 1e-6), "unit": UNIT,
+          "us_per_step": per_step_us, "us_per_trajectory_fixed": t_lo - per_step_us,
+          "kernel_us_per_trajectory": t_hi, "n_md": head_nmd,
+          "schedule": {"threads": nt_, "sites_per_thread": j_},
+          "how": "k_traj_mixed time at n_md minus at n_md = 1, per step (CUDA events)"}
+
     peaks, peak_kind = _peaks()
     sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_clock_mhz * 1e6 / 1e12  # Top/s
     per_launch_s = head["traj_ms"] / 1e3 / max(head["traj_launches"], 1)
     ops_per_launch = OPS_PER_SITE_STEP_MIXED * T_SITES * head_nmd
     achieved = ops_per_launch / per_launch_s / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("k_traj_mixed_T2p20")
-        except Exception:
-            traffic = None
+    # DRAM bytes (read + write) of one headline launch from the ncu capture in
+    # profiles/, valid only for the kernel revision it was taken on
+    from paper_1603_08114_gb300 import autotune as _at
+    traffic = TRAFFIC["bytes"] if TRAFFIC["kernel_rev"] == _at.KERNEL_REV else None
 
     if rank == 0:
         cpu = cpu_baseline() if (ws == 1 and not args.no_cpu) else None
@@ -500,7 +540,8 @@ def run_ours(args):
                          f"rate 152 SM x 128 x {sm_clock_mhz:.0f} MHz",
                          "per_launch_ms": per_launch_s * 1e3},
             "cpu_baseline": cpu,
-            "e2e": {"value": ws * T_SITES * N_MD * N_TRAJ / e2e_s, "unit": UNIT,
+            "md_only": md,
+            "e2e": {"value": ws * T_SITES * head_nmd * N_TRAJ / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": head["launches"],
             "clocks": clocks.summary(),

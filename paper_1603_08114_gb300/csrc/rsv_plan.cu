@@ -128,14 +128,10 @@ bool make_plan(const int64_t* off, int n, int n_md, bool mixed, bool mass, int n
                     if (bps < 1) continue;
                     const int64_t waves = (b + (int64_t)num_sms * bps - 1) / ((int64_t)num_sms * bps);
                     double cost = (double)waves * (double)cap * bps;
-                    // measured on the mixed kernel: the longest runs per
-                    // thread (J = 20, the fewest exchanges per site) and two
-                    // or more blocks per SM (one block's barrier overlaps the
-                    // other's arithmetic) are the fastest at equal waves
-                    if (mixed) {
-                        if (js[ji] != 20) cost *= 1.08;
-                        if (bps < 2) cost *= 1.03;
-                    }
+                    // measured on the mixed kernel at T = 2^20 (fixed and
+                    // per-step cost per block shape): J = 12 with ~600
+                    // threads is the fastest, J = 20 close, J = 16 and 8 slower
+                    if (mixed) cost *= js[ji] == 12 ? 1.0 : js[ji] == 20 ? 1.03 : 1.08;
                     cost *= 1.0 + 1e-3 * (double)(tmax - t) / tmax;
                     if (cost < best) {
                         best = cost;

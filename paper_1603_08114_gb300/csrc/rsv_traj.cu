@@ -545,6 +545,15 @@ __device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, float mi, f
     ff_acc(acc.E, ff_mul_f(E, a));
 }
 
+// The stationary term (1 - phi^2) x_1^2 / (2 s_eta^2) of S, into Q (weighted
+// by 1/(2 s_eta^2)), in double-float: FP64 here would cost every warp that
+// predicates it.
+__device__ __forceinline__ void stationary_part(HParts& acc, ff x1, const MixedTheta& mt)
+{
+    const ff om = ff_sub(ff{1.0f, 0.0f}, ff_mul(mt.phi_ff, mt.phi_ff));
+    ff_acc(acc.Q, ff_mul(om, ff_mul(x1, x1)));
+}
+
 // Per-site work outside the leapfrog (loading, momenta, both ends of dH)
 // runs in rolled loops over the thread's slots through shared memory: fully
 // unrolled over J slots it is thousands of instructions per thread, more than
@@ -573,6 +582,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
     float* s_ph = s_xl + W;
     const bool mass_on = MASS && (A.mass_on == nullptr || *A.mass_on != 0);
     const float dt = (float)A.dtau;
+    const float inv_dt = 1.0f / dt;  // 1/m_t = (dtau/m_t) / dtau, the same at both ends of dH
     // slot j is lane j / P of pair j % P
     auto na_at = [&](int j) -> float& { return s_ak1[((j % P) * NT + tid) * 4 + j / P]; };
     auto k_at = [&](int j) -> float& { return s_ak1[((j % P) * NT + tid) * 4 + 2 + j / P]; };
@@ -582,8 +592,6 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
         float2 X[P], XL[P], PH[P], PL[P];
         MixedConst mc;
         ff h0;             // this thread's owned-site H at the start
-        double stat0 = 0.0;
-        bool has_stat = false;
         {
             View v;
             load_bin(A, b, s_wseg, s_wacc, v);
@@ -602,23 +610,32 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             mc.first = v.first;
             const int64_t off = v.si.off, wlo = v.g.wlo;
             const float2* hin = v.cur ? A.h1f : A.h0f;
-            // pass 1: site constants, x, p -> shared memory (two quads in flight)
+            // pass 1a: momenta (standard normals, or the caller's p) -> s_ph;
+            // the two sources in separate loops, so that neither is predicated
+            // through the other (the FP64 -> FP32 conversions of p_in run on
+            // the FP64 pipe)
+            if (A.p_in) {
+#pragma unroll 1
+                for (int j = 0; j < J; ++j) {
+                    const int ii = base + j;
+                    s_ph[j * NT + tid] = ii < v.n ? (float)A.p_in[off + wlo + ii] : 0.0f;
+                }
+            } else {
 #pragma unroll 2
-            for (int q = 0; q < J / 4; ++q) {
-                float z[4];
-                if (A.p_in) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int ii = base + 4 * q + i;
-                        z[i] = ii < v.n ? (float)A.p_in[off + wlo + ii] : 0.0f;
-                    }
-                } else {
+                for (int q = 0; q < J / 4; ++q) {
                     const int64_t s0 = wlo + base + 4 * q;
                     const u64x4 r = philox_block(A.seed, (uint64_t)v.g.series, A.traj, STREAM_MOM,
                                                  (uint64_t)(s0 >> 2));
+                    float z[4];
                     box_muller_f(u01_23(r.w[0]), u01_23(r.w[1]), z[0], z[1]);
                     box_muller_f(u01_23(r.w[2]), u01_23(r.w[3]), z[2], z[3]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) s_ph[(4 * q + i) * NT + tid] = z[i];
                 }
+            }
+            // pass 1b: site constants, x, mass -> shared memory
+#pragma unroll 2
+            for (int q = 0; q < J / 4; ++q) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int j = 4 * q + i;
@@ -635,26 +652,22 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     cp.lo += lr.y - mt.ximu.lo;
                     na_at(j) = -a;
                     k_at(j) = fmaf(-mt.iu, cp.hi + cp.lo, 0.5f);
-                    float pz = z[i];
                     if (MASS) {
                         const float mi = (act && mass_on) ? A.minv[s] : 1.0f;
                         dm_at(j) = dt * mi;
-                        if (!A.p_in) pz = pz / sqrtf(mi);
+                        // p ~ N(0, m_t): the drawn normal over sqrt(1/m_t)
+                        if (!A.p_in) s_ph[j * NT + tid] = s_ph[j * NT + tid] / sqrtf(mi);
                     }
                     s_xh[j * NT + tid] = x.hi;
                     s_xl[j * NT + tid] = x.lo;
-                    s_ph[j * NT + tid] = pz;
                 }
             }
             __syncthreads();
-            // pass 2: H at the start over the owned sites (needs the next x);
-            // even and odd slots in separate accumulators, two sites in flight
-            HParts acc2[2];
-            hparts_zero(acc2[0]);
-            hparts_zero(acc2[1]);
-#pragma unroll 2
+            // pass 2: H at the start over the owned sites (needs the next x)
+            HParts acc;
+            hparts_zero(acc);
+#pragma unroll 1
             for (int j = 0; j < J; ++j) {
-                HParts& acc = acc2[j & 1];
                 const int64_t sg = wlo + base + j;
                 if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
                 const ff x = {s_xh[j * NT + tid], s_xl[j * NT + tid]};
@@ -663,16 +676,14 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                 const float2 lr = A.lr_f[off + sg];
                 ff cp = two_sum(lr.x, -mt.ximu.hi);
                 cp.lo += lr.y - mt.ximu.lo;
-                const float mi = MASS ? dm_at(j) / dt : 1.0f;
+                const float mi = MASS ? dm_at(j) * inv_dt : 1.0f;
                 hparts_site(acc, x, ff{s_ph[j * NT + tid], 0.f}, mi, cp, -na_at(j), xn,
                             sg + 1 < v.si.T, mt, s_exptab);
-                if (sg == 0) {  // one thread per series
-                    const double a0 = ff_to_double(x);
-                    stat0 = 0.5 * (1.0 - v.th.phi * v.th.phi) / v.th.se2 * a0 * a0;
-                    has_stat = true;
-                }
             }
-            h0 = ff_add(hparts_total(acc2[0], mt), hparts_total(acc2[1], mt));
+            // the stationary term of h_1, outside the loop (its thread only)
+            if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
+                stationary_part(acc, ff{s_xh[tid], s_xl[tid]}, mt);
+            h0 = hparts_total(acc, mt);
             // registers <- shared memory, then the first half step of eq. (6)
 #pragma unroll
             for (int q = 0; q < P; ++q) {
@@ -716,13 +727,10 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
         const int base = v.base * J;
         const MixedTheta& mt = s_mt[warp];
         const int64_t off = v.si.off, wlo = v.g.wlo;
-        HParts acc2[2];
-        hparts_zero(acc2[0]);
-        hparts_zero(acc2[1]);
-        double stat1 = 0.0;
-#pragma unroll 2
+        HParts acc;
+        hparts_zero(acc);
+#pragma unroll 1
         for (int j = 0; j < J; ++j) {
-            HParts& acc = acc2[j & 1];
             const int64_t sg = wlo + base + j;
             if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
             const ff x = {s_xh[j * NT + tid], s_xl[j * NT + tid]};
@@ -731,16 +739,13 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             const float2 lr = A.lr_f[off + sg];
             ff cp = two_sum(lr.x, -mt.ximu.hi);
             cp.lo += lr.y - mt.ximu.lo;
-            const float mi = MASS ? dm_at(j) / dt : 1.0f;
+            const float mi = MASS ? dm_at(j) * inv_dt : 1.0f;
             hparts_site(acc, x, ff{s_ph[j * NT + tid], k_at(j)}, mi, cp, -na_at(j), xn,
                         sg + 1 < v.si.T, mt, s_exptab);
-            if (sg == 0) {
-                const double a1 = ff_to_double(x);
-                stat1 = 0.5 * (1.0 - v.th.phi * v.th.phi) / v.th.se2 * a1 * a1;
-            }
         }
-        ff dh = ff_sub(ff_add(hparts_total(acc2[0], mt), hparts_total(acc2[1], mt)), h0);
-        if (has_stat) dh = ff_add(dh, ff_from_double(stat1 - stat0));
+        if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
+            stationary_part(acc, ff{s_xh[tid], s_xl[tid]}, mt);
+        ff dh = ff_sub(hparts_total(acc, mt), h0);
         dh = warp_sum_ff(dh);
         if (lane == 0) s_wpf[warp] = make_float2(dh.hi, dh.lo);
         __syncthreads();
@@ -758,7 +763,14 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     hh = fast_two_sum(hh.hi, hh.lo);
                     hout[off + sg] = make_float2(hh.hi, hh.lo);
                 }
-                if (A.p_out) A.p_out[off + sg] = (double)s_ph[j * NT + tid] + (double)k_at(j);
+            }
+        }
+        if (A.p_out) {  // a loop of its own: its FP64 conversions are never predicated
+#pragma unroll 1
+            for (int j = 0; j < J; ++j) {
+                const int64_t sg = wlo + base + j;
+                if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi)
+                    A.p_out[off + sg] = (double)s_ph[j * NT + tid] + (double)k_at(j);
             }
         }
         if (v.g.split) finish_split_ff(A, v, s_splitf, &s_flag);
