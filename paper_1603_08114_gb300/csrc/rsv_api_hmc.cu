@@ -188,6 +188,9 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
         a.dH_out = o.dH_out ? o.dH_out + i * (int64_t)n : c->ser_dh.as<double>();
         a.acc_out = o.acc_out ? o.acc_out + i * (int64_t)n : c->ser_acc.as<int>();
         if ((e = timed_traj(c, a, P, s)) != cudaSuccess) return cuda_fail(e, "trajectory kernel");
+        const bool snap_due = o.snaps && (i + 1) % o.thin == 0;
+        float* snap_dst = snap_due ? o.snaps + (size_t)((i + 1) / o.thin - 1) * N : nullptr;
+        bool snap_done = false;
         if (o.update_theta) {
             GibbsArgs g;
             memset(&g, 0, sizeof(g));
@@ -208,6 +211,13 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
             g.partials = c->gibbs.as<double>();
             g.counter = reinterpret_cast<unsigned*>(ints + kGibbsCounter);
             g.theta_f = mixed ? c->theta_f.as<MixedTheta>() : nullptr;
+            // the mixed sweep reads every site of the new state: it writes this
+            // trajectory's snapshot on the way (single series: the packed state
+            // is the series)
+            if (mixed && snap_due && P.nseries == 1) {
+                g.snap_out = snap_dst;
+                snap_done = true;
+            }
             if ((e = counted(c, launch_gibbs, g, mixed, s)) != cudaSuccess)
                 return cuda_fail(e, "theta kernel");
         } else if (o.theta_out) {
@@ -215,11 +225,10 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
                                      cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
                 return cuda_fail(e, "theta record");
         }
-        if (o.snaps && (i + 1) % o.thin == 0) {
-            float* dst = o.snaps + (size_t)((i + 1) / o.thin - 1) * N;
+        if (snap_due && !snap_done) {
             if ((e = counted(c, launch_snapshot, P, (const int*)a.ser_cur, (const double*)a.h0d,
                              (const double*)a.h1d, (const float2*)a.h0f, (const float2*)a.h1f,
-                             dst, s)) != cudaSuccess)
+                             snap_dst, s)) != cudaSuccess)
                 return cuda_fail(e, "snapshot kernel");
         }
     }

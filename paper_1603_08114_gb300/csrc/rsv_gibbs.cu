@@ -372,10 +372,13 @@ __device__ __forceinline__ void site_stats_d(const double* h, const double* lnrv
 }
 
 // Per-site contributions, (hi, lo) FP32 state: double-float arithmetic.
-__device__ __forceinline__ void site_stats_f(const float2* h, const float2* lr, int64_t t,
-                                            int64_t T, ff xi, ff mu, ff phi, ff (&s)[NSTAT])
+__device__ __forceinline__ void site_stats_f(const float2* __restrict__ h,
+                                            const float2* __restrict__ lr, int64_t t, int64_t T,
+                                            ff xi, ff mu, ff phi, ff (&s)[NSTAT],
+                                            float* __restrict__ snap)
 {
     const float2 hv = h[t];
+    if (snap) snap[t] = hv.x + hv.y;  // the chain's snapshot of h, taken on the way
     const ff ht = {hv.x, hv.y};
     const float2 lv = lr[t];
     const ff q = ff_sub(ff_sub(ff{lv.x, lv.y}, xi), ht);
@@ -559,9 +562,15 @@ __global__ void __launch_bounds__(kGibbsMixedBlock, 2) k_gibbs_mixed(GibbsArgs A
         ff s[NSTAT];
         for (int i = 0; i < NSTAT; ++i) s[i] = ff{0.f, 0.f};
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        if (A.snap_out) {
 #pragma unroll 4
-        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
-            site_stats_f(h, A.lr_f, t, A.T, xi, mu, phi, s);
+            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
+                site_stats_f(h, A.lr_f, t, A.T, xi, mu, phi, s, A.snap_out);
+        } else {
+#pragma unroll 4
+            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
+                site_stats_f(h, A.lr_f, t, A.T, xi, mu, phi, s, nullptr);
+        }
         block_sum_ff(s, redf);
         float2* pf = reinterpret_cast<float2*>(A.partials);
         if (threadIdx.x == 0)

@@ -25,6 +25,7 @@ struct GibbsArgs {
     unsigned* counter;
     int* phi_acc;        // optional
     MixedTheta* theta_f; // mixed path: the current theta's constants, read and refreshed
+    float* snap_out;     // mixed path, optional: h (FP32) of the state the sweep reads
 };
 
 int gibbs_grid(int64_t T);
