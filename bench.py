@@ -554,6 +554,90 @@ def run_ours(args):
     return 0
 
 
+# The paper's Table 2 (Sec. 5): time of one elementary MD step (Kernels 1-3,
+# one leapfrog step over all T sites), T = 512 B, fitted as f(B) = A + C B;
+# GTX 760 (CUDA Fortran, FP32) and i7-4770.
+PAPER_TABLE2 = {"gpu": {"A": 1.13e-5, "C": 2.25e-7}, "cpu": {"A": -1.42e-6, "C": 3.87e-6},
+                "gain_limit": 17.2, "hardware": "GTX 760 / i7-4770 3.4 GHz, FP32"}
+TABLE2_B = (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048)
+
+
+def fit_linear(B, f):
+    """Least-squares f(B) = A + C B; returns (A, C)."""
+    B = np.asarray(B, dtype=np.float64)
+    M = np.stack([np.ones_like(B), B], axis=1)
+    (A, C), *_ = np.linalg.lstsq(M, np.asarray(f, dtype=np.float64), rcond=None)
+    return float(A), float(C)
+
+
+def run_table2(args):
+    """Time per elementary step vs B on this GPU (mixed and FP64 paths: the
+    trajectory kernel's time at two lengths on one tiling, per extra step) and
+    for the oracle's leapfrog on one host core; both fitted like Table 2."""
+    import torch
+
+    from paper_1603_08114_gb300 import rsv, synth
+    import oracle
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = rsv.Context(0)
+    n_lo, n_hi = 10, 110
+    res = {"B": list(TABLE2_B), "gpu_mixed": [], "gpu_fp64": [], "cpu_oracle": []}
+    for B in TABLE2_B:
+        T = 512 * B
+        s = synth.rsv_series(T, synth.THETA_STD, seed=1)
+        y = torch.tensor(s.y, device=dev)
+        lr = torch.tensor(s.lnrv, device=dev)
+        for prec in ("mixed", "fp64"):
+            pl = rsv.Plan(ctx, np.array([0, T], dtype=np.int64), n_hi, prec)
+            pi = pl.info()
+            pl.close()
+            nt, j = pi["threads"], pi["sites_per_thread"]
+            if T > nt * j - 2 * (n_hi + 1) - 3:  # a tiled series: one tile size for both lengths
+                rsv.rsv_set_schedule(ctx, nt, j, nt * j - 2 * (n_hi + 1) - 3)
+            times = []
+            for n_md in (n_lo, n_hi):
+                h = torch.tensor(s.h_true, device=dev)
+                th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
+                n = 10 if prec == "mixed" else 2
+                rsv.rsv_hmc_chain(ctx, h, y, lr, th, n_md, 0.005, 2, prec=prec, seed=1)
+                torch.cuda.synchronize()
+                rsv.rsv_stats(ctx, reset=True)
+                rsv.rsv_timing(ctx, True)
+                rsv.rsv_hmc_chain(ctx, h, y, lr, th, n_md, 0.005, n, prec=prec, seed=2)
+                torch.cuda.synchronize()
+                rsv.rsv_timing(ctx, False)
+                _, nl, ms = rsv.rsv_stats(ctx, reset=True)
+                times.append(ms / 1e3 / max(nl, 1))
+            rsv.rsv_set_schedule(ctx)
+            res["gpu_" + prec].append((times[1] - times[0]) / (n_hi - n_lo))
+        # oracle: leapfrog steps on the host, one core
+        p0 = synth.standard_normals(T, 5)
+        n_steps = max(2, min(200, int(2e6 // T)))
+        t0 = time.perf_counter()
+        oracle.leapfrog(s.h_true, p0, s.y, s.lnrv, s.theta, n_steps, 0.005)
+        res["cpu_oracle"].append((time.perf_counter() - t0) / n_steps)
+    fits = {k: dict(zip(("A", "C"), fit_linear(res["B"], res[k])))
+            for k in ("gpu_mixed", "gpu_fp64", "cpu_oracle")}
+    line = {
+        "table2": {
+            "T": [512 * b for b in TABLE2_B], **res,
+            "unit": "seconds per elementary step (one leapfrog step over all T sites)",
+            "fit": fits,
+            "gain_limit_mixed_vs_oracle": fits["cpu_oracle"]["C"] / fits["gpu_mixed"]["C"],
+            "gain_limit_fp64_vs_oracle": fits["cpu_oracle"]["C"] / fits["gpu_fp64"]["C"],
+            "site_updates_per_s_at_2048": 512 * 2048 / res["gpu_mixed"][-1],
+            "paper": PAPER_TABLE2,
+            "how": "GPU: k_traj_mixed / k_traj_fp64 time at n_md = 110 minus at n_md = 10 "
+                   "(one tiling, CUDA events) / 100; oracle: FP64 leapfrog in plain C on "
+                   "one host core; FP64 oracle vs the paper's FP32 CPU code",
+        }
+    }
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -571,6 +655,8 @@ def main():
                     help="headline arm without the learned mass (profiling)")
     ap.add_argument("--n-snap", type=int, default=10000,
                     help="plain-sampler snapshots for the learned mass")
+    ap.add_argument("--table2", action="store_true",
+                    help="time per elementary step vs B (T = 512 B) like the paper's Table 2")
     args = ap.parse_args()
     if args.traj_per_step:
         global N_TRAJ
@@ -579,6 +665,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.table2:
+        return run_table2(args)
     return run_ours(args)
 
 
