@@ -90,6 +90,27 @@ rsv_status rsv_sync_status(rsv_ctx* ctx, void* stream);
  * depend on the tiling. */
 rsv_status rsv_set_schedule(rsv_ctx* ctx, int threads, int sites_per_thread, int64_t tile);
 
+/* ---- integrator -------------------------------------------------------------
+ * The molecular-dynamics integrator of the trajectories run afterwards through
+ * this context (rsv_hmc_trajectory, rsv_hmc_chain) and of plans created
+ * afterwards (a plan keeps the integrator it was made with):
+ *  RSV_LEAPFROG  eqs. (6)-(8), one force evaluation per step (the default);
+ *  RSV_OMELYAN2  the second-order minimum-norm integrator of Omelyan, Mryglod
+ *                and Folk (Phys. Rev. E 65, 056706, 2002), one of the
+ *                higher-order integrators Sec. 3 cites: per step
+ *                h += lambda dtau p/m; p -= dtau/2 dS/dh; h += (1-2 lambda) dtau p/m;
+ *                p -= dtau/2 dS/dh; h += lambda dtau p/m -- two force
+ *                evaluations per step, an energy error far smaller than the
+ *                leapfrog's at equal cost.  lambda <= 0 selects the minimum-norm
+ *                value RSV_OMELYAN2_LAMBDA; lambda = 1/2 is the leapfrog with its
+ *                force step split in two.
+ * With RSV_OMELYAN2 a tile's halo and the `tile` bound of rsv_set_schedule
+ * count 2 n_md force evaluations instead of n_md.  lambda > 1/2 or NaN gives
+ * RSV_EINVAL. */
+typedef enum rsv_integrator { RSV_LEAPFROG = 0, RSV_OMELYAN2 = 1 } rsv_integrator;
+#define RSV_OMELYAN2_LAMBDA 0.19318332750378357
+rsv_status rsv_set_integrator(rsv_ctx* ctx, rsv_integrator kind, double lambda);
+
 /* ---- S(h) -----------------------------------------------------------------
  * S(h) of Sec. 3 (see above), FP64, deterministic reduction order.
  * h, y, lnrv: [T] FP64.  S_out: device FP64 scalar.  T >= 1. */

@@ -63,13 +63,16 @@ def lib():
             L.orc_force.argtypes = [_D, _D, _D, ctypes.c_long, Theta, _D]
             L.orc_leapfrog.argtypes = [_D, _D, _D, _D, ctypes.c_long, Theta, _D, ctypes.c_int,
                                        ctypes.c_double]
+            L.orc_omelyan2.argtypes = [_D, _D, _D, _D, ctypes.c_long, Theta, _D, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double]
             L.orc_delta_H.restype = ctypes.c_double
             L.orc_delta_H.argtypes = [_D, _D, _D, _D, _D, _D, ctypes.c_long, Theta, _D]
             L.orc_metropolis.restype = ctypes.c_int
             L.orc_metropolis.argtypes = [ctypes.c_double, ctypes.c_double]
             L.orc_trajectory.restype = ctypes.c_int
             L.orc_trajectory.argtypes = [_D, _D, _D, _D, ctypes.c_long, Theta, _D, ctypes.c_int,
-                                         ctypes.c_double, ctypes.c_double, _D]
+                                         ctypes.c_double, ctypes.c_double, _D, ctypes.c_int,
+                                         ctypes.c_double]
             L.orc_philox4x64_10.argtypes = [_U64, _U64, _U64]
             L.orc_u01.restype = ctypes.c_double
             L.orc_u01.argtypes = [ctypes.c_uint64, ctypes.c_int]
@@ -86,7 +89,8 @@ def lib():
             L.orc_chain.argtypes = [_D, _D, _D, ctypes.c_long, ctypes.POINTER(Theta), _D,
                                     ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_long, ctypes.c_int,
-                                    ctypes.c_int, _D, _I, _D, _D, ctypes.c_long]
+                                    ctypes.c_int, _D, _I, _D, _D, ctypes.c_long, ctypes.c_int,
+                                    ctypes.c_double]
             _lib = L
     return _lib
 
@@ -151,14 +155,34 @@ def metropolis(dH, log_u) -> int:
     return lib().orc_metropolis(float(dH), float(log_u))
 
 
-def trajectory(h, p, y, lnrv, th, n_md, dtau, log_u, minv=None):
+# lambda of the second-order minimum-norm integrator (Omelyan, Mryglod, Folk,
+# Phys. Rev. E 65, 056706 (2002)): the root 1/2 - c/12 + 1/(6c),
+# c = (2 sqrt(326) + 36)^(1/3), of its error-norm minimisation
+LAMBDA_2MN = 0.19318332750378357
+
+_INTEGRATORS = {"leapfrog": 0, "omelyan2": 1}
+
+
+def omelyan2(h, p, y, lnrv, th, n_md, dtau, lam=LAMBDA_2MN, minv=None):
+    """n_md steps of the minimum-norm integrator; returns (h', p')."""
+    h, p = _f64(h).copy(), _f64(p).copy()
+    y, lnrv = _f64(y), _f64(lnrv)
+    mv = None if minv is None else _f64(minv)
+    lib().orc_omelyan2(_d(h), _d(p), _d(y), _d(lnrv), len(h), theta(th), _d(mv), int(n_md),
+                       float(dtau), float(lam))
+    return h, p
+
+
+def trajectory(h, p, y, lnrv, th, n_md, dtau, log_u, minv=None, integrator="leapfrog",
+               lam=LAMBDA_2MN):
     """One HMC trajectory; returns (h_new, p', dH, accept)."""
     h, p = _f64(h).copy(), _f64(p).copy()
     y, lnrv = _f64(y), _f64(lnrv)
     mv = None if minv is None else _f64(minv)
     dH = ctypes.c_double()
     acc = lib().orc_trajectory(_d(h), _d(p), _d(y), _d(lnrv), len(h), theta(th), _d(mv),
-                               int(n_md), float(dtau), float(log_u), ctypes.byref(dH))
+                               int(n_md), float(dtau), float(log_u), ctypes.byref(dH),
+                               _INTEGRATORS[integrator], float(lam))
     return h, p, dH.value, acc
 
 
@@ -203,7 +227,7 @@ def gibbs_theta(h, lnrv, th, seed, series, traj, mask=31):
 
 
 def chain(h, y, lnrv, th, n_md, dtau, seed, n_traj, traj0=0, series=0, update_theta=False,
-          bits=53, minv=None, thin=0):
+          bits=53, minv=None, thin=0, integrator="leapfrog", lam=LAMBDA_2MN):
     """n_traj trajectories with Philox draws; returns a dict of per-trajectory records."""
     h = _f64(h).copy()
     y, lnrv = _f64(y), _f64(lnrv)
@@ -217,6 +241,7 @@ def chain(h, y, lnrv, th, n_md, dtau, seed, n_traj, traj0=0, series=0, update_th
     n_acc = lib().orc_chain(_d(h), _d(y), _d(lnrv), T, ctypes.byref(t), _d(mv), int(n_md),
                             float(dtau), int(seed), int(series), int(traj0), int(n_traj),
                             int(bool(update_theta)), int(bits), _d(dH),
-                            acc.ctypes.data_as(_I), _d(ths), _d(snaps), int(thin))
+                            acc.ctypes.data_as(_I), _d(ths), _d(snaps), int(thin),
+                            _INTEGRATORS[integrator], float(lam))
     return dict(h=h, theta=t.as_tuple(), dH=dH, accept=acc, thetas=ths, snaps=snaps,
                 n_accept=int(n_acc))

@@ -141,6 +141,39 @@ void orc_leapfrog(double* h, double* p, const double* y, const double* lnrv,
     free(F);
 }
 
+/* n_md steps of the second-order minimum-norm integrator of Omelyan, Mryglod
+ * and Folk (Phys. Rev. E 65, 056706 (2002)), one of the higher-order
+ * integrators the paper cites (Sec. 3), taken literally: per step
+ *   h += lambda dtau p/m;  p -= dtau/2 dS/dh;  h += (1 - 2 lambda) dtau p/m;
+ *   p -= dtau/2 dS/dh;  h += lambda dtau p/m.
+ * lambda = 1/2 gives eqs. (6)-(8) with the force step split in two halves. */
+void orc_omelyan2(double* h, double* p, const double* y, const double* lnrv,
+                  long T, orc_theta th, const double* minv, int n_md, double dtau,
+                  double lambda)
+{
+    double* F = (double*)malloc(sizeof(double) * (size_t)(T > 0 ? T : 1));
+    const double c[3] = {lambda * dtau, (1.0 - 2.0 * lambda) * dtau, lambda * dtau};
+    for (int k = 0; k < n_md; ++k) {
+        for (int s = 0; s < 3; ++s) {
+            for (long t = 0; t < T; ++t) h[t] = h[t] + c[s] * (minv ? minv[t] * p[t] : p[t]);
+            if (s == 2) break;
+            orc_force(h, y, lnrv, T, th, F);
+            for (long t = 0; t < T; ++t) p[t] = p[t] - 0.5 * dtau * F[t];
+        }
+    }
+    free(F);
+}
+
+/* The integrator of a trajectory: 0 = leapfrog (eqs. (6)-(8)), 1 = the
+ * minimum-norm integrator above with the given lambda. */
+static void orc_integrate(double* h, double* p, const double* y, const double* lnrv, long T,
+                          orc_theta th, const double* minv, int n_md, double dtau,
+                          int integrator, double lambda)
+{
+    if (integrator == 1) orc_omelyan2(h, p, y, lnrv, T, th, minv, n_md, dtau, lambda);
+    else orc_leapfrog(h, p, y, lnrv, T, th, minv, n_md, dtau);
+}
+
 /* dH = H(p', h') - H(p, h), summed as per-site differences with compensation
  * so that the O(1) result is not lost against the O(T) action (Sec. 3). */
 double orc_delta_H(const double* h0, const double* p0, const double* h1, const double* p1,
@@ -170,14 +203,14 @@ int orc_metropolis(double dH, double log_u)
  * Returns the accept flag; *dH_out receives dH. */
 int orc_trajectory(double* h, double* p, const double* y, const double* lnrv,
                    long T, orc_theta th, const double* minv, int n_md, double dtau,
-                   double log_u, double* dH_out)
+                   double log_u, double* dH_out, int integrator, double lambda)
 {
     size_t n = (size_t)(T > 0 ? T : 1);
     double* h1 = (double*)malloc(sizeof(double) * n);
     double* p0 = (double*)malloc(sizeof(double) * n);
     memcpy(h1, h, sizeof(double) * (size_t)T);
     memcpy(p0, p, sizeof(double) * (size_t)T);
-    orc_leapfrog(h1, p, y, lnrv, T, th, minv, n_md, dtau);
+    orc_integrate(h1, p, y, lnrv, T, th, minv, n_md, dtau, integrator, lambda);
     double dH = orc_delta_H(h, p0, h1, p, y, lnrv, T, th, minv);
     int acc = orc_metropolis(dH, log_u);
     if (acc) memcpy(h, h1, sizeof(double) * (size_t)T);
@@ -434,7 +467,8 @@ int orc_gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
 long orc_chain(double* h, const double* y, const double* lnrv, long T, orc_theta* th,
                const double* minv, int n_md, double dtau, uint64_t seed, uint64_t series,
                uint64_t traj0, long n_traj, int update_theta, int bits,
-               double* dH_out, int* acc_out, double* theta_out, double* snaps, long thin)
+               double* dH_out, int* acc_out, double* theta_out, double* snaps, long thin,
+               int integrator, double lambda)
 {
     size_t n = (size_t)(T > 0 ? T : 1);
     double* p = (double*)malloc(sizeof(double) * n);
@@ -444,7 +478,8 @@ long orc_chain(double* h, const double* y, const double* lnrv, long T, orc_theta
         orc_draw_momenta(seed, series, traj, T, minv, bits, p);
         double log_u = orc_draw_log_u(seed, series, traj);
         double dH;
-        int acc = orc_trajectory(h, p, y, lnrv, T, *th, minv, n_md, dtau, log_u, &dH);
+        int acc = orc_trajectory(h, p, y, lnrv, T, *th, minv, n_md, dtau, log_u, &dH,
+                                 integrator, lambda);
         n_acc += acc;
         if (update_theta) orc_gibbs_theta(h, lnrv, T, th, seed, series, traj, 31);
         if (dH_out) dH_out[i] = dH;

@@ -171,6 +171,21 @@ rsv_status rsv_reserve(rsv_ctx* c, int64_t max_T, int64_t max_series)
     return RSV_OK;
 }
 
+rsv_status rsv_set_integrator(rsv_ctx* c, rsv_integrator kind, double lambda)
+{
+    if (!c) return fail(RSV_EINVAL, "null context");
+    if (kind == RSV_LEAPFROG) {
+        c->integrator = 0;
+        c->lambda = 0.0;
+        return RSV_OK;
+    }
+    if (kind != RSV_OMELYAN2) return fail(RSV_EINVAL, "unknown integrator");
+    if (!(lambda <= 0.5) || lambda != lambda) return fail(RSV_EINVAL, "lambda must be <= 1/2");
+    c->integrator = 1;
+    c->lambda = lambda > 0.0 ? lambda : RSV_OMELYAN2_LAMBDA;
+    return RSV_OK;
+}
+
 rsv_status rsv_set_schedule(rsv_ctx* c, int threads, int sites_per_thread, int64_t tile)
 {
     if (!c) return fail(RSV_EINVAL, "null context");

@@ -48,6 +48,7 @@ rsv_status single_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, c
 {
     for (auto& e : c->plans) {
         if (e.T == T && e.n_md == n_md && e.mixed == mixed && e.mass == mass &&
+            e.integrator == c->integrator && e.lambda == c->lambda &&
             e.nt == c->sched_nt && e.j == c->sched_j && e.tile == c->sched_tile) {
             *out = &e.plan;
             return RSV_OK;
@@ -61,10 +62,11 @@ rsv_status single_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, c
         c->plans.erase(c->plans.begin());
     }
     const int64_t off[2] = {0, T};
-    rsv_ctx::Cached e{T, n_md, mixed, mass, c->sched_nt, c->sched_j, c->sched_tile, Plan()};
+    rsv_ctx::Cached e{T,          n_md,        c->integrator, c->lambda, mixed,
+                      mass,       c->sched_nt, c->sched_j,    c->sched_tile, Plan()};
     const char* why = "";
-    if (!make_plan(off, 1, n_md, mixed, mass, c->num_sms, c->sched_nt, c->sched_j,
-                   c->sched_tile, e.plan, &why))
+    if (!make_plan(off, 1, n_md, c->integrator, c->lambda, mixed, mass, c->num_sms, c->sched_nt,
+                   c->sched_j, c->sched_tile, e.plan, &why))
         return fail(RSV_EINVAL, "%s", why);
     c->plans.push_back(e);
     *out = &c->plans.back().plan;
@@ -159,6 +161,8 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
     a.minv = o.minv;
     a.mass_on = ints + kMassOn;
     a.n_md = P.n_md;
+    a.integrator = P.integrator;
+    a.lambda = P.lambda;
     a.dtau = o.dtau;
     a.seed = o.seed;
     a.status = ints + kStatus;
@@ -350,8 +354,9 @@ rsv_status rsv_plan_create(rsv_ctx* c, const int64_t* offsets, int64_t n_series,
     rsv_plan* p = new rsv_plan();
     p->device = c->device;
     const char* why = "";
-    if (!make_plan(offsets, (int)n_series, n_md, prec == RSV_MIXED, with_mass != 0, c->num_sms,
-                   c->sched_nt, c->sched_j, c->sched_tile, p->plan, &why)) {
+    if (!make_plan(offsets, (int)n_series, n_md, c->integrator, c->lambda, prec == RSV_MIXED,
+                   with_mass != 0, c->num_sms, c->sched_nt, c->sched_j, c->sched_tile, p->plan,
+                   &why)) {
         delete p;
         return fail(RSV_EINVAL, "%s", why);
     }

@@ -50,6 +50,8 @@ struct rsv_ctx {
     struct Cached {
         int64_t T;
         int n_md;
+        int integrator;
+        double lambda;
         bool mixed, mass;
         int nt, j;
         int64_t tile;
@@ -58,6 +60,8 @@ struct rsv_ctx {
     std::vector<Cached> plans;
     rsv::Buf ser_cur, ser_cnt, ser_dh, ser_acc;  // per-series scratch
     int sched_nt = 0, sched_j = 0;  // rsv_set_schedule override (0 = automatic)
+    int integrator = 0;             // rsv_set_integrator (0 leapfrog)
+    double lambda = 0.0;
     int64_t sched_tile = 0;
     // accounting: kernel launches, and CUDA events around trajectory kernels
     int64_t launches = 0;

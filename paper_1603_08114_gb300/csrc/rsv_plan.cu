@@ -7,7 +7,8 @@
 //    model keeps whole) is one segment on ceil(T / (32 j)) whole warps; such
 //    segments are packed side by side into bins first-fit-decreasing;
 //  - a longer series is cut into tiles of `tile` owned sites, each with a
-//    halo of K = n_md + 1 sites per side, one tile per bin.
+//    halo of K = (force evaluations per trajectory) + 1 sites per side, one
+//    tile per bin.
 // Segment ids run series by series so that the tiles of one series are
 // consecutive (their partial dH are summed in that order).
 #include <algorithm>
@@ -56,10 +57,12 @@ void free_plan(Plan& p)
     p = Plan();
 }
 
-bool make_plan(const int64_t* off, int n, int n_md, bool mixed, bool mass, int num_sms,
-               int sched_nt, int sched_j, int64_t sched_tile, Plan& P, const char** why)
+bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambda, bool mixed,
+               bool mass, int num_sms, int sched_nt, int sched_j, int64_t sched_tile, Plan& P,
+               const char** why)
 {
-    const int64_t K = (int64_t)n_md + 1;
+    // one site of staleness per force evaluation
+    const int64_t K = (int64_t)n_md * (integrator == 1 ? 2 : 1) + 1;
     const size_t smem_cap = 227 * 1024;
     if (n < 1) {
         *why = "no series";
@@ -258,6 +261,8 @@ bool make_plan(const int64_t* off, int n, int n_md, bool mixed, bool mass, int n
     p.nsplit = nsplit;
     p.total = off[n];
     p.n_md = n_md;
+    p.integrator = integrator;
+    p.lambda = lambda;
     p.mixed = mixed;
     p.mass = mass;
     int bps = blocks_per_sm(mixed, mass, j, nt, p.smem);

@@ -345,31 +345,41 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
         double E0 = 0.0, E1 = 0.0;
         owned_energy(E0);
 
+        // Per step, drifts and kicks in the literal order: leapfrog eqs. (6)-(8)
+        // (drift dtau/2, kick dtau, drift dtau/2) or the minimum-norm integrator
+        // (drift lambda dtau, kick dtau/2, drift (1-2 lambda) dtau, kick dtau/2,
+        // drift lambda dtau).
         const double dt = A.dtau, hd = 0.5 * A.dtau;
+        const bool mn = A.integrator == 1;
+        const int nk = mn ? 2 : 1;
+        const double d_end = mn ? A.lambda * dt : hd, d_mid = (1.0 - 2.0 * A.lambda) * dt;
+        const double kick = mn ? hd : dt;
         for (int k = 0; k < A.n_md; ++k) {
-            // eq. (6): h(tau + dtau/2) = h(tau) + dtau/2 p / m
+            for (int st = 0; st <= nk; ++st) {
+                // eq. (6)/(8): h += c dtau p / m
+                const double cd = (st == 0 || st == nk) ? d_end : d_mid;
 #pragma unroll
-            for (int j = 0; j < J; ++j) x[j] = fma(MASS ? hd * s_mi[j * NT + tid] : hd, p[j], x[j]);
-            double xL, xR, e[J];
-            exchange(x[0], x[J - 1], xL, xR, s_edge + par * 2 * nw, nw);
-            par ^= 1;
-            if (edge_thread) innovations<J, double, true>(x, xR, phi, la, e);
-            else innovations<J, double, false>(x, xR, phi, la, e);
-            // e_{-1}: left neighbour's innovation, or the stationary term at a window start
-            double eprev = v.first ? st0 * x[0] : fma(-phi, xL, x[0]);
-            // eq. (7): p(tau + dtau) = p(tau) - dtau dS/dh
+                for (int j = 0; j < J; ++j)
+                    x[j] = fma(MASS ? cd * s_mi[j * NT + tid] : cd, p[j], x[j]);
+                if (st == nk) break;
+                double xL, xR, e[J];
+                exchange(x[0], x[J - 1], xL, xR, s_edge + par * 2 * nw, nw);
+                par ^= 1;
+                if (edge_thread) innovations<J, double, true>(x, xR, phi, la, e);
+                else innovations<J, double, false>(x, xR, phi, la, e);
+                // e_{-1}: left neighbour's innovation, or the stationary term at a window start
+                double eprev = v.first ? st0 * x[0] : fma(-phi, xL, x[0]);
+                // eq. (7): p -= kick dS/dh
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const double ar = fma(-phi, e[j], eprev);
-                eprev = e[j];
-                double f = fma(iu, x[j], s_kc[j * NT + tid]);
-                f = fma(ie, ar, f);
-                f = fma(-s_a[j * NT + tid], exp(-x[j]), f);
-                p[j] = fma(-dt, f, p[j]);
+                for (int j = 0; j < J; ++j) {
+                    const double ar = fma(-phi, e[j], eprev);
+                    eprev = e[j];
+                    double f = fma(iu, x[j], s_kc[j * NT + tid]);
+                    f = fma(ie, ar, f);
+                    f = fma(-s_a[j * NT + tid], exp(-x[j]), f);
+                    p[j] = fma(-kick, f, p[j]);
+                }
             }
-            // eq. (8): h(tau + dtau) = h(tau + dtau/2) + dtau/2 p / m
-#pragma unroll
-            for (int j = 0; j < J; ++j) x[j] = fma(MASS ? hd * s_mi[j * NT + tid] : hd, p[j], x[j]);
         }
         owned_energy(E1);
 
@@ -420,6 +430,10 @@ __device__ float2 g_exptab[32];
 // Per-block constants of the leapfrog of one segment.
 struct MixedConst {
     float phi, c0, c1, cmu, dt;
+    // integrator as substeps {kick; drift}: kick size, drift ratios (to dtau)
+    // of even / odd / last substeps, substep count (see mixed_steps)
+    float kick, r_even, r_odd, r_last;
+    int n_sub;
     int la;        // slot of the series' last site in this thread (or out of [0, J))
     bool first;    // this thread holds the series' first site in slot 0
 };
@@ -468,8 +482,8 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
     const int NT = blockDim.x, tid = threadIdx.x;
     const float2 c0 = f2(c.c0, c.c0), c1 = f2(c.c1, c.c1);
     const float2 nl2e = f2(-kLog2e, -kLog2e), cmu = f2(c.cmu, c.cmu);
-    const float2 ndt = f2(-c.dt, -c.dt);
-    for (int k = 0; k < n_md; ++k) {
+    const float2 ndt = f2(-c.kick, -c.kick);
+    for (int k = 0; k < c.n_sub; ++k) {
         float xL, xR;
         exchange(X[0].x, X[P - 1].y, xL, xR, s_edge + par * 2 * nw, nw);
         par ^= 1;
@@ -477,7 +491,7 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
         if (!EDGE && c.la == J - 1) xR = c.phi * X[P - 1].y;
         const float xP = X[0].y;  // x_P before the step
         float2 prev = f2(xL, X[P - 1].x);  // left neighbours of pair 0, before the step
-        const float hs = (k + 1 < n_md) ? 1.0f : 0.5f;
+        const float hs = (k + 1 < c.n_sub) ? ((k & 1) ? c.r_odd : c.r_even) : c.r_last;
         const float2 cx = f2(hs * c.dt, hs * c.dt);
 #pragma unroll
         for (int q = 0; q < P; ++q) {
@@ -606,6 +620,17 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             mc.c1 = mt.c1;
             mc.cmu = mt.cmu;
             mc.dt = dt;
+            // substeps: leapfrog {kick dtau; drift dtau (last dtau/2)} after a
+            // first drift of dtau/2; minimum-norm {kick dtau/2; drift
+            // (1-2 lambda) dtau or 2 lambda dtau alternately (last lambda dtau)}
+            // after a first drift of lambda dtau (its two end drifts merged)
+            const bool mn = A.integrator == 1;
+            const float lam = (float)A.lambda;
+            mc.kick = mn ? 0.5f * dt : dt;
+            mc.r_even = mn ? 1.0f - 2.0f * lam : 1.0f;
+            mc.r_odd = mn ? 2.0f * lam : 1.0f;
+            mc.r_last = mn ? lam : 0.5f;
+            mc.n_sub = mn ? 2 * A.n_md : A.n_md;
             mc.la = v.n - 1 - base;
             mc.first = v.first;
             const int64_t off = v.si.off, wlo = v.g.wlo;
@@ -692,10 +717,11 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                 PH[q] = f2(s_ph[q * NT + tid], s_ph[(q + P) * NT + tid]);
                 PL[q] = f2(0.0f, 0.0f);
             }
+            const float r0 = A.integrator == 1 ? (float)A.lambda : 0.5f;  // first drift
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                const float2 c0 = MASS ? f2(0.5f * dm_at(q), 0.5f * dm_at(q + P))
-                                       : f2(0.5f * dt, 0.5f * dt);
+                const float2 c0 = MASS ? f2(r0 * dm_at(q), r0 * dm_at(q + P))
+                                       : f2(r0 * dt, r0 * dt);
                 cupd2(X[q], XL[q], c0, PH[q]);
             }
         }

@@ -47,6 +47,8 @@ struct Plan {
     int* d_bin_seg = nullptr;    // segment ids, bin-major
     SerInfo* d_ser = nullptr;
     int n_md = 0;
+    int integrator = 0;         // 0 leapfrog, 1 minimum-norm (two forces per step)
+    double lambda = 0.0;        // of the minimum-norm integrator
     bool mixed = false, mass = false;
 };
 
@@ -110,6 +112,8 @@ struct TrajArgs {
     const float* minv;   // optional inverse mass (FP32, packed)
     const int* mass_on;  // optional flag; 0 = use m = 1
     int n_md;
+    int integrator;      // 0 leapfrog (eqs. (6)-(8)), 1 minimum-norm, two forces per step
+    double lambda;       // of the minimum-norm integrator
     double dtau;
     uint64_t seed, traj;
     int* status;
@@ -120,8 +124,10 @@ struct TrajArgs {
 // Build a plan for the series with the given offsets (host, [n+1]).
 // sched_nt / sched_j / sched_tile > 0 fix the tiling, 0 chooses it.
 // Returns false (reason in *why) if no tiling fits.
-bool make_plan(const int64_t* offsets, int n, int n_md, bool mixed, bool mass, int num_sms,
-               int sched_nt, int sched_j, int64_t sched_tile, Plan& plan, const char** why);
+// integrator / lambda: see Plan; the halo is n_md * (forces per step) + 1.
+bool make_plan(const int64_t* offsets, int n, int n_md, int integrator, double lambda, bool mixed,
+               bool mass, int num_sms, int sched_nt, int sched_j, int64_t sched_tile, Plan& plan,
+               const char** why);
 void free_plan(Plan& plan);
 
 cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st);

@@ -61,6 +61,7 @@ def lib():
         L.rsv_reserve.argtypes = [_P, _I64, _I64]
         L.rsv_sync_status.argtypes = [_P, _P]
         L.rsv_set_schedule.argtypes = [_P, _INT, _INT, _I64]
+        L.rsv_set_integrator.argtypes = [_P, _INT, ctypes.c_double]
         L.rsv_action.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
         L.rsv_force.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
         L.rsv_hmc_trajectory.argtypes = [_P, _P, _P, _P, _P, _I64, Theta, _P, _INT,
@@ -79,7 +80,8 @@ def lib():
         L.rsv_timing.argtypes = [_P, _INT]
         L.rsv_stats.argtypes = [_P, _INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                 ctypes.POINTER(ctypes.c_double)]
-        for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule", "rsv_action", "rsv_force",
+        for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule",
+                     "rsv_set_integrator", "rsv_action", "rsv_force",
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
                      "rsv_timing", "rsv_stats", "rsv_gibbs_theta", "rsv_plan_create",
                      "rsv_plan_info", "rsv_hmc_batched"):
@@ -140,6 +142,17 @@ class Context:
 
 def rsv_reserve(ctx: Context, max_T: int, max_series: int = 0):
     _check(lib().rsv_reserve(ctx.handle, int(max_T), int(max_series)))
+
+
+RSV_LEAPFROG, RSV_OMELYAN2 = 0, 1
+RSV_OMELYAN2_LAMBDA = 0.19318332750378357
+
+
+def rsv_set_integrator(ctx: Context, kind="leapfrog", lam: float = 0.0):
+    """Integrator of later trajectories and plans: "leapfrog" or "omelyan2"
+    (lam <= 0: the minimum-norm value)."""
+    k = {"leapfrog": RSV_LEAPFROG, "omelyan2": RSV_OMELYAN2}.get(kind, kind)
+    _check(lib().rsv_set_integrator(ctx.handle, int(k), float(lam)))
 
 
 def rsv_set_schedule(ctx: Context, threads: int = 0, sites_per_thread: int = 0, tile: int = 0):
