@@ -413,12 +413,39 @@ def run_ours(args):
         learned_info["fell_back"] = bool(sampler.fell_back)
         learned_info["window_accept"] = [round(r, 3) for r in sampler.history]
     # comparisons: plain mixed and plain FP64 samplers (identity mass, 100 x 0.005)
-    ident = fp64 = batched = None
+    ident = fp64 = batched = mn = None
     if args.only != "mixed":
         if minv is not None:
             ident = arm("mixed", None, min(args.warmup, 3), min(args.steps, 3))
         fp64 = arm("fp64", None, min(args.warmup, 3), min(args.steps, 3))
         batched = batched_leg(max(3, min(args.steps, 10)))
+        # the minimum-norm integrator (two forces per step) at the plain
+        # sampler's trajectory length (0.5; 2.5 in the learned mass's units):
+        # the fewest steps whose acceptance over 40 trial trajectories
+        # reaches 0.8, identity mass and learned mass
+        def tune_mn(mass, length):
+            h_t = torch.tensor(s.h_true, device=dev)
+            th_t = torch.tensor(s.theta, dtype=torch.float64, device=dev)
+            acc_t = torch.empty(40, dtype=torch.int32, device=dev)
+            for n_try in (3, 4, 5, 6, 8, 10, 12, 15, 20, 30):
+                rsv.rsv_hmc_chain(ctx, h_t.clone(), y, lnrv, th_t.clone(), n_try, length / n_try,
+                                  40, prec="mixed", minv=mass, seed=123, accept_out=acc_t)
+                if float(acc_t.float().mean()) >= 0.8:
+                    return n_try
+            return 30
+        rsv.rsv_set_integrator(ctx, "omelyan2")
+        try:
+            mn = {}
+            for tag, mass, length in (("identity", None, 0.5), ("learned", minv, 2.5)):
+                if tag == "learned" and mass is None:
+                    continue
+                n_mn = tune_mn(mass, length)
+                r = arm("mixed", mass, min(args.warmup, 3), min(args.steps, 3), n_md=n_mn,
+                        dtau=length / n_mn)
+                r["n_md"], r["dtau"] = n_mn, length / n_mn
+                mn[tag] = r
+        finally:
+            rsv.rsv_set_integrator(ctx, "leapfrog")
 
     # end to end through the public API with host buffers: H2D of the step's
     # inputs (h, y, lnRV, theta) from pinned memory, the chain, D2H of h' and
@@ -534,6 +561,15 @@ def run_ours(args):
                 "ess_h_min_per_s": ident["ess_h_min_per_s"],
                 "ess_theta_per_s": ident["ess_theta_per_s"],
                 "accept_rate": ident["accept_rate"]},
+            "mixed_omelyan2": None if mn is None else {
+                tag: {"integrator": "minimum-norm (Omelyan), 2 force evaluations per step",
+                      "mass": tag, "n_md": r["n_md"], "dtau": r["dtau"],
+                      "force_evaluations_per_trajectory": 2 * r["n_md"],
+                      "ms_per_step": r["ms_per_step"],
+                      "ess_h_median_per_s": r["ess_h_median_per_s"],
+                      "ess_h_min_per_s": r["ess_h_min_per_s"],
+                      "ess_theta_per_s": r["ess_theta_per_s"],
+                      "accept_rate": r["accept_rate"]} for tag, r in mn.items()},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
                          "kernel": "k_traj_mixed", "peak_kind": "nominal FP32-lane issue "
