@@ -26,13 +26,18 @@ _lib = None
 
 
 class Theta(ctypes.Structure):
-    """theta = (phi, mu, xi, sigma_eta^2, sigma_u^2), the parameters of eqs. (1)-(3)."""
+    """theta = (phi, mu, xi, sigma_eta^2, sigma_u^2), the parameters of eqs. (1)-(3),
+    and rho = corr(eps_t, eta_t) of the RSV model with leverage (0 if not given)."""
 
     _fields_ = [("phi", ctypes.c_double), ("mu", ctypes.c_double), ("xi", ctypes.c_double),
-                ("sig_eta2", ctypes.c_double), ("sig_u2", ctypes.c_double)]
+                ("sig_eta2", ctypes.c_double), ("sig_u2", ctypes.c_double),
+                ("rho", ctypes.c_double)]
 
     def as_tuple(self):
         return (self.phi, self.mu, self.xi, self.sig_eta2, self.sig_u2)
+
+    def copy(self):
+        return Theta(*self.as_tuple(), self.rho)
 
 
 def build(force: bool = False) -> str:
@@ -220,9 +225,11 @@ def gibbs_theta(h, lnrv, th, seed, series, traj, mask=31):
     """One theta sweep (xi, s_u^2, mu, s_eta^2, phi; mask bits 0..4 select which);
     returns (theta', phi_accepted)."""
     h, lnrv = _f64(h), _f64(lnrv)
-    t = Theta(*theta(th).as_tuple())
+    t = theta(th).copy()
     acc = lib().orc_gibbs_theta(_d(h), _d(lnrv), len(h), ctypes.byref(t), int(seed), int(series),
                                 int(traj), int(mask))
+    if acc < 0:
+        raise ValueError("the theta conditionals assume rho = 0")
     return t.as_tuple(), acc
 
 
@@ -232,7 +239,7 @@ def chain(h, y, lnrv, th, n_md, dtau, seed, n_traj, traj0=0, series=0, update_th
     h = _f64(h).copy()
     y, lnrv = _f64(y), _f64(lnrv)
     T = len(h)
-    t = Theta(*theta(th).as_tuple())
+    t = theta(th).copy()
     mv = None if minv is None else _f64(minv)
     dH = np.empty(n_traj)
     acc = np.empty(n_traj, dtype=np.int32)
@@ -243,5 +250,7 @@ def chain(h, y, lnrv, th, n_md, dtau, seed, n_traj, traj0=0, series=0, update_th
                             int(bool(update_theta)), int(bits), _d(dH),
                             acc.ctypes.data_as(_I), _d(ths), _d(snaps), int(thin),
                             _INTEGRATORS[integrator], float(lam))
+    if n_acc < 0:
+        raise ValueError("the theta update assumes rho = 0")
     return dict(h=h, theta=t.as_tuple(), dH=dH, accept=acc, thetas=ths, snaps=snaps,
                 n_accept=int(n_acc))

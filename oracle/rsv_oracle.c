@@ -32,8 +32,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* theta of eqs. (1)-(3), and rho = corr(eps_t, eta_t) of the RSV model with
+ * leverage (Takahashi, Omori and Watanabe, Comput. Stat. Data Anal. 53 (2009)
+ * 2404, the RSV model the paper cites in Sec. 2); rho = 0 is eqs. (1)-(3). */
 typedef struct {
-    double phi, mu, xi, sig_eta2, sig_u2;
+    double phi, mu, xi, sig_eta2, sig_u2, rho;
 } orc_theta;
 
 /* ------------------------------------------------------------------------ */
@@ -54,8 +57,13 @@ static double sum_get(const orc_sum* a) { return a->s + a->c; }
 /* Action S(h) = -ln f(h | theta, y, lnRV), constants dropped (Sec. 3 with    */
 /* the model of eqs. (1)-(3)).  Per-site split used for dH:                  */
 /*   s_t = h_t/2 + (y_t^2/2) e^{-h_t} + (lnRV_t - xi - h_t)^2 / (2 s_u^2)     */
-/*       + [t < T-1] (x_{t+1} - phi x_t)^2 / (2 s_eta^2)                      */
-/*       + [t = 0]   (1 - phi^2) x_0^2 / (2 s_eta^2),      x_t = h_t - mu.    */
+/*       + [t < T-1] d_t^2 / (2 s_eta^2 (1 - rho^2))                          */
+/*       + [t = 0]   (1 - phi^2) x_0^2 / (2 s_eta^2),      x_t = h_t - mu,    */
+/*   d_t = x_{t+1} - phi x_t - rho s_eta eps_t,  eps_t = y_t e^{-h_t/2}.      */
+/* With leverage (rho != 0) the pair (eps_t, eta_t) is bivariate normal with  */
+/* correlation rho, so eta_t | eps_t ~ N(rho s_eta eps_t, s_eta^2 (1-rho^2)); */
+/* the marginal of eta_t, hence the stationary law of h_1, is unchanged.      */
+/* rho = 0 gives the d_t = x_{t+1} - phi x_t of eq. (3).                      */
 /* ------------------------------------------------------------------------ */
 double orc_site_action(const double* h, const double* y, const double* lnrv,
                        long T, orc_theta th, long t)
@@ -66,11 +74,13 @@ double orc_site_action(const double* h, const double* y, const double* lnrv,
     /* eq. (2): lnRV_t ~ N(xi + h_t, s_u^2) */
     double r = lnrv[t] - th.xi - ht;
     s += r * r / (2.0 * th.sig_u2);
-    /* eq. (3): h_{t+1} ~ N(mu + phi (h_t - mu), s_eta^2) */
+    /* eq. (3): h_{t+1} ~ N(mu + phi (h_t - mu), s_eta^2), given eps_t with
+     * leverage: N(mu + phi (h_t - mu) + rho s_eta eps_t, s_eta^2 (1 - rho^2)) */
     double x = ht - th.mu;
     if (t + 1 < T) {
-        double e = (h[t + 1] - th.mu) - th.phi * x;
-        s += e * e / (2.0 * th.sig_eta2);
+        double eps = y[t] * exp(-0.5 * ht);
+        double d = (h[t + 1] - th.mu) - th.phi * x - th.rho * sqrt(th.sig_eta2) * eps;
+        s += d * d / (2.0 * th.sig_eta2 * (1.0 - th.rho * th.rho));
     }
     /* stationary law of h_1: N(mu, s_eta^2 / (1 - phi^2)) */
     if (t == 0) s += (1.0 - th.phi * th.phi) * x * x / (2.0 * th.sig_eta2);
@@ -92,28 +102,35 @@ double orc_action(const double* h, const double* y, const double* lnrv,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Gradient dS/dh_t (the dH/dh_i of eq. (7)).                                */
-/*   dS/dh_t = 1/2 - (y_t^2/2) e^{-h_t} - (lnRV_t - xi - h_t)/s_u^2 + AR_t    */
-/*   AR_t    = [(1+phi^2) x_t - phi (x_{t-1} + x_{t+1})] / s_eta^2 (interior) */
-/*   AR_0    = (x_0 - phi x_1) / s_eta^2,  AR_{T-1} = (x_{T-1} - phi x_{T-2}) */
-/*             / s_eta^2,  and AR_0 = (1 - phi^2) x_0 / s_eta^2 when T = 1.  */
+/* Gradient dS/dh_t (the dH/dh_i of eq. (7)), term by term from s_t above:   */
+/*   dS/dh_t = 1/2 - (y_t^2/2) e^{-h_t} - (lnRV_t - xi - h_t)/s_u^2 + AR_t,   */
+/*   AR_t = [t = 0] (1 - phi^2) x_0 / s_eta^2                                */
+/*        + [t < T-1] B d_t (rho s_eta eps_t / 2 - phi)     (from d_t)        */
+/*        + [t > 0]   B d_{t-1}                             (from d_{t-1}),   */
+/*   B = 1 / (s_eta^2 (1 - rho^2)),  d d_t/d h_t = -phi + rho s_eta eps_t/2.  */
+/* With rho = 0 the interior rows are [(1+phi^2) x_t - phi (x_{t-1} +        */
+/* x_{t+1})] / s_eta^2, the end rows (x_0 - phi x_1) / s_eta^2 and            */
+/* (x_{T-1} - phi x_{T-2}) / s_eta^2, and (1 - phi^2) x_0 / s_eta^2 for T = 1.*/
 /* ------------------------------------------------------------------------ */
+static double innovation(const double* h, const double* y, orc_theta th, long t)
+{
+    double eps = y[t] * exp(-0.5 * h[t]);
+    return (h[t + 1] - th.mu) - th.phi * (h[t] - th.mu) - th.rho * sqrt(th.sig_eta2) * eps;
+}
+
 void orc_force(const double* h, const double* y, const double* lnrv,
                long T, orc_theta th, double* F)
 {
-    const double phi = th.phi, mu = th.mu;
+    const double phi = th.phi, mu = th.mu, rs = th.rho * sqrt(th.sig_eta2);
+    const double B = 1.0 / (th.sig_eta2 * (1.0 - th.rho * th.rho));
     for (long t = 0; t < T; ++t) {
-        double x = h[t] - mu, ar;
-        if (T == 1) {
-            ar = (1.0 - phi * phi) * x;
-        } else if (t == 0) {
-            ar = x - phi * (h[1] - mu);
-        } else if (t == T - 1) {
-            ar = x - phi * (h[T - 2] - mu);
-        } else {
-            ar = (1.0 + phi * phi) * x - phi * ((h[t - 1] - mu) + (h[t + 1] - mu));
+        double x = h[t] - mu, ar = 0.0;
+        if (t == 0) ar += (1.0 - phi * phi) * x / th.sig_eta2;
+        if (t + 1 < T) {
+            double eps = y[t] * exp(-0.5 * h[t]);
+            ar += B * innovation(h, y, th, t) * (0.5 * rs * eps - phi);
         }
-        ar /= th.sig_eta2;
+        if (t > 0) ar += B * innovation(h, y, th, t - 1);
         F[t] = 0.5 - 0.5 * y[t] * y[t] * exp(-h[t])
              - (lnrv[t] - th.xi - h[t]) / th.sig_u2 + ar;
     }
@@ -377,11 +394,13 @@ static double stream_gamma(orc_stream* s, double alpha)
 /* Every sum is taken directly over the series with the current values.     */
 /* mask selects the components updated (bit 0 xi, 1 s_u^2, 2 mu, 3 s_eta^2, */
 /* 4 phi); the draws of a skipped component are not consumed.               */
-/* Returns 1 if the phi proposal was accepted.                              */
+/* Returns 1 if the phi proposal was accepted, -1 (theta untouched) under   */
+/* leverage, where these conditionals are not the model's.                  */
 /* ------------------------------------------------------------------------ */
 int orc_gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
                     uint64_t seed, uint64_t series, uint64_t traj, int mask)
 {
+    if (th->rho != 0.0) return -1;
     orc_stream st;
     stream_init(&st, seed, series, traj);
     double Td = (double)T;
@@ -463,6 +482,7 @@ int orc_gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
 /* the theta update.  Records dH, accept and theta per trajectory, and h    */
 /* after every `thin`-th trajectory into snaps (n_traj/thin rows of T).      */
 /* bits selects the uniform width used for the momenta (53 FP64, 24 FP32).   */
+/* Returns -1 if a theta update is asked for under leverage.                */
 /* ------------------------------------------------------------------------ */
 long orc_chain(double* h, const double* y, const double* lnrv, long T, orc_theta* th,
                const double* minv, int n_md, double dtau, uint64_t seed, uint64_t series,
@@ -470,6 +490,7 @@ long orc_chain(double* h, const double* y, const double* lnrv, long T, orc_theta
                double* dH_out, int* acc_out, double* theta_out, double* snaps, long thin,
                int integrator, double lambda)
 {
+    if (update_theta && th->rho != 0.0) return -1;
     size_t n = (size_t)(T > 0 ? T : 1);
     double* p = (double*)malloc(sizeof(double) * n);
     long n_acc = 0;

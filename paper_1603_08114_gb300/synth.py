@@ -63,6 +63,29 @@ def rsv_series(T: int, theta=THETA_STD, seed: int = 0) -> Series:
     return Series(h_true=h, y=y, lnrv=lnrv, theta=(phi, mu, xi, se2, su2), h0=lnrv - xi)
 
 
+#: leverage of the RSV-with-leverage workloads: corr(eps_t, eta_t), negative as
+#: for equity returns (a fall in price raises the next volatility)
+RHO_STD = -0.4
+
+
+def rsv_series_leverage(T: int, theta=THETA_STD, rho: float = RHO_STD, seed: int = 0) -> Series:
+    """One synthetic series of the RSV model with leverage: eqs. (1)-(3) with
+    corr(eps_t, eta_t) = rho.  Draw order: h_1 ~ N(mu, s_eta^2 / (1 - phi^2));
+    eps_1..T ~ N(0, 1); z_1..T-1 ~ N(0, 1); u_1..T ~ N(0, s_u^2);
+    eta_t = s_eta (rho eps_t + sqrt(1 - rho^2) z_t)."""
+    phi, mu, xi, se2, su2 = (float(v) for v in theta)
+    rng = np.random.default_rng(seed)
+    h1 = rng.normal(mu, np.sqrt(se2 / (1.0 - phi * phi)))
+    eps = rng.normal(0.0, 1.0, T)
+    z = rng.normal(0.0, 1.0, T - 1)
+    u = rng.normal(0.0, np.sqrt(su2), T)
+    eta = np.sqrt(se2) * (rho * eps[:-1] + np.sqrt(1.0 - rho * rho) * z)
+    h = _ar1(h1 - mu, eta, phi) + mu
+    y = np.exp(h / 2.0) * eps
+    lnrv = xi + h + u
+    return Series(h_true=h, y=y, lnrv=lnrv, theta=(phi, mu, xi, se2, su2), h0=lnrv - xi)
+
+
 def standard_normals(n: int, seed: int) -> np.ndarray:
     """Seeded N(0,1) draws (momenta passed in explicitly by parity tests)."""
     return np.random.default_rng(seed).standard_normal(n)
