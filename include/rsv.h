@@ -111,6 +111,24 @@ typedef enum rsv_integrator { RSV_LEAPFROG = 0, RSV_OMELYAN2 = 1 } rsv_integrato
 #define RSV_OMELYAN2_LAMBDA 0.19318332750378357
 rsv_status rsv_set_integrator(rsv_ctx* ctx, rsv_integrator kind, double lambda);
 
+/* ---- model: leverage -------------------------------------------------------
+ * The RSV model with leverage: eqs. (1)-(3) of Sec. 2 with corr(eps_t, eta_t)
+ * = rho, the form of the RSV model in the reference the paper cites for it
+ * (Takahashi, Omori and Watanabe, Comput. Stat. Data Anal. 53 (2009) 2404).
+ * Given eps_t = y_t e^{-h_t/2}, eta_t is N(rho s_eta eps_t, s_eta^2 (1-rho^2)),
+ * so the AR term of S becomes
+ *   sum_{t<T} d_t^2 / (2 s_eta^2 (1 - rho^2)),
+ *   d_t = h_{t+1} - mu - phi (h_t - mu) - rho s_eta y_t e^{-h_t/2},
+ * and dS/dh follows term by term; the law of h_1 is unchanged.  rho applies to
+ * every later rsv_action, rsv_force, rsv_hmc_trajectory and rsv_hmc_chain call
+ * of this context, and to plans created afterwards (a plan made with rho = 0
+ * cannot run with rho != 0 or the reverse: RSV_EINVAL).  rho = 0 restores
+ * eqs. (1)-(3) exactly.  The theta update (rsv_gibbs_theta, update_theta of
+ * rsv_hmc_chain) draws from the conditionals of the rho = 0 model and returns
+ * RSV_EINVAL while rho != 0.  rsv_action_noalloc has no context and is always
+ * the rho = 0 model.  |rho| >= 1 or NaN gives RSV_EINVAL. */
+rsv_status rsv_set_leverage(rsv_ctx* ctx, double rho);
+
 /* ---- S(h) -----------------------------------------------------------------
  * S(h) of Sec. 3 (see above), FP64, deterministic reduction order.
  * h, y, lnrv: [T] FP64.  S_out: device FP64 scalar.  T >= 1. */

@@ -186,6 +186,14 @@ rsv_status rsv_set_integrator(rsv_ctx* c, rsv_integrator kind, double lambda)
     return RSV_OK;
 }
 
+rsv_status rsv_set_leverage(rsv_ctx* c, double rho)
+{
+    if (!c) return fail(RSV_EINVAL, "null context");
+    if (!(rho > -1.0 && rho < 1.0)) return fail(RSV_EINVAL, "rho must be in (-1, 1)");
+    c->rho = rho;
+    return RSV_OK;
+}
+
 rsv_status rsv_set_schedule(rsv_ctx* c, int threads, int sites_per_thread, int64_t tile)
 {
     if (!c) return fail(RSV_EINVAL, "null context");
@@ -227,7 +235,9 @@ rsv_status rsv_action(rsv_ctx* c, const double* h, const double* y, const double
     if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
     if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
     if ((st = ctx_ensure_partials(c, action_grid(T))) != RSV_OK) return st;
-    cudaError_t e = counted(c, launch_action, h, y, lnrv, T, to_dev(theta), c->partials.as<double>(),
+    ThetaD th = to_dev(theta);
+    th.rho = c->rho;
+    cudaError_t e = counted(c, launch_action, h, y, lnrv, T, th, c->partials.as<double>(),
                                   reinterpret_cast<unsigned*>(c->ints.as<int>() + kActionCounter),
                                   S_out, (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "action kernel");
@@ -242,7 +252,9 @@ rsv_status rsv_force(rsv_ctx* c, const double* h, const double* y, const double*
     if (F_out == h) return fail(RSV_EINVAL, "F_out must not alias h");
     if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
     if (!theta_ok(theta)) return fail(RSV_EINVAL, "invalid theta");
-    cudaError_t e = counted(c, launch_force, h, y, lnrv, T, to_dev(theta), F_out, (cudaStream_t)stream);
+    ThetaD th = to_dev(theta);
+    th.rho = c->rho;
+    cudaError_t e = counted(c, launch_force, h, y, lnrv, T, th, F_out, (cudaStream_t)stream);
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "force kernel");
 }
 
@@ -269,6 +281,8 @@ rsv_status rsv_gibbs_theta(rsv_ctx* c, const double* h, const double* lnrv, int6
     if (T < 1) return fail(RSV_EINVAL, "T must be >= 1");
     if (mask < 0 || mask > 31) return fail(RSV_EINVAL, "mask must be in 0..31");
     if (prec != RSV_FP64 && prec != RSV_MIXED) return fail(RSV_EINVAL, "bad precision");
+    if (c->rho != 0.0)
+        return fail(RSV_EINVAL, "the theta update is for the model without leverage (rho = 0)");
     const bool mixed = prec == RSV_MIXED;
     if ((st = c->gibbs.ensure((size_t)gibbs_grid(T) * 8 * sizeof(double))) != RSV_OK) return st;
     if (mixed && ((st = c->fbuf0.ensure((size_t)T * 8)) != RSV_OK ||
@@ -284,7 +298,7 @@ rsv_status rsv_gibbs_theta(rsv_ctx* c, const double* h, const double* lnrv, int6
                          (cudaStream_t)stream)) != cudaSuccess ||
             (e = counted(c, launch_h_to_ff, lnrv, c->lr_f.as<float2>(), T,
                          (cudaStream_t)stream)) != cudaSuccess ||
-            (e = counted(c, launch_theta_prep, (const double*)theta, ThetaD{}, 1,
+            (e = counted(c, launch_theta_prep, (const double*)theta, ThetaD{}, 1, 0.0,
                          c->theta_f.as<MixedTheta>(), (cudaStream_t)stream)) != cudaSuccess)
             return cuda_fail(e, "theta update set-up");
         g.h0f = c->fbuf0.as<float2>();

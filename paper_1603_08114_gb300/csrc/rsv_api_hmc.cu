@@ -48,7 +48,7 @@ rsv_status single_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, c
 {
     for (auto& e : c->plans) {
         if (e.T == T && e.n_md == n_md && e.mixed == mixed && e.mass == mass &&
-            e.integrator == c->integrator && e.lambda == c->lambda &&
+            e.lev == (c->rho != 0.0) && e.integrator == c->integrator && e.lambda == c->lambda &&
             e.nt == c->sched_nt && e.j == c->sched_j && e.tile == c->sched_tile) {
             *out = &e.plan;
             return RSV_OK;
@@ -62,11 +62,12 @@ rsv_status single_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, c
         c->plans.erase(c->plans.begin());
     }
     const int64_t off[2] = {0, T};
-    rsv_ctx::Cached e{T,          n_md,        c->integrator, c->lambda, mixed,
-                      mass,       c->sched_nt, c->sched_j,    c->sched_tile, Plan()};
+    const bool lev = c->rho != 0.0;
+    rsv_ctx::Cached e{T,    n_md, c->integrator, c->lambda,  mixed,         mass,
+                      lev,  c->sched_nt, c->sched_j, c->sched_tile, Plan()};
     const char* why = "";
-    if (!make_plan(off, 1, n_md, c->integrator, c->lambda, mixed, mass, c->num_sms, c->sched_nt,
-                   c->sched_j, c->sched_tile, e.plan, &why))
+    if (!make_plan(off, 1, n_md, c->integrator, c->lambda, mixed, mass, lev, c->num_sms,
+                   c->sched_nt, c->sched_j, c->sched_tile, e.plan, &why))
         return fail(RSV_EINVAL, "%s", why);
     c->plans.push_back(e);
     *out = &c->plans.back().plan;
@@ -163,6 +164,7 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
     a.n_md = P.n_md;
     a.integrator = P.integrator;
     a.lambda = P.lambda;
+    a.rho = c->rho;
     a.dtau = o.dtau;
     a.seed = o.seed;
     a.status = ints + kStatus;
@@ -174,7 +176,7 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
         a.h0f = c->fbuf0.as<float2>();
         a.h1f = c->fbuf1.as<float2>();
         a.theta_f = c->theta_f.as<MixedTheta>();
-        if ((e = counted(c, launch_theta_prep, o.theta, o.th_inline, (int)n,
+        if ((e = counted(c, launch_theta_prep, o.theta, o.th_inline, (int)n, c->rho,
                          c->theta_f.as<MixedTheta>(), s)) != cudaSuccess)
             return cuda_fail(e, "theta prep kernel");
         if ((e = counted(c, launch_prep_mixed, o.y, o.lnrv, c->a_f.as<float>(),
@@ -314,6 +316,8 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
     if (n_traj < 0) return fail(RSV_EINVAL, "n_traj must be >= 0");
     if (snaps && thin < 1) return fail(RSV_EINVAL, "thin must be >= 1 with snapshots");
     if (fallback_window < 0) return fail(RSV_EINVAL, "fallback_window must be >= 0");
+    if (update_theta && c->rho != 0.0)
+        return fail(RSV_EINVAL, "the theta update is for the model without leverage (rho = 0)");
     const Plan* P = nullptr;
     if ((st = single_plan(c, T, n_md, prec == RSV_MIXED, minv != nullptr, &P)) != RSV_OK) return st;
     RunOpts o;
@@ -355,8 +359,8 @@ rsv_status rsv_plan_create(rsv_ctx* c, const int64_t* offsets, int64_t n_series,
     p->device = c->device;
     const char* why = "";
     if (!make_plan(offsets, (int)n_series, n_md, c->integrator, c->lambda, prec == RSV_MIXED,
-                   with_mass != 0, c->num_sms, c->sched_nt, c->sched_j, c->sched_tile, p->plan,
-                   &why)) {
+                   with_mass != 0, c->rho != 0.0, c->num_sms, c->sched_nt, c->sched_j,
+                   c->sched_tile, p->plan, &why)) {
         delete p;
         return fail(RSV_EINVAL, "%s", why);
     }
@@ -398,6 +402,8 @@ rsv_status rsv_hmc_batched(rsv_ctx* c, rsv_plan* plan, double* h, double* p, con
     if (n_traj < 0) return fail(RSV_EINVAL, "n_traj must be >= 0");
     if ((p || log_u) && n_traj != 1) return fail(RSV_EINVAL, "p and log_u need n_traj = 1");
     if ((minv != nullptr) != plan->plan.mass) return fail(RSV_EINVAL, "minv does not match the plan");
+    if ((c->rho != 0.0) != plan->plan.lev)
+        return fail(RSV_EINVAL, "the plan was made for another leverage setting");
     RunOpts o;
     memset(&o, 0, sizeof(o));
     o.h = h;

@@ -52,7 +52,7 @@ struct rsv_ctx {
         int n_md;
         int integrator;
         double lambda;
-        bool mixed, mass;
+        bool mixed, mass, lev;
         int nt, j;
         int64_t tile;
         rsv::Plan plan;
@@ -62,6 +62,7 @@ struct rsv_ctx {
     int sched_nt = 0, sched_j = 0;  // rsv_set_schedule override (0 = automatic)
     int integrator = 0;             // rsv_set_integrator (0 leapfrog)
     double lambda = 0.0;
+    double rho = 0.0;               // rsv_set_leverage (0: no leverage)
     int64_t sched_tile = 0;
     // accounting: kernel launches, and CUDA events around trajectory kernels
     int64_t launches = 0;

@@ -222,13 +222,16 @@ __device__ __forceinline__ double block_sum(double v, double* red)
     return s;
 }
 
-// Theta as stored on the device: (phi, mu, xi, sigma_eta^2, sigma_u^2).
+// Theta as stored on the device: (phi, mu, xi, sigma_eta^2, sigma_u^2), and
+// the leverage rho = corr(eps_t, eta_t) of the RSV model with leverage (a
+// context setting, not stored with theta; 0 is the model of eqs. (1)-(3)).
 struct ThetaD {
     double phi, mu, xi, se2, su2;
+    double rho = 0.0;
 };
-__device__ __forceinline__ ThetaD load_theta(const double* th)
+__device__ __forceinline__ ThetaD load_theta(const double* th, double rho = 0.0)
 {
-    return {th[0], th[1], th[2], th[3], th[4]};
+    return {th[0], th[1], th[2], th[3], th[4], rho};
 }
 
 }  // namespace rsv

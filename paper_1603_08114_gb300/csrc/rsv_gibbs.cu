@@ -347,6 +347,14 @@ __device__ MixedTheta mixed_theta_f(const float (&t)[5])
     const float hu = 0.5f / su2, he = 0.5f / se2;
     m.hu = ff{hu, fmaf(-hu, su2, 0.5f) / su2};
     m.he = ff{he, fmaf(-he, se2, 0.5f) / se2};
+    // the leverage constants at rho = 0 (the theta update is for eqs. (1)-(3))
+    m.cst = 0.0f;
+    m.ia = 1.0f;
+    m.omr = 1.0f;
+    m.rsb = 0.0f;
+    m.ibf = se2;
+    m.st = ff_sub(ff{1.0f, 0.0f}, two_prod(phi, phi));
+    for (int i = 0; i < 9; ++i) m.pad[i] = 0.f;
     return m;
 }
 

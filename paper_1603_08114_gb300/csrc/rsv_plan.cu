@@ -26,12 +26,12 @@ const int kJ_fp64[] = {4, 8, 16, 28};
 const int kJ_mixed[] = {4, 8, 12, 16, 20};
 const int kNJ_fp64 = 4, kNJ_mixed = 5;
 
-// mixed: (a, k) float2 + x0 (hi, lo) + p0 per site (+ dtau/m with a mass);
-// FP64: a', kc (+ 1/m) per site
-size_t smem_for(bool mixed, bool mass, int nt, int j)
+// mixed: (a, k) float2 + x0 (hi, lo) + p0 per site (+ dtau/m with a mass,
+// + the leverage v with leverage); FP64: a' (or y e^{-mu/2}), kc (+ 1/m) per site
+size_t smem_for(bool mixed, bool mass, bool lev, int nt, int j)
 {
     const size_t W = (size_t)nt * (size_t)j;
-    return mixed ? (5 + (mass ? 1 : 0)) * W * sizeof(float)
+    return mixed ? (5 + (mass ? 1 : 0) + (lev ? 1 : 0)) * W * sizeof(float)
                  : (2 + (mass ? 1 : 0)) * W * sizeof(double);
 }
 
@@ -58,8 +58,8 @@ void free_plan(Plan& p)
 }
 
 bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambda, bool mixed,
-               bool mass, int num_sms, int sched_nt, int sched_j, int64_t sched_tile, Plan& P,
-               const char** why)
+               bool mass, bool lev, int num_sms, int sched_nt, int sched_j, int64_t sched_tile,
+               Plan& P, const char** why)
 {
     // one site of staleness per force evaluation
     const int64_t K = (int64_t)n_md * (integrator == 1 ? 2 : 1) + 1;
@@ -84,7 +84,7 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
     if (sched_nt > 0) {
         if (!valid_j(mixed, sched_j) || sched_nt % 32 || sched_nt > ntmax(mixed, sched_j) ||
             sched_tile < 1 || sched_tile + 2 * K + 3 > (int64_t)sched_nt * sched_j ||
-            smem_for(mixed, mass, sched_nt, sched_j) > smem_cap) {
+            smem_for(mixed, mass, lev, sched_nt, sched_j) > smem_cap) {
             *why = "the fixed schedule does not fit this call";
             return false;
         }
@@ -102,7 +102,7 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
             const int tmax = ntmax(mixed, js[ji]);
             for (int t = 32; t <= tmax; t += 32) {
                 const int64_t cap = (int64_t)t * js[ji];
-                if (smem_for(mixed, mass, t, js[ji]) > smem_cap) continue;
+                if (smem_for(mixed, mass, lev, t, js[ji]) > smem_cap) continue;
                 const int64_t tl = cap - 2 * K - 3;
                 int64_t bins;
                 int64_t use_tile;
@@ -127,7 +127,8 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
                     }
                     // blocks resident per SM share it: an SM's work per wave
                     // is bps windows
-                    int bps = blocks_per_sm(mixed, mass, js[ji], t, smem_for(mixed, mass, t, js[ji]));
+                    int bps = blocks_per_sm(mixed, mass, lev, js[ji], t,
+                                            smem_for(mixed, mass, lev, t, js[ji]));
                     if (bps < 1) continue;
                     const int64_t waves = (b + (int64_t)num_sms * bps - 1) / ((int64_t)num_sms * bps);
                     double cost = (double)waves * (double)cap * bps;
@@ -255,7 +256,7 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
     p.nt = nt;
     p.j = j;
     p.nbins = nbins;
-    p.smem = smem_for(mixed, mass, nt, j);
+    p.smem = smem_for(mixed, mass, lev, nt, j);
     p.nsegs = (int64_t)segs.size();
     p.nseries = n;
     p.nsplit = nsplit;
@@ -265,7 +266,8 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
     p.lambda = lambda;
     p.mixed = mixed;
     p.mass = mass;
-    int bps = blocks_per_sm(mixed, mass, j, nt, p.smem);
+    p.lev = lev;
+    int bps = blocks_per_sm(mixed, mass, lev, j, nt, p.smem);
     if (bps < 1) bps = 1;
     p.grid = std::min(nbins, num_sms * bps);
 

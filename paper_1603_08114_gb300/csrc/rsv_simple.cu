@@ -3,6 +3,9 @@
 // S(h) and dS/dh of the RSV model (arXiv:1603.08114, Sec. 3 with eqs. (1)-(3));
 // both are streaming kernels bound by HBM bandwidth: dS/dh reads h (and its
 // two neighbours, served from L1/L2), y and lnRV and writes F, 32 B per site.
+// With leverage (th.rho != 0, the RSV model with corr(eps_t, eta_t) = rho of
+// the RSV reference cited in Sec. 2) the AR term of site t is
+// d_t^2 / (2 s_eta^2 (1 - rho^2)), d_t = x_{t+1} - phi x_t - rho s_eta y_t e^{-h_t/2}.
 #include <cmath>
 
 #include "rsv_device.cuh"
@@ -12,16 +15,34 @@ namespace rsv {
 
 namespace {
 
+// d_t of the leverage model (t < T-1)
+__device__ __forceinline__ double lev_innovation(const double* h, const double* y, int64_t t,
+                                                 const ThetaD& th, double rs)
+{
+    return (h[t + 1] - th.mu) - th.phi * (h[t] - th.mu) - rs * (y[t] * exp(-0.5 * h[t]));
+}
+
 __global__ void __launch_bounds__(256) k_force(const double* __restrict__ h,
                                                const double* __restrict__ y,
                                                const double* __restrict__ lnrv, int64_t T,
                                                ThetaD th, double* __restrict__ F)
 {
     const double phi = th.phi, mu = th.mu, ie = 1.0 / th.se2, iu = 1.0 / th.su2;
+    const double rs = th.rho * sqrt(th.se2), B = 1.0 / (th.se2 * (1.0 - th.rho * th.rho));
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
         const double ht = h[t], x = ht - mu;
         double ar;
+        if (th.rho != 0.0) {
+            // derivative of the terms of s_t and s_{t-1} that hold h_t
+            double g = t == 0 ? (1.0 - phi * phi) * x * ie : 0.0;
+            if (t + 1 < T)
+                g += B * lev_innovation(h, y, t, th, rs) * (0.5 * rs * y[t] * exp(-0.5 * ht) - phi);
+            if (t > 0) g += B * lev_innovation(h, y, t - 1, th, rs);
+            const double yt = y[t];
+            F[t] = 0.5 - 0.5 * yt * yt * exp(-ht) - (lnrv[t] - th.xi - ht) * iu + g;
+            continue;
+        }
         if (T == 1) {
             ar = (1.0 - phi * phi) * x;
         } else if (t == 0) {
@@ -48,6 +69,7 @@ __global__ void __launch_bounds__(256) k_action(const double* __restrict__ h,
     __shared__ double red[32];
     __shared__ int s_last;
     const double phi = th.phi, mu = th.mu, ie = 1.0 / th.se2, iu = 1.0 / th.su2;
+    const double rs = th.rho * sqrt(th.se2), B = 1.0 / (th.se2 * (1.0 - th.rho * th.rho));
     double acc = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -56,8 +78,13 @@ __global__ void __launch_bounds__(256) k_action(const double* __restrict__ h,
         double s = 0.5 * ht + 0.5 * yt * yt * exp(-ht) + 0.5 * iu * r * r;
         const double x = ht - mu;
         if (t + 1 < T) {
-            const double e = (h[t + 1] - mu) - phi * x;
-            s += 0.5 * ie * e * e;
+            if (th.rho != 0.0) {
+                const double d = lev_innovation(h, y, t, th, rs);
+                s += 0.5 * B * d * d;
+            } else {
+                const double e = (h[t + 1] - mu) - phi * x;
+                s += 0.5 * ie * e * e;
+            }
         }
         if (t == 0) s += 0.5 * ie * (1.0 - phi * phi) * x * x;
         acc += s;

@@ -26,6 +26,14 @@
 // stencil (1+phi^2) x_t - phi (x_{t-1} + x_{t+1}) inside the series).  The
 // FP64 kernel uses this innovation form; the mixed kernel the equivalent
 // three-point form with ghost neighbours (see mixed_steps).
+//
+// LEV instantiations take the RSV model with leverage, corr(eps_t, eta_t) =
+// rho (the RSV reference cited in Sec. 2): with eps_t = y_t e^{-h_t/2},
+//   S holds d_t^2 / (2 s_eta^2 (1 - rho^2)),  d_t = e_t - rho s_eta eps_t,
+//   dS/dh_t = ... + B [d_{t-1} + d_t (rho s_eta eps_t / 2 - phi)],
+//   B = 1 / (s_eta^2 (1 - rho^2)),
+// and the y-term (y^2/2) e^{-h} = eps^2 / 2; the stationary term of h_1 is
+// unchanged.
 #include <cmath>
 
 #include "rsv_device.cuh"
@@ -105,6 +113,7 @@ __device__ __forceinline__ void view_of(const TrajArgs& A, const int* s_wseg, Vi
         v.g = A.segs[v.sid];
         v.si = A.ser[v.g.series];
         v.th = A.theta ? load_theta(A.theta + 5 * (int64_t)v.g.series) : A.th_inline;
+        v.th.rho = A.rho;
         v.cur = A.ser_cur ? *(volatile int*)(A.ser_cur + v.g.series) : 0;
     } else {
         // idle warp: an empty segment with harmless parameters
@@ -253,9 +262,9 @@ __device__ __forceinline__ void segment_decisions_ff(const TrajArgs& A, const Vi
 
 // ---------------------------------------------------------------------------
 // FP64 path.  Dynamic shared memory (slot-major, index j*NT + tid):
-// a'[W], kc[W], and 1/m [W] with a mass.
+// a'[W] (with leverage y e^{-mu/2} instead), kc[W], and 1/m [W] with a mass.
 // ---------------------------------------------------------------------------
-template <int J, bool MASS>
+template <int J, bool MASS, bool LEV>
 __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -276,8 +285,13 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
         const ThetaD th = v.th;
         const double phi = th.phi, mu = th.mu;
         const double ie = 1.0 / th.se2, iu = 1.0 / th.su2;
-        const double emu = exp(-mu);
+        const double emu = exp(-mu), emh = exp(-0.5 * mu);
         const double st0 = 1.0 - phi * phi;
+        // leverage: rs = rho s_eta, B = 1/(s_eta^2 (1 - rho^2)); B e_{-1} is the
+        // stationary row (1 - phi^2) x_0 / s_eta^2
+        const double rho = LEV ? th.rho : 0.0;
+        const double rs = rho * sqrt(th.se2), ib = LEV ? 1.0 / (th.se2 * (1.0 - rho * rho)) : ie;
+        const double stB = LEV ? st0 * (1.0 - rho * rho) : st0;
         const int64_t off = v.si.off, wlo = v.g.wlo;
         double* hin = v.cur ? A.h1d : A.h0d;
         double* hout = v.g.split ? (v.cur ? A.h0d : A.h1d) : hin;
@@ -292,7 +306,7 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
             const double yv = act ? A.y[s] : 0.0;
             const double lr = act ? A.lnrv[s] : th.xi + mu;
             x[j] = hv - mu;
-            s_a[j * NT + tid] = 0.5 * yv * yv * emu;
+            s_a[j * NT + tid] = LEV ? yv * emh : 0.5 * yv * yv * emu;
             s_kc[j * NT + tid] = 0.5 - ((lr - th.xi) - mu) * iu;
             if (MASS) s_mi[j * NT + tid] = (act && mass_on) ? (double)A.minv[s] : 1.0;
         }
@@ -317,24 +331,37 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
             }
         }
         __syncthreads();
+        // leverage: y e^{-mu/2} of the left neighbour site (none at a window start)
+        const double yL = (LEV && !v.first) ? s_a[(J - 1) * NT + tid - 1] : 0.0;
+
+        // eps_j = y_j e^{-h_j/2} and d_j = e_j - rs eps_j of this thread's run
+        // (leverage only)
+        auto lev_terms = [&](const double (&xx)[J], double (&eps)[J], double (&e)[J]) {
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                eps[j] = s_a[j * NT + tid] * exp(-0.5 * xx[j]);
+                if (!(edge_thread && j == la)) e[j] = fma(-rs, eps[j], e[j]);
+            }
+        };
 
         // H restricted to this thread's owned sites (x coordinates; the
         // constant mu/2 per site cancels in dH).
         int par = 0;
         auto owned_energy = [&](double& acc) {
-            double xL, xR, e[J];
+            double xL, xR, e[J], eps[J];
             exchange(x[0], x[J - 1], xL, xR, s_edge + par * 2 * nw, nw);
             par ^= 1;
             if (edge_thread) innovations<J, double, true>(x, xR, phi, la, e);
             else innovations<J, double, false>(x, xR, phi, la, e);
+            if (LEV) lev_terms(x, eps, e);
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const int64_t s = wlo + base + j;
                 if (v.sid >= 0 && s >= v.g.lo && s < v.g.hi) {
                     const double cp = (A.lnrv[off + s] - th.xi) - mu;
                     const double r = cp - x[j];
-                    double val = 0.5 * x[j] + s_a[j * NT + tid] * exp(-x[j]) + 0.5 * iu * r * r +
-                                 0.5 * ie * e[j] * e[j];
+                    const double ey = LEV ? 0.5 * eps[j] * eps[j] : s_a[j * NT + tid] * exp(-x[j]);
+                    double val = 0.5 * x[j] + ey + 0.5 * iu * r * r + 0.5 * ib * e[j] * e[j];
                     if (s == 0) val += 0.5 * ie * st0 * x[j] * x[j];
                     const double mi = MASS ? s_mi[j * NT + tid] : 1.0;
                     val += 0.5 * mi * p[j] * p[j];
@@ -362,21 +389,32 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
                 for (int j = 0; j < J; ++j)
                     x[j] = fma(MASS ? cd * s_mi[j * NT + tid] : cd, p[j], x[j]);
                 if (st == nk) break;
-                double xL, xR, e[J];
+                double xL, xR, e[J], eps[J];
                 exchange(x[0], x[J - 1], xL, xR, s_edge + par * 2 * nw, nw);
                 par ^= 1;
                 if (edge_thread) innovations<J, double, true>(x, xR, phi, la, e);
                 else innovations<J, double, false>(x, xR, phi, la, e);
                 // e_{-1}: left neighbour's innovation, or the stationary term at a window start
-                double eprev = v.first ? st0 * x[0] : fma(-phi, xL, x[0]);
+                double eprev = v.first ? stB * x[0] : fma(-phi, xL, x[0]);
+                if (LEV) {
+                    lev_terms(x, eps, e);
+                    if (!v.first) eprev = fma(-rs, yL * exp(-0.5 * xL), eprev);
+                }
                 // eq. (7): p -= kick dS/dh
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    const double ar = fma(-phi, e[j], eprev);
-                    eprev = e[j];
                     double f = fma(iu, x[j], s_kc[j * NT + tid]);
-                    f = fma(ie, ar, f);
-                    f = fma(-s_a[j * NT + tid], exp(-x[j]), f);
+                    if (LEV) {
+                        // d_{j-1} + d_j (rs eps_j / 2 - phi), and eps^2 / 2
+                        const double ar = fma(e[j], fma(0.5 * rs, eps[j], -phi), eprev);
+                        f = fma(ib, ar, f);
+                        f = fma(-0.5 * eps[j], eps[j], f);
+                    } else {
+                        const double ar = fma(-phi, e[j], eprev);
+                        f = fma(ie, ar, f);
+                        f = fma(-s_a[j * NT + tid], exp(-x[j]), f);
+                    }
+                    eprev = e[j];
                     p[j] = fma(-kick, f, p[j]);
                 }
             }
@@ -436,6 +474,9 @@ struct MixedConst {
     int n_sub;
     int la;        // slot of the series' last site in this thread (or out of [0, J))
     bool first;    // this thread holds the series' first site in slot 0
+    // leverage: v of the left neighbour site (0 at a window start), and the
+    // first-site correction cst (0 on other threads)
+    float vL, cfirst;
 };
 
 // Packed FP32 pair arithmetic (FFMA2/FADD2: two independent FP32 lanes per
@@ -471,17 +512,29 @@ __device__ __forceinline__ void cupd2(float2& hi, float2& lo, float2 c, float2 u
 // EDGE: some thread of the warp ends a series before its last slot; the ghost
 // replaces the right neighbour there by a select.
 // s_ak: float4 [P][NT] = (-a_p, -a_{p+P}, k_p, k_{p+P}); s_dm: float2 [P][NT].
-template <int J, bool MASS, bool EDGE>
+//
+// LEV (leverage): with B in c0 and c1, the force gains
+//   w_t (phi + (x_{t+1} - phi x_t)/2) - w_{t-1},  w_t = v_t e^{-h_t/2},
+//   v_t = B rho s_eta y_t (0 at the series' last site, which has no d_t),
+// the y-term weight a/(1-rho^2) at sites with a successor (the eps^2 part of
+// d_t^2), and cst x_0 at the series' first site, where the stationary row
+// (1-phi^2) x_0/s_eta^2 differs from the ghost's B (1-phi^2) x_0.
+// e^{-h} is taken as (e^{-h/2})^2 from one ex2.  s_v: float2 [P][NT] of v.
+template <int J, bool MASS, bool EDGE, bool LEV>
 __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J / 2],
                                             float2 (&PH)[J / 2], float2 (&PL)[J / 2],
                                             const float4* __restrict__ s_ak,
-                                            const float2* __restrict__ s_dm, float* s_edge,
+                                            const float2* __restrict__ s_dm,
+                                            const float2* __restrict__ s_v, float* s_edge,
                                             int& par, int nw, int n_md, const MixedConst& c)
 {
     constexpr int P = J / 2;
     const int NT = blockDim.x, tid = threadIdx.x;
     const float2 c0 = f2(c.c0, c.c0), c1 = f2(c.c1, c.c1);
     const float2 nl2e = f2(-kLog2e, -kLog2e), cmu = f2(c.cmu, c.cmu);
+    const float2 nl2h = f2(-0.5f * kLog2e, -0.5f * kLog2e), cmh = f2(0.5f * c.cmu, 0.5f * c.cmu);
+    const float2 half = f2(0.5f, 0.5f), phi2 = f2(c.phi, c.phi), nphi2 = f2(-c.phi, -c.phi);
+    const float2 zero = f2(0.0f, 0.0f);
     const float2 ndt = f2(-c.kick, -c.kick);
     for (int k = 0; k < c.n_sub; ++k) {
         float xL, xR;
@@ -491,6 +544,12 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
         if (!EDGE && c.la == J - 1) xR = c.phi * X[P - 1].y;
         const float xP = X[0].y;  // x_P before the step
         float2 prev = f2(xL, X[P - 1].x);  // left neighbours of pair 0, before the step
+        float2 prevw = zero;               // their w (leverage)
+        if (LEV) {
+            const float2 vP = s_v[(P - 1) * NT + tid];
+            prevw = f2(c.vL * ex2_approx(fmaf(-0.5f * kLog2e, xL, 0.5f * c.cmu)),
+                       vP.x * ex2_approx(fmaf(-0.5f * kLog2e, X[P - 1].x, 0.5f * c.cmu)));
+        }
         const float hs = (k + 1 < c.n_sub) ? ((k & 1) ? c.r_odd : c.r_even) : c.r_last;
         const float2 cx = f2(hs * c.dt, hs * c.dt);
 #pragma unroll
@@ -504,9 +563,20 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
             }
             float2 f = fma2(c0, xq, f2(ak.z, ak.w));
             f = fma2(c1, add2(prev, nxt), f);
-            // (y^2/2) e^{-h} = a 2^{-(x + mu) log2 e}: a small exponent argument
-            const float2 t = fma2(nl2e, xq, cmu);
-            f = fma2(f2(ak.x, ak.y), f2(ex2_approx(t.x), ex2_approx(t.y)), f);
+            if (LEV) {
+                const float2 t = fma2(nl2h, xq, cmh);
+                const float2 e2 = f2(ex2_approx(t.x), ex2_approx(t.y));  // e^{-h/2}
+                f = fma2(f2(ak.x, ak.y), fma2(e2, e2, zero), f);
+                const float2 w = fma2(s_v[q * NT + tid], e2, zero);
+                const float2 g = fma2(half, fma2(nphi2, xq, nxt), phi2);
+                f = sub2(fma2(w, g, f), prevw);
+                prevw = w;
+                if (q == 0) f.x = fmaf(c.cfirst, xq.x, f.x);
+            } else {
+                // (y^2/2) e^{-h} = a 2^{-(x + mu) log2 e}: a small exponent argument
+                const float2 t = fma2(nl2e, xq, cmu);
+                f = fma2(f2(ak.x, ak.y), f2(ex2_approx(t.x), ex2_approx(t.y)), f);
+            }
             prev = xq;
             cupd2(PH[q], PL[q], ndt, f);
             float2 cq = cx;
@@ -541,9 +611,12 @@ __device__ __forceinline__ ff hparts_total(const HParts& a, const MixedTheta& mt
 }
 // x: h - mu; p: momentum (hi, lo); mi: 1/m; cp: c' = lnRV - xi - mu; a: y^2/2;
 // xn: next site's x (used only if has_next).
+// LEV: Q is d_t^2 = (x_{t+1} - phi x_t - rs_y e^{-h_t/2})^2, rs_y = rho s_eta y_t
+// (weighted by B/2 in he).
+template <bool LEV>
 __device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, float mi, ff cp, float a,
                                             ff xn, bool has_next, const MixedTheta& mt,
-                                            const float2* tab)
+                                            const float2* tab, float rs_y = 0.0f)
 {
     ff p2 = two_prod(p.hi, p.hi);  // (hi + lo)^2 to ~2^-48
     p2.lo = fmaf(2.0f * p.hi, p.lo, p2.lo);
@@ -551,20 +624,32 @@ __device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, float mi, f
     ff_acc(acc.L, x);
     const ff r = ff_sub(x, cp);
     ff_acc(acc.R, ff_mul(r, r));
-    if (has_next) {
-        const ff e = ff_sub(xn, ff_mul(mt.phi_ff, x));
-        ff_acc(acc.Q, ff_mul(e, e));
+    const ff nh = ff_sub(ff{-mt.mu.hi, -mt.mu.lo}, x);  // -h
+    if (LEV) {
+        const ff E2 = ff_exp(ff{0.5f * nh.hi, 0.5f * nh.lo}, tab);  // e^{-h/2}
+        if (has_next) {
+            const ff e = ff_sub(ff_sub(xn, ff_mul(mt.phi_ff, x)), ff_mul_f(E2, rs_y));
+            ff_acc(acc.Q, ff_mul(e, e));
+        }
+        ff_acc(acc.E, ff_mul_f(ff_mul(E2, E2), a));
+    } else {
+        if (has_next) {
+            const ff e = ff_sub(xn, ff_mul(mt.phi_ff, x));
+            ff_acc(acc.Q, ff_mul(e, e));
+        }
+        const ff E = ff_exp(nh, tab);
+        ff_acc(acc.E, ff_mul_f(E, a));
     }
-    const ff E = ff_exp(ff_sub(ff{-mt.mu.hi, -mt.mu.lo}, x), tab);
-    ff_acc(acc.E, ff_mul_f(E, a));
 }
 
 // The stationary term (1 - phi^2) x_1^2 / (2 s_eta^2) of S, into Q (weighted
 // by 1/(2 s_eta^2)), in double-float: FP64 here would cost every warp that
-// predicates it.
+// predicates it.  With leverage Q is weighted by B/2 and the factor is
+// (1 - phi^2)(1 - rho^2).
+template <bool LEV>
 __device__ __forceinline__ void stationary_part(HParts& acc, ff x1, const MixedTheta& mt)
 {
-    const ff om = ff_sub(ff{1.0f, 0.0f}, ff_mul(mt.phi_ff, mt.phi_ff));
+    const ff om = LEV ? mt.st : ff_sub(ff{1.0f, 0.0f}, ff_mul(mt.phi_ff, mt.phi_ff));
     ff_acc(acc.Q, ff_mul(om, ff_mul(x1, x1)));
 }
 
@@ -572,7 +657,7 @@ __device__ __forceinline__ void stationary_part(HParts& acc, ff x1, const MixedT
 // runs in rolled loops over the thread's slots through shared memory: fully
 // unrolled over J slots it is thousands of instructions per thread, more than
 // the instruction caches hold.
-template <int J, bool MASS>
+template <int J, bool MASS, bool LEV>
 __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajArgs A)
 {
     static_assert(J % 4 == 0, "J must be a multiple of 4");
@@ -591,7 +676,9 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
     float* s_ak1 = reinterpret_cast<float*>(smem_raw);
     float2* s_dm = reinterpret_cast<float2*>(s_ak + P * NT);  // [P][NT] dtau/m of (p, p+P)
     float* s_dm1 = reinterpret_cast<float*>(s_dm);
-    float* s_xh = reinterpret_cast<float*>(s_dm + (MASS ? P * NT : 0));  // [J][NT]
+    float2* s_v = s_dm + (MASS ? P * NT : 0);  // [P][NT] leverage v of (p, p+P)
+    float* s_v1 = reinterpret_cast<float*>(s_v);
+    float* s_xh = reinterpret_cast<float*>(s_v + (LEV ? P * NT : 0));  // [J][NT]
     float* s_xl = s_xh + W;
     float* s_ph = s_xl + W;
     const bool mass_on = MASS && (A.mass_on == nullptr || *A.mass_on != 0);
@@ -601,6 +688,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
     auto na_at = [&](int j) -> float& { return s_ak1[((j % P) * NT + tid) * 4 + j / P]; };
     auto k_at = [&](int j) -> float& { return s_ak1[((j % P) * NT + tid) * 4 + 2 + j / P]; };
     auto dm_at = [&](int j) -> float& { return s_dm1[((j % P) * NT + tid) * 2 + j / P]; };
+    auto v_at = [&](int j) -> float& { return s_v1[((j % P) * NT + tid) * 2 + j / P]; };
 
     for (int b = blockIdx.x; b < A.nbins; b += gridDim.x) {
         float2 X[P], XL[P], PH[P], PL[P];
@@ -610,9 +698,8 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             View v;
             load_bin(A, b, s_wseg, s_wacc, v);
             const int base = v.base * J;
-            if (lane < 16)
-                reinterpret_cast<float*>(&s_mt[warp])[lane] =
-                    reinterpret_cast<const float*>(A.theta_f + v.g.series)[lane];
+            reinterpret_cast<float*>(&s_mt[warp])[lane] =
+                reinterpret_cast<const float*>(A.theta_f + v.g.series)[lane];
             __syncwarp();
             const MixedTheta& mt = s_mt[warp];
             mc.phi = mt.phi;
@@ -671,11 +758,18 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     ff x = two_sum(hv.x, -mt.mu.hi);  // x = h - mu in double-float
                     x.lo += hv.y - mt.mu.lo;
                     x = fast_two_sum(x.hi, x.lo);
-                    const float a = act ? A.a_f[s] : 0.0f;  // y^2/2
+                    const float as = act ? A.a_f[s] : 0.0f;  // y^2/2 with the sign of y
+                    const float a = fabsf(as);
                     const float2 lr = act ? A.lr_f[s] : make_float2(mt.ximu.hi, mt.ximu.lo);
                     ff cp = two_sum(lr.x, -mt.ximu.hi);  // c' = lnRV - xi - mu
                     cp.lo += lr.y - mt.ximu.lo;
-                    na_at(j) = -a;
+                    if (LEV) {
+                        const bool has_next = act && wlo + ii + 1 < v.si.T;
+                        na_at(j) = has_next ? -a * mt.ia : -a;
+                        v_at(j) = has_next ? mt.rsb * copysignf(sqrtf(2.0f * a), as) : 0.0f;
+                    } else {
+                        na_at(j) = -a;
+                    }
                     k_at(j) = fmaf(-mt.iu, cp.hi + cp.lo, 0.5f);
                     if (MASS) {
                         const float mi = (act && mass_on) ? A.minv[s] : 1.0f;
@@ -688,6 +782,8 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                 }
             }
             __syncthreads();
+            mc.vL = (LEV && !v.first) ? s_v1[((P - 1) * NT + tid - 1) * 2 + 1] : 0.0f;
+            mc.cfirst = (LEV && v.first) ? mt.cst : 0.0f;
             // pass 2: H at the start over the owned sites (needs the next x)
             HParts acc;
             hparts_zero(acc);
@@ -702,12 +798,14 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                 ff cp = two_sum(lr.x, -mt.ximu.hi);
                 cp.lo += lr.y - mt.ximu.lo;
                 const float mi = MASS ? dm_at(j) * inv_dt : 1.0f;
-                hparts_site(acc, x, ff{s_ph[j * NT + tid], 0.f}, mi, cp, -na_at(j), xn,
-                            sg + 1 < v.si.T, mt, s_exptab);
+                const bool has_next = sg + 1 < v.si.T;
+                const float a = (LEV && has_next) ? -na_at(j) * mt.omr : -na_at(j);
+                hparts_site<LEV>(acc, x, ff{s_ph[j * NT + tid], 0.f}, mi, cp, a, xn, has_next, mt,
+                                 s_exptab, LEV ? v_at(j) * mt.ibf : 0.0f);
             }
             // the stationary term of h_1, outside the loop (its thread only)
             if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
-                stationary_part(acc, ff{s_xh[tid], s_xl[tid]}, mt);
+                stationary_part<LEV>(acc, ff{s_xh[tid], s_xl[tid]}, mt);
             h0 = hparts_total(acc, mt);
             // registers <- shared memory, then the first half step of eq. (6)
 #pragma unroll
@@ -729,9 +827,11 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
         int par = 0;
         const bool mid_end = mc.la >= 0 && mc.la < J - 1;
         if (__any_sync(0xffffffffu, mid_end))
-            mixed_steps<J, MASS, true>(X, XL, PH, PL, s_ak, s_dm, s_edge, par, nw, A.n_md, mc);
+            mixed_steps<J, MASS, true, LEV>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par, nw,
+                                            A.n_md, mc);
         else
-            mixed_steps<J, MASS, false>(X, XL, PH, PL, s_ak, s_dm, s_edge, par, nw, A.n_md, mc);
+            mixed_steps<J, MASS, false, LEV>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par, nw,
+                                             A.n_md, mc);
 
         // ---- the end of the trajectory: state -> shared memory (x over the
         // start's slots, p lo over k, which the leapfrog no longer needs) ----
@@ -766,11 +866,13 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             ff cp = two_sum(lr.x, -mt.ximu.hi);
             cp.lo += lr.y - mt.ximu.lo;
             const float mi = MASS ? dm_at(j) * inv_dt : 1.0f;
-            hparts_site(acc, x, ff{s_ph[j * NT + tid], k_at(j)}, mi, cp, -na_at(j), xn,
-                        sg + 1 < v.si.T, mt, s_exptab);
+            const bool has_next = sg + 1 < v.si.T;
+            const float a = (LEV && has_next) ? -na_at(j) * mt.omr : -na_at(j);
+            hparts_site<LEV>(acc, x, ff{s_ph[j * NT + tid], k_at(j)}, mi, cp, a, xn, has_next, mt,
+                             s_exptab, LEV ? v_at(j) * mt.ibf : 0.0f);
         }
         if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
-            stationary_part(acc, ff{s_xh[tid], s_xl[tid]}, mt);
+            stationary_part<LEV>(acc, ff{s_xh[tid], s_xl[tid]}, mt);
         ff dh = ff_sub(hparts_total(acc, mt), h0);
         dh = warp_sum_ff(dh);
         if (lane == 0) s_wpf[warp] = make_float2(dh.hi, dh.lo);
@@ -824,7 +926,7 @@ __global__ void k_prep_mixed(const double* __restrict__ y, const double* __restr
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
         const double a = 0.5 * y[t] * y[t];
-        a_f[t] = (float)a;
+        a_f[t] = copysignf((float)a, (float)y[t]);  // the sign of y for the leverage term
         const ff l = ff_from_double(lnrv[t]);
         lr_f[t] = make_float2(l.hi, l.lo);
     }
@@ -896,20 +998,20 @@ int grid_for(int64_t T)
     return (int)g;
 }
 
-template <int J, bool MASS>
+template <int J, bool MASS, bool LEV>
 cudaError_t launch_fp64(const TrajArgs& a, const Plan& p, cudaStream_t st)
 {
-    auto k = k_traj_fp64<J, MASS>;
+    auto k = k_traj_fp64<J, MASS, LEV>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)p.smem);
     if (e != cudaSuccess) return e;
     k<<<p.grid, p.nt, p.smem, st>>>(a);
     return cudaGetLastError();
 }
-template <int J, bool MASS>
+template <int J, bool MASS, bool LEV>
 cudaError_t launch_mixed(const TrajArgs& a, const Plan& p, cudaStream_t st)
 {
-    auto k = k_traj_mixed<J, MASS>;
+    auto k = k_traj_mixed<J, MASS, LEV>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)p.smem);
     if (e != cudaSuccess) return e;
@@ -918,23 +1020,27 @@ cudaError_t launch_mixed(const TrajArgs& a, const Plan& p, cudaStream_t st)
 }
 
 __global__ void k_theta_prep(const double* __restrict__ theta, ThetaD th_inline, int n,
-                             MixedTheta* __restrict__ out)
+                             double rho, MixedTheta* __restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         const ff v = ff_from_double(exp2((double)threadIdx.x / 32.0));
         g_exptab[threadIdx.x] = make_float2(v.hi, v.lo);
     }
-    if (i < n) out[i] = mixed_theta(theta ? load_theta(theta + 5 * (int64_t)i) : th_inline);
+    if (i < n) {
+        ThetaD th = theta ? load_theta(theta + 5 * (int64_t)i) : th_inline;
+        th.rho = rho;
+        out[i] = mixed_theta(th);
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, MixedTheta* theta_f,
-                              cudaStream_t st)
+cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, double rho,
+                              MixedTheta* theta_f, cudaStream_t st)
 {
     const int g = (n + 127) / 128;
-    k_theta_prep<<<g < 1 ? 1 : g, 128, 0, st>>>(theta, th_inline, n, theta_f);
+    k_theta_prep<<<g < 1 ? 1 : g, 128, 0, st>>>(theta, th_inline, n, rho, theta_f);
     return cudaGetLastError();
 }
 
@@ -950,7 +1056,7 @@ int mixed_max_threads(int j)
     }
 }
 
-int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem)
+int blocks_per_sm(bool mixed, bool mass, bool lev, int j, int nt, size_t smem)
 {
     int n = 0;
     cudaError_t e = cudaSuccess;
@@ -963,13 +1069,17 @@ int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem)
     } while (0)
 #define RSV_JM(JJ)                                                         \
     case JJ:                                                               \
-        if (mass) RSV_OCC((k_traj_mixed<JJ, true>));                       \
-        else RSV_OCC((k_traj_mixed<JJ, false>));                           \
+        if (mass && lev) RSV_OCC((k_traj_mixed<JJ, true, true>));          \
+        else if (mass) RSV_OCC((k_traj_mixed<JJ, true, false>));           \
+        else if (lev) RSV_OCC((k_traj_mixed<JJ, false, true>));            \
+        else RSV_OCC((k_traj_mixed<JJ, false, false>));                    \
         break;
 #define RSV_JD(JJ)                                                         \
     case JJ:                                                               \
-        if (mass) RSV_OCC((k_traj_fp64<JJ, true>));                        \
-        else RSV_OCC((k_traj_fp64<JJ, false>));                            \
+        if (mass && lev) RSV_OCC((k_traj_fp64<JJ, true, true>));           \
+        else if (mass) RSV_OCC((k_traj_fp64<JJ, true, false>));            \
+        else if (lev) RSV_OCC((k_traj_fp64<JJ, false, true>));             \
+        else RSV_OCC((k_traj_fp64<JJ, false, false>));                     \
         break;
     if (mixed) {
         switch (j) { RSV_JM(4) RSV_JM(8) RSV_JM(12) RSV_JM(16) RSV_JM(20) default: return 0; }
@@ -988,8 +1098,10 @@ int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem)
 
 cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st)
 {
-#define RSV_CASE(FN, JJ) \
-    case JJ: return p.mass ? FN<JJ, true>(a, p, st) : FN<JJ, false>(a, p, st);
+#define RSV_CASE(FN, JJ)                                                        \
+    case JJ:                                                                    \
+        if (p.lev) return p.mass ? FN<JJ, true, true>(a, p, st) : FN<JJ, false, true>(a, p, st); \
+        return p.mass ? FN<JJ, true, false>(a, p, st) : FN<JJ, false, false>(a, p, st);
     if (p.mixed) {
         switch (p.j) {
             RSV_CASE(launch_mixed, 4)

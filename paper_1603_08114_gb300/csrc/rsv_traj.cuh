@@ -50,27 +50,41 @@ struct Plan {
     int integrator = 0;         // 0 leapfrog, 1 minimum-norm (two forces per step)
     double lambda = 0.0;        // of the minimum-norm integrator
     bool mixed = false, mass = false;
+    bool lev = false;           // RSV model with leverage (rho != 0)
 };
 
 // theta-derived constants of one series in FP32 / double-float for the mixed
-// path, 16 floats per series.  The FP64 pipe of this GPU runs at 1/64 of the
+// path, 32 floats per series.  The FP64 pipe of this GPU runs at 1/64 of the
 // FP32 rate and every FP64 instruction occupies it for the whole warp, even
 // with one lane active, so these are derived once per series (mixed_theta, by
 // a small kernel or the theta update) instead of inside the trajectory kernel.
+//
+// With leverage (rho != 0) B = 1/(s_eta^2 (1 - rho^2)) takes the place of
+// 1/s_eta^2 in c0, c1 and he, and the force and dH need the extra constants
+// below; with rho = 0 they reduce to the plain model's values.
 struct MixedTheta {
-    // leapfrog: phi, c0 = 1/s_u^2 + (1+phi^2)/s_eta^2, 1/s_u^2, 1/s_eta^2,
-    // -mu log2 e; c1 = -phi/s_eta^2 (the force's stencil weights)
+    // leapfrog: phi, c0 = 1/s_u^2 + (1+phi^2) B, 1/s_u^2, 1/s_eta^2,
+    // -mu log2 e; c1 = -phi B (the force's stencil weights)
     float phi, c0, iu, ie, cmu;
-    ff mu, ximu, phi_ff, hu, he;  // dH: mu, xi + mu, phi, 1/(2 s_u^2), 1/(2 s_eta^2)
+    ff mu, ximu, phi_ff, hu, he;  // dH: mu, xi + mu, phi, 1/(2 s_u^2), B/2
     float c1;
+    // leverage: cst = -(1-phi^2) rho^2 B (first-site correction of the ghost
+    // row), ia = 1/(1-rho^2) (y-term weight of sites with a successor), omr =
+    // 1 - rho^2, rsb = B rho s_eta (per-site v = rsb y), ibf = 1/B,
+    // st = (1-phi^2)(1-rho^2) (stationary term in units of B/2)
+    float cst, ia, omr, rsb, ibf;
+    ff st;
+    float pad[9];
 };
-static_assert(sizeof(MixedTheta) == 64, "MixedTheta is 16 floats");
+static_assert(sizeof(MixedTheta) == 128, "MixedTheta is 32 floats");
 __device__ __forceinline__ MixedTheta mixed_theta(const ThetaD& th)
 {
     MixedTheta m;
+    const double omr = 1.0 - th.rho * th.rho;
+    const double B = 1.0 / (th.se2 * omr);
     m.phi = (float)th.phi;
-    m.c0 = (float)(1.0 / th.su2 + (1.0 + th.phi * th.phi) / th.se2);
-    m.c1 = (float)(-th.phi / th.se2);
+    m.c0 = (float)(1.0 / th.su2 + (1.0 + th.phi * th.phi) / (th.se2 * omr));
+    m.c1 = (float)(-th.phi / (th.se2 * omr));
     m.iu = (float)(1.0 / th.su2);
     m.ie = (float)(1.0 / th.se2);
     m.cmu = (float)(-th.mu * 1.4426950408889634);  // exponent of e^{-mu}
@@ -78,7 +92,14 @@ __device__ __forceinline__ MixedTheta mixed_theta(const ThetaD& th)
     m.ximu = ff_from_double(th.xi + th.mu);
     m.phi_ff = ff_from_double(th.phi);
     m.hu = ff_from_double(0.5 / th.su2);
-    m.he = ff_from_double(0.5 / th.se2);
+    m.he = ff_from_double(0.5 / (th.se2 * omr));
+    m.cst = (float)(-(1.0 - th.phi * th.phi) * th.rho * th.rho * B);
+    m.ia = (float)(1.0 / omr);
+    m.omr = (float)omr;
+    m.rsb = (float)(B * th.rho * sqrt(th.se2));
+    m.ibf = (float)(th.se2 * omr);
+    m.st = ff_from_double((1.0 - th.phi * th.phi) * omr);
+    for (int i = 0; i < 9; ++i) m.pad[i] = 0.f;
     return m;
 }
 
@@ -106,9 +127,10 @@ struct TrajArgs {
     double* p_out;       // optional p' (FP64, packed), must not alias p_in
     const double* y;     // FP64 path
     const double* lnrv;
-    const float* a_f;    // mixed path: y^2/2 and lnRV as (hi, lo)
+    const float* a_f;    // mixed path: y^2/2 with the sign of y, and lnRV as (hi, lo)
     const float2* lr_f;
     const MixedTheta* theta_f;  // mixed path: per-series constants (launch_theta_prep)
+    double rho;          // leverage corr(eps_t, eta_t) of every series (0: eqs. (1)-(3))
     const float* minv;   // optional inverse mass (FP32, packed)
     const int* mass_on;  // optional flag; 0 = use m = 1
     int n_md;
@@ -126,20 +148,21 @@ struct TrajArgs {
 // Returns false (reason in *why) if no tiling fits.
 // integrator / lambda: see Plan; the halo is n_md * (forces per step) + 1.
 bool make_plan(const int64_t* offsets, int n, int n_md, int integrator, double lambda, bool mixed,
-               bool mass, int num_sms, int sched_nt, int sched_j, int64_t sched_tile, Plan& plan,
-               const char** why);
+               bool mass, bool lev, int num_sms, int sched_nt, int sched_j, int64_t sched_tile,
+               Plan& plan, const char** why);
 void free_plan(Plan& plan);
 
 cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st);
-// theta_f[s] = mixed_theta(theta of series s) for n series (theta: device
-// [n][5], or NULL for th_inline); also fills the device table of 2^(j/32).
-cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, MixedTheta* theta_f,
-                              cudaStream_t st);
+// theta_f[s] = mixed_theta(theta of series s, leverage rho) for n series
+// (theta: device [n][5], or NULL for th_inline); also fills the device table
+// of 2^(j/32).
+cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, double rho,
+                              MixedTheta* theta_f, cudaStream_t st);
 // Largest block (threads) of the mixed kernel with `j` sites per thread (0 if
 // j is not instantiated).
 int mixed_max_threads(int j);
 // Resident blocks per SM of a trajectory kernel configuration (0 if invalid).
-int blocks_per_sm(bool mixed, bool mass, int j, int nt, size_t smem);
+int blocks_per_sm(bool mixed, bool mass, bool lev, int j, int nt, size_t smem);
 
 cudaError_t launch_commit_fp64(double* h, const double* hprop, double* p, const double* pprop,
                                const int* acc, int64_t T, cudaStream_t st);

@@ -62,6 +62,7 @@ def lib():
         L.rsv_sync_status.argtypes = [_P, _P]
         L.rsv_set_schedule.argtypes = [_P, _INT, _INT, _I64]
         L.rsv_set_integrator.argtypes = [_P, _INT, ctypes.c_double]
+        L.rsv_set_leverage.argtypes = [_P, ctypes.c_double]
         L.rsv_action.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
         L.rsv_force.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
         L.rsv_hmc_trajectory.argtypes = [_P, _P, _P, _P, _P, _I64, Theta, _P, _INT,
@@ -81,7 +82,7 @@ def lib():
         L.rsv_stats.argtypes = [_P, _INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                 ctypes.POINTER(ctypes.c_double)]
         for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule",
-                     "rsv_set_integrator", "rsv_action", "rsv_force",
+                     "rsv_set_integrator", "rsv_set_leverage", "rsv_action", "rsv_force",
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
                      "rsv_timing", "rsv_stats", "rsv_gibbs_theta", "rsv_plan_create",
                      "rsv_plan_info", "rsv_hmc_batched"):
@@ -153,6 +154,12 @@ def rsv_set_integrator(ctx: Context, kind="leapfrog", lam: float = 0.0):
     (lam <= 0: the minimum-norm value)."""
     k = {"leapfrog": RSV_LEAPFROG, "omelyan2": RSV_OMELYAN2}.get(kind, kind)
     _check(lib().rsv_set_integrator(ctx.handle, int(k), float(lam)))
+
+
+def rsv_set_leverage(ctx: Context, rho: float = 0.0):
+    """Leverage corr(eps_t, eta_t) = rho of the RSV model for later calls and
+    plans of this context (0: eqs. (1)-(3))."""
+    _check(lib().rsv_set_leverage(ctx.handle, float(rho)))
 
 
 def rsv_set_schedule(ctx: Context, threads: int = 0, sites_per_thread: int = 0, tile: int = 0):
