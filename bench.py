@@ -319,6 +319,88 @@ def run_ours(args):
             launches=launches, traj_launches=traj_launches, traj_ms=traj_ms,
             nonfinite_dH_seen=bool(nonfinite))
 
+    def step_kernel_us(yv, lv, h0, n_hi, n=10):
+        """Per-step time of the mixed trajectory kernel (identity mass, theta
+        fixed): its time at n_hi steps minus at one step, on the tiling the
+        library picks for n_hi, per extra step; and its time at one step."""
+        pl = rsv.Plan(ctx, np.array([0, T_SITES], dtype=np.int64), n_hi, "mixed")
+        pi = pl.info()
+        pl.close()
+        nt_, j_ = pi["threads"], pi["sites_per_thread"]
+        rsv.rsv_set_schedule(ctx, nt_, j_, nt_ * j_ - 2 * (n_hi + 1) - 3)
+        out = []
+        try:
+            for n_md in (n_hi, 1):
+                hh = torch.tensor(h0, device=dev)
+                th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
+                rsv.rsv_hmc_chain(ctx, hh, yv, lv, th, n_md, DTAU, 2, prec="mixed", seed=77)
+                torch.cuda.synchronize()
+                rsv.rsv_stats(ctx, reset=True)
+                rsv.rsv_timing(ctx, True)
+                rsv.rsv_hmc_chain(ctx, hh, yv, lv, th, n_md, DTAU, n, prec="mixed", seed=78,
+                                  traj0=2)
+                torch.cuda.synchronize()
+                rsv.rsv_timing(ctx, False)
+                _, nl, ms = rsv.rsv_stats(ctx, reset=True)
+                out.append(1e3 * ms / max(nl, 1))
+        finally:
+            rsv.rsv_set_schedule(ctx)
+        return (out[0] - out[1]) / (n_hi - 1), out[1], {"threads": nt_, "sites_per_thread": j_}
+
+    def leverage_leg(steps):
+        """The RSV model with leverage, rho = corr(eps_t, eta_t) = RHO_STD, on a
+        2^20-site series drawn from it: mixed, identity mass, 100 x 0.005, theta
+        fixed at its true value (the theta update is for rho = 0).  Chain rate,
+        ESS of h, and the step time of the leverage kernel against the plain
+        one (same series, rho = 0) on one tiling."""
+        sl = synth.rsv_series_leverage(T_SITES, synth.THETA_STD, synth.RHO_STD,
+                                       seed=SEED_DATA + 7 + 1000 * rank)
+        yl, ll = torch.tensor(sl.y, device=dev), torch.tensor(sl.lnrv, device=dev)
+        rsv.rsv_set_leverage(ctx, synth.RHO_STD)
+        try:
+            h = torch.tensor(sl.h_true, device=dev)
+            th = torch.tensor(sl.theta, dtype=torch.float64, device=dev)
+            traj = 0
+            for _ in range(2):
+                rsv.rsv_hmc_chain(ctx, h, yl, ll, th, N_MD, DTAU, N_TRAJ, prec="mixed",
+                                  seed=21 + rank, traj0=traj)
+                traj += N_TRAJ
+            rsv.rsv_sync_status(ctx)
+            ms, ess_med, ess_min, rates = [], [], [], []
+            for _ in range(steps):
+                flush.zero_()
+                a_ev = torch.cuda.Event(enable_timing=True)
+                b_ev = torch.cuda.Event(enable_timing=True)
+                a_ev.record()
+                rsv.rsv_hmc_chain(ctx, h, yl, ll, th, N_MD, DTAU, N_TRAJ, prec="mixed",
+                                  seed=21 + rank, traj0=traj, snaps=snaps, thin=1,
+                                  accept_out=acc)
+                b_ev.record()
+                traj += N_TRAJ
+                e = rsv.rsv_ess(ctx, snaps)
+                ess_med.append(float(e.median()))
+                ess_min.append(float(e.min()))
+                rates.append(float(acc.float().mean()))
+                ms.append(a_ev.elapsed_time(b_ev))
+            rsv.rsv_sync_status(ctx)
+            sec = _barrier_max(ws, sum(ms) / 1e3) / steps
+            us_lev, us_lev1, sched = step_kernel_us(yl, ll, sl.h_true, N_MD)
+        finally:
+            rsv.rsv_set_leverage(ctx, 0.0)
+        us_plain, us_plain1, _ = step_kernel_us(yl, ll, sl.h_true, N_MD)
+        return {"rho": synth.RHO_STD, "T": T_SITES, "n_md": N_MD, "dtau": DTAU,
+                "theta": "fixed (true value)", "precision": "mixed", "mass": "identity",
+                "site_updates_per_s": ws * T_SITES * N_MD * N_TRAJ / sec,
+                "ms_per_step": 1e3 * sec, "traj_per_step": N_TRAJ,
+                "ess_h_median_per_s": ws * statistics.mean(ess_med) / sec,
+                "ess_h_min_per_s": ws * statistics.mean(ess_min) / sec,
+                "accept_rate": statistics.mean(rates),
+                "kernel_us_per_step": us_lev, "kernel_us_one_step": us_lev1,
+                "plain_kernel_us_per_step": us_plain, "plain_kernel_us_one_step": us_plain1,
+                "schedule": sched,
+                "how": "chain: CUDA events around each step of N trajectories (L2 flushed); "
+                       "kernel: k_traj_mixed time at n_md minus at n_md = 1, per step"}
+
     def batched_leg(steps):
         """The 4096-series workload: one persistent launch per trajectory of all
         series, autotuned block shape, replayed from a CUDA graph."""
@@ -413,12 +495,13 @@ def run_ours(args):
         learned_info["fell_back"] = bool(sampler.fell_back)
         learned_info["window_accept"] = [round(r, 3) for r in sampler.history]
     # comparisons: plain mixed and plain FP64 samplers (identity mass, 100 x 0.005)
-    ident = fp64 = batched = mn = None
+    ident = fp64 = batched = mn = levr = None
     if args.only != "mixed":
         if minv is not None:
             ident = arm("mixed", None, min(args.warmup, 3), min(args.steps, 3))
         fp64 = arm("fp64", None, min(args.warmup, 3), min(args.steps, 3))
         batched = batched_leg(max(3, min(args.steps, 10)))
+        levr = leverage_leg(min(args.steps, 3))
         # the minimum-norm integrator (two forces per step) at the plain
         # sampler's trajectory length (0.5; 2.5 in the learned mass's units):
         # the fewest steps whose acceptance over 40 trial trajectories
@@ -561,6 +644,7 @@ def run_ours(args):
                 "ess_h_min_per_s": ident["ess_h_min_per_s"],
                 "ess_theta_per_s": ident["ess_theta_per_s"],
                 "accept_rate": ident["accept_rate"]},
+            "leverage": levr,
             "mixed_omelyan2": None if mn is None else {
                 tag: {"integrator": "minimum-norm (Omelyan), 2 force evaluations per step",
                       "mass": tag, "n_md": r["n_md"], "dtau": r["dtau"],
