@@ -241,6 +241,43 @@ def test_full_size_T2p22_mixed_precision_report(rsv, ctx):
     assert (lu < -dH.item()) == (lu < -dHr) or abs(dHr + lu) <= 1e-2
 
 
+@pytest.mark.parametrize("case", ["T2p22", "T2p20_mass", "T2p20_leverage"])
+def test_mixed_dH_evaluation_error(rsv, ctx, case):
+    """The mixed dH against the oracle's dH of the kernel's own end state (h',
+    p' read back) from its own start (p rounded to FP32 as the kernel takes
+    it): the evaluation error alone, without the FP32 trajectory's deviation."""
+    T, th, n_md, dtau, rho, minv = 1 << 22, synth.THETA_LARGE, 100, 0.003, 0.0, None
+    if case != "T2p22":
+        T, th, n_md, dtau = 1 << 20, TH, 100, 0.005
+    if case == "T2p20_mass":
+        minv = np.random.default_rng(4).uniform(0.5, 2.0, T).astype(np.float32)
+        dtau = 0.004
+    if case == "T2p20_leverage":
+        rho = synth.RHO_STD
+        s = synth.rsv_series_leverage(T, th, rho, seed=7)
+    else:
+        s = synth.rsv_series(T, th, seed=3)
+    p0 = synth.standard_normals(T, 5)
+    if minv is not None:
+        p0 = p0 / np.sqrt(minv.astype(np.float64))
+    p0 = p0.astype(np.float32).astype(np.float64)
+    h, p = dev(s.h_true), dev(p0)
+    rsv.rsv_set_leverage(ctx, rho)
+    try:
+        dH, _ = rsv.rsv_hmc_trajectory(ctx, h, p, dev(s.y), dev(s.lnrv), th, n_md, dtau,
+                                       prec="mixed", log_u=dev([-1e300]),
+                                       minv=None if minv is None else dev(minv, torch.float32))
+        rsv.rsv_sync_status(ctx)
+    finally:
+        rsv.rsv_set_leverage(ctx, 0.0)
+    mv = None if minv is None else minv.astype(np.float64)
+    dHe = oracle.delta_H(s.h_true, p0, h.cpu().numpy(), p.cpu().numpy(), s.y, s.lnrv,
+                         th + (rho,), minv=mv)
+    err = abs(dH.item() - dHe)
+    print(f"mixed dH evaluation error {case}: {err:.3e} (dH = {dHe:.4f})")
+    assert err < 1e-4, err
+
+
 # ---------------------------------------------------------------------------
 def test_invalid_arguments_rejected(rsv, ctx):
     T = 10
