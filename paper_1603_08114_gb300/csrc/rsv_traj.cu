@@ -746,10 +746,15 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
     const float dt = (float)A.dtau;
     const float inv_dt = 1.0f / dt;  // 1/m_t = (dtau/m_t) / dtau, the same at both ends of dH
     // slot j is lane j / P of pair j % P
-    auto na_at = [&](int j) -> float& { return s_ak1[((j % P) * NT + tid) * 4 + j / P]; };
-    auto k_at = [&](int j) -> float& { return s_ak1[((j % P) * NT + tid) * 4 + 2 + j / P]; };
-    auto dm_at = [&](int j) -> float& { return s_dm1[((j % P) * NT + tid) * 2 + j / P]; };
-    auto v_at = [&](int j) -> float& { return s_v1[((j % P) * NT + tid) * 2 + j / P]; };
+    // slot j of thread t
+    auto na_t = [&](int j, int t) -> float& { return s_ak1[((j % P) * NT + t) * 4 + j / P]; };
+    auto k_t = [&](int j, int t) -> float& { return s_ak1[((j % P) * NT + t) * 4 + 2 + j / P]; };
+    auto dm_t = [&](int j, int t) -> float& { return s_dm1[((j % P) * NT + t) * 2 + j / P]; };
+    auto v_t = [&](int j, int t) -> float& { return s_v1[((j % P) * NT + t) * 2 + j / P]; };
+    auto na_at = [&](int j) -> float& { return na_t(j, tid); };
+    auto k_at = [&](int j) -> float& { return k_t(j, tid); };
+    auto dm_at = [&](int j) -> float& { return dm_t(j, tid); };
+    auto v_at = [&](int j) -> float& { return v_t(j, tid); };
 
     for (int b = blockIdx.x; b < A.nbins; b += gridDim.x) {
         float2 X[P], XL[P], PH[P], PL[P];
@@ -806,13 +811,18 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     for (int i = 0; i < 4; ++i) s_ph[(4 * q + i) * NT + tid] = z[i];
                 }
             }
-            // pass 1b: site constants, x, mass -> shared memory
-#pragma unroll 2
-            for (int q = 0; q < J / 4; ++q) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int j = 4 * q + i;
-                    const int ii = base + j;
+            // pass 1b: site constants, x, mass -> shared memory.  The warp
+            // loads its 32 J consecutive sites with consecutive lanes
+            // (coalesced) and files each into its owner's slots; the warp's
+            // threads share one segment.
+            __syncwarp();  // the owners' momenta of pass 1a are in s_ph
+            {
+                const int wb = (warp - v.g.warp0) * 32 * J;
+#pragma unroll 4
+                for (int kk = lane; kk < 32 * J; kk += 32) {
+                    const int ol = kk / J, j = kk - ol * J;
+                    const int to = (warp << 5) + ol;  // the owner thread
+                    const int ii = wb + kk;
                     const int64_t s = off + wlo + ii;
                     const bool act = ii < v.n;
                     const float2 hv = act ? hin[s] : make_float2(mt.mu.hi, mt.mu.lo);
@@ -826,20 +836,20 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     cp.lo += lr.y - mt.ximu.lo;
                     if (LEV) {
                         const bool has_next = act && wlo + ii + 1 < v.si.T;
-                        na_at(j) = has_next ? -a * mt.ia : -a;
-                        v_at(j) = has_next ? mt.rsb * copysignf(sqrtf(2.0f * a), as) : 0.0f;
+                        na_t(j, to) = has_next ? -a * mt.ia : -a;
+                        v_t(j, to) = has_next ? mt.rsb * copysignf(sqrtf(2.0f * a), as) : 0.0f;
                     } else {
-                        na_at(j) = -a;
+                        na_t(j, to) = -a;
                     }
-                    k_at(j) = fmaf(-mt.iu, cp.hi + cp.lo, 0.5f);
+                    k_t(j, to) = fmaf(-mt.iu, cp.hi + cp.lo, 0.5f);
                     if (MASS) {
                         const float mi = (act && mass_on) ? A.minv[s] : 1.0f;
-                        dm_at(j) = dt * mi;
+                        dm_t(j, to) = dt * mi;
                         // p ~ N(0, m_t): the drawn normal over sqrt(1/m_t)
-                        if (!A.p_in) s_ph[j * NT + tid] = s_ph[j * NT + tid] / sqrtf(mi);
+                        if (!A.p_in) s_ph[j * NT + to] = s_ph[j * NT + to] / sqrtf(mi);
                     }
-                    s_xh[j * NT + tid] = x.hi;
-                    s_xl[j * NT + tid] = x.lo;
+                    s_xh[j * NT + to] = x.hi;
+                    s_xl[j * NT + to] = x.lo;
                 }
             }
             __syncthreads();
@@ -942,13 +952,19 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
         __syncthreads();
         const bool write_h = v.sid >= 0 && (v.g.split || s_wacc[v.g.warp0]);
         float2* hout = v.g.split ? (v.cur ? A.h0f : A.h1f) : (v.cur ? A.h1f : A.h0f);
+        if (write_h) {
+            // the warp writes its 32 J consecutive sites with consecutive lanes
+            // (coalesced), reading each site from its owner's slot; write_h is
+            // the same for the whole warp (a segment is whole warps)
+            const int64_t wbase = wlo + (int64_t)(warp - v.g.warp0) * 32 * J;
 #pragma unroll 1
-        for (int j = 0; j < J; ++j) {
-            const int64_t sg = wlo + base + j;
-            if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
-                if (write_h) {
-                    ff hh = two_sum(s_xh[j * NT + tid], mt.mu.hi);
-                    hh.lo += s_xl[j * NT + tid] + mt.mu.lo;
+            for (int k = lane; k < 32 * J; k += 32) {
+                const int ol = k / J, j = k - ol * J;
+                const int64_t sg = wbase + k;
+                if (sg >= v.g.lo && sg < v.g.hi) {
+                    const int idx = j * NT + warp * 32 + ol;
+                    ff hh = two_sum(s_xh[idx], mt.mu.hi);
+                    hh.lo += s_xl[idx] + mt.mu.lo;
                     hh = fast_two_sum(hh.hi, hh.lo);
                     hout[off + sg] = make_float2(hh.hi, hh.lo);
                 }
