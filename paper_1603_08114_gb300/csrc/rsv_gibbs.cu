@@ -379,31 +379,28 @@ __device__ __forceinline__ void site_stats_d(const double* h, const double* lnrv
     if (t >= 1 && t + 1 < T) s[4] += x * x;
 }
 
-// Per-site contributions, (hi, lo) FP32 state: double-float arithmetic.
-__device__ __forceinline__ void site_stats_f(const float2* __restrict__ h,
-                                            const float2* __restrict__ lr, int64_t t, int64_t T,
-                                            ff xi, ff mu, ff phi, ff (&s)[NSTAT],
-                                            float* __restrict__ snap)
+// Per-site contributions, (hi, lo) FP32 state, in FP32: the sweep reads the
+// totals in FP32, so per-site FP32 terms (relative error ~1e-7, unbiased)
+// summed per thread in FP32 and across threads in double-float are enough.
+// The centring values xi, mu, phi are the FP32 theta the sweep starts from.
+// hv = h_t, lv = lnRV_t, hn = h_{t+1} (read only if t + 1 < T), as (hi, lo).
+__device__ __forceinline__ void site_stats_f(float2 hv, float2 lv, float2 hn, int64_t t, int64_t T,
+                                            float xi, float mu, float phi, float (&s)[NSTAT])
 {
-    const float2 hv = h[t];
-    if (snap) snap[t] = hv.x + hv.y;  // the chain's snapshot of h, taken on the way
-    const ff ht = {hv.x, hv.y};
-    const float2 lv = lr[t];
-    const ff q = ff_sub(ff_sub(ff{lv.x, lv.y}, xi), ht);
-    const ff x = ff_sub(ht, mu);
-    ff_acc(s[0], q);
-    ff_acc(s[1], ff_mul(q, q));
+    const float q = ((lv.x - hv.x) - xi) + (lv.y - hv.y);
+    const float x = (hv.x - mu) + hv.y;
+    s[0] += q;
+    s[1] = fmaf(q, q, s[1]);
     if (t + 1 < T) {
-        const float2 hn = h[t + 1];
-        const ff xn = ff_sub(ff{hn.x, hn.y}, mu);
-        const ff e = ff_sub(xn, ff_mul(phi, x));
-        ff_acc(s[2], x);
-        ff_acc(s[5], ff_mul(x, xn));
-        ff_acc(s[6], e);
-        ff_acc(s[7], ff_mul(e, e));
+        const float xn = (hn.x - mu) + hn.y;
+        const float e = fmaf(-phi, x, xn);
+        s[2] += x;
+        s[5] = fmaf(x, xn, s[5]);
+        s[6] += e;
+        s[7] = fmaf(e, e, s[7]);
     }
-    if (t >= 1) ff_acc(s[3], x);
-    if (t >= 1 && t + 1 < T) ff_acc(s[4], ff_mul(x, x));
+    if (t >= 1) s[3] += x;
+    if (t >= 1 && t + 1 < T) s[4] = fmaf(x, x, s[4]);
 }
 
 // The sweep itself (called by every lane of one warp, uniformly).
@@ -565,20 +562,41 @@ __global__ void __launch_bounds__(kGibbsMixedBlock, 2) k_gibbs_mixed(GibbsArgs A
     const int cur = A.cur ? *(volatile int*)A.cur : 0;
     const float2* h = cur ? A.h1f : A.h0f;
     const MixedTheta& m0 = *A.theta_f;
-    const ff xi = ff_sub(m0.ximu, m0.mu), mu = m0.mu, phi = m0.phi_ff;
+    const ff mu = m0.mu;
+    // the FP32 theta of the sweep (the hi parts of the prepared constants)
+    const float xi_f = ff_sub(m0.ximu, m0.mu).hi, mu_f = m0.mu.hi, phi_f = m0.phi_ff.hi;
     {
-        ff s[NSTAT];
-        for (int i = 0; i < NSTAT; ++i) s[i] = ff{0.f, 0.f};
+        float sf[NSTAT];
+        for (int i = 0; i < NSTAT; ++i) sf[i] = 0.f;
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        if (A.snap_out) {
-#pragma unroll 4
-            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
-                site_stats_f(h, A.lr_f, t, A.T, xi, mu, phi, s, A.snap_out);
-        } else {
-#pragma unroll 4
-            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.T; t += stride)
-                site_stats_f(h, A.lr_f, t, A.T, xi, mu, phi, s, nullptr);
+        // U sites per thread per round, their loads issued before any of
+        // their arithmetic (the pass is bound by load latency otherwise)
+        constexpr int U = 4;
+        for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t0 < A.T;
+             t0 += U * stride) {
+            float2 hv[U], lv[U], hn[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t t = t0 + u * stride;
+                hv[u] = lv[u] = hn[u] = make_float2(0.f, 0.f);
+                if (t < A.T) {
+                    hv[u] = h[t];
+                    lv[u] = A.lr_f[t];
+                    if (t + 1 < A.T) hn[u] = h[t + 1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t t = t0 + u * stride;
+                if (t < A.T) {
+                    // the chain's snapshot of h, taken on the way
+                    if (A.snap_out) A.snap_out[t] = hv[u].x + hv[u].y;
+                    site_stats_f(hv[u], lv[u], hn[u], t, A.T, xi_f, mu_f, phi_f, sf);
+                }
+            }
         }
+        ff s[NSTAT];
+        for (int i = 0; i < NSTAT; ++i) s[i] = ff{sf[i], 0.f};
         block_sum_ff(s, redf);
         float2* pf = reinterpret_cast<float2*>(A.partials);
         if (threadIdx.x == 0)
@@ -598,10 +616,18 @@ __global__ void __launch_bounds__(kGibbsMixedBlock, 2) k_gibbs_mixed(GibbsArgs A
         const float2* pf = reinterpret_cast<const float2*>(A.partials);
         ff acc = {0.f, 0.f};
         const int nb = (int)gridDim.x;
-#pragma unroll 4
-        for (int b = lane; b < nb; b += 32) {
-            const float2 v = __ldcg(pf + (int64_t)b * NSTAT + warp);
-            acc = ff_add(acc, ff{v.x, v.y});
+        // up to 16 partials per lane (the grid is at most 2 x 152 blocks,
+        // 10 per lane), all loads issued before the sums
+        constexpr int NB = 16;
+        for (int b0 = lane; b0 < nb; b0 += 32 * NB) {
+            float2 v[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int b = b0 + 32 * i;
+                v[i] = b < nb ? __ldcg(pf + (int64_t)b * NSTAT + warp) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i) acc = ff_add(acc, ff{v[i].x, v[i].y});
         }
         acc = warp_sum_ff(acc);
         if (lane == 0) s_tot[warp] = make_float2(acc.hi, acc.lo);
