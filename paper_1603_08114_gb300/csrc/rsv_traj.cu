@@ -714,10 +714,12 @@ __device__ __forceinline__ void stationary_part(HParts& acc, ff x1, const MixedT
     ff_acc(acc.Q, ff_mul(om, ff_mul(x1, x1)));
 }
 
-// Per-site work outside the leapfrog (loading, momenta, both ends of dH)
-// runs in rolled loops over the thread's slots through shared memory: fully
-// unrolled over J slots it is thousands of instructions per thread, more than
-// the instruction caches hold.
+// Per-site work outside the leapfrog goes through shared memory: each warp
+// loads its sites' inputs and writes their new state with consecutive lanes
+// (coalesced), filing each site to or from its owner thread's slots; momenta
+// and both ends of dH run in rolled loops over the thread's own slots (fully
+// unrolled over J slots they are thousands of instructions per thread, more
+// than the instruction caches hold).
 template <int J, bool MASS, bool LEV>
 __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajArgs A)
 {
