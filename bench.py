@@ -137,22 +137,39 @@ def _dist():
 
 
 def _barrier_max(ws, value):
+    """The maximum of `value` over the ranks (the job's time is its slowest
+    replica's)."""
     import torch
     if ws == 1:
         return value
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def _barrier(ws):
     import torch
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
+def replica_data_seed(rank: int) -> int:
+    """Seed of the synthetic series of one replica: the replicas are independent
+    chains on independent data (no data-path exchange between ranks)."""
+    return SEED_DATA + 1000 * rank
+
+
+def job_rate(ws: int, units_per_rank: float, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return ws * units_per_rank / seconds_max
 
 
 def cpu_baseline(budget_s: float = 12.0):
@@ -218,7 +235,7 @@ def run_ours(args):
     ws, rank, local = _dist()
     dev = torch.device("cuda", local)
     ctx = rsv.Context(local)
-    s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA + 1000 * rank)
+    s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=replica_data_seed(rank))
     y = torch.tensor(s.y, device=dev)
     lnrv = torch.tensor(s.lnrv, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -305,7 +322,7 @@ def run_ours(args):
         ess_min = [float(x) for x in ess_min]
         ess_th = torch.stack(ess_th).mean(0).cpu().numpy()
         return dict(
-            site_updates_per_s=ws * T_SITES * md_per_step / sec_per_step,
+            site_updates_per_s=job_rate(ws, T_SITES * md_per_step, sec_per_step),
             md_steps_per_step=md_per_step,
             n_md=n_md, dtau=dtau,
             ms_per_step=1e3 * sec_per_step,
