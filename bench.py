@@ -188,9 +188,42 @@ def cpu_baseline(budget_s: float = 12.0):
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 50:
             break
+    # one trajectory of the small workload (T = 2000, 50 x 0.02) for scale
+    s1 = synth.rsv_series(2000, synth.THETA_STD, seed=0)
+    t1 = time.perf_counter()
+    oracle.chain(s1.h_true, s1.y, s1.lnrv, s1.theta, 50, 0.02, seed=7, n_traj=20)
+    small_s = (time.perf_counter() - t1) / 20
     return {"value": T_SITES * N_MD * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} FP64 oracle trajectories of the same workload (T=2^20, 100 x 0.005), "
-                      f"{el:.1f} s, single-threaded C"}
+                      f"{el:.1f} s, single-threaded C",
+            "s_per_trajectory": {"T=2^20, 100 x 0.005": el / n, "T=2000, 50 x 0.02": small_s},
+            "host": _host()}
+
+
+def _host():
+    """CPU model and logical core count of this host."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model name"):
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            import subprocess
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"cpu": model or platform.machine(), "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -222,7 +255,7 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": WORKLOAD, "T": T_SITES, "n_md": N_MD,
                                         "dtau": DTAU, "step": "1 trajectory"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": _host()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
     return 0
 
