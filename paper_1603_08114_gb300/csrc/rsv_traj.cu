@@ -813,14 +813,19 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     for (int i = 0; i < 4; ++i) s_ph[(4 * q + i) * NT + tid] = z[i];
                 }
             }
-            // pass 1b: site constants, x, mass -> shared memory.  The warp
-            // loads its 32 J consecutive sites with consecutive lanes
-            // (coalesced) and files each into its owner's slots; the warp's
-            // threads share one segment.
+            // pass 1b: site constants, x, mass -> shared memory, and H at the
+            // start of the sites the lane loads.  The warp loads its 32 J
+            // consecutive sites with consecutive lanes (coalesced) and files
+            // each into its owner's slots; the warp's threads share one
+            // segment.  H is formed from the values as filed (the end of the
+            // trajectory reads the same ones back), and summed per warp with
+            // the end's H, so which lane takes which site does not matter.
             __syncwarp();  // the owners' momenta of pass 1a are in s_ph
+            HParts acc;
+            hparts_zero(acc);
             {
                 const int wb = (warp - v.g.warp0) * 32 * J;
-#pragma unroll 4
+#pragma unroll 2
                 for (int kk = lane; kk < 32 * J; kk += 32) {
                     const int ol = kk / J, j = kk - ol * J;
                     const int to = (warp << 5) + ol;  // the owner thread
@@ -836,49 +841,51 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     const float2 lr = act ? A.lr_f[s] : make_float2(mt.ximu.hi, mt.ximu.lo);
                     ff cp = two_sum(lr.x, -mt.ximu.hi);  // c' = lnRV - xi - mu
                     cp.lo += lr.y - mt.ximu.lo;
+                    float na = -a, vv = 0.0f;
                     if (LEV) {
                         const bool has_next = act && wlo + ii + 1 < v.si.T;
-                        na_t(j, to) = has_next ? -a * mt.ia : -a;
-                        v_t(j, to) = has_next ? mt.rsb * copysignf(sqrtf(2.0f * a), as) : 0.0f;
-                    } else {
-                        na_t(j, to) = -a;
+                        na = has_next ? -a * mt.ia : -a;
+                        vv = has_next ? mt.rsb * copysignf(sqrtf(2.0f * a), as) : 0.0f;
+                        v_t(j, to) = vv;
                     }
+                    na_t(j, to) = na;
                     k_t(j, to) = fmaf(-mt.iu, cp.hi + cp.lo, 0.5f);
+                    float dmv = dt;
+                    float p0 = s_ph[j * NT + to];
                     if (MASS) {
                         const float mi = (act && mass_on) ? A.minv[s] : 1.0f;
-                        dm_t(j, to) = dt * mi;
+                        dmv = dt * mi;
+                        dm_t(j, to) = dmv;
                         // p ~ N(0, m_t): the drawn normal over sqrt(1/m_t)
-                        if (!A.p_in) s_ph[j * NT + to] = s_ph[j * NT + to] / sqrtf(mi);
+                        if (!A.p_in) {
+                            p0 = p0 / sqrtf(mi);
+                            s_ph[j * NT + to] = p0;
+                        }
                     }
                     s_xh[j * NT + to] = x.hi;
                     s_xl[j * NT + to] = x.lo;
+                    // H at the start of this site if the segment owns it
+                    const int64_t sg = wlo + ii;
+                    if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
+                        const bool has_next = sg + 1 < v.si.T;
+                        ff xn = {0.f, 0.f};
+                        if (has_next) {  // inside the window: owned sites are not its last
+                            const float2 hn = hin[s + 1];
+                            xn = two_sum(hn.x, -mt.mu.hi);
+                            xn.lo += hn.y - mt.mu.lo;
+                            xn = fast_two_sum(xn.hi, xn.lo);
+                        }
+                        const float mi = MASS ? dmv * inv_dt : 1.0f;
+                        const float ah = (LEV && has_next) ? -na * mt.omr : -na;
+                        hparts_site<LEV>(acc, x, ff{p0, 0.f}, mi, cp, ah, xn, has_next, mt,
+                                         s_exptab, LEV ? vv * mt.ibf : 0.0f);
+                        if (sg == 0) stationary_part<LEV>(acc, x, mt);
+                    }
                 }
             }
             __syncthreads();
             mc.vL = (LEV && !v.first) ? s_v1[((P - 1) * NT + tid - 1) * 2 + 1] : 0.0f;
             mc.cfirst = (LEV && v.first) ? mt.cst : 0.0f;
-            // pass 2: H at the start over the owned sites (needs the next x)
-            HParts acc;
-            hparts_zero(acc);
-#pragma unroll 1
-            for (int j = 0; j < J; ++j) {
-                const int64_t sg = wlo + base + j;
-                if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
-                const ff x = {s_xh[j * NT + tid], s_xl[j * NT + tid]};
-                const int nidx = j + 1 < J ? (j + 1) * NT + tid : tid + 1;
-                const ff xn = {s_xh[nidx], s_xl[nidx]};
-                const float2 lr = A.lr_f[off + sg];
-                ff cp = two_sum(lr.x, -mt.ximu.hi);
-                cp.lo += lr.y - mt.ximu.lo;
-                const float mi = MASS ? dm_at(j) * inv_dt : 1.0f;
-                const bool has_next = sg + 1 < v.si.T;
-                const float a = (LEV && has_next) ? -na_at(j) * mt.omr : -na_at(j);
-                hparts_site<LEV>(acc, x, ff{s_ph[j * NT + tid], 0.f}, mi, cp, a, xn, has_next, mt,
-                                 s_exptab, LEV ? v_at(j) * mt.ibf : 0.0f);
-            }
-            // the stationary term of h_1, outside the loop (its thread only)
-            if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
-                stationary_part<LEV>(acc, ff{s_xh[tid], s_xl[tid]}, mt);
             h0 = hparts_total(acc, mt);
             // registers <- shared memory, then the first half step of eq. (6)
 #pragma unroll
