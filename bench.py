@@ -507,9 +507,12 @@ def run_ours(args):
     # headline: mixed precision (diagonal mass when given)
     # learned diagonal mass (untimed set-up): moments of the plain sampler over
     # n_snap trajectories, 2000 Adam steps, inverse mass, step tuned to ~0.8
-    # acceptance at trajectory length 2.5; fallback to the plain sampler below
+    # acceptance at the plain sampler's physical trajectory length (0.5 sqrt(m)
+    # in the mass's time units, m the median mass: with p ~ N(0, m) a site
+    # moves at ~1/sqrt(m) per unit time); fallback to the plain sampler below
     # 0.6 acceptance
     learned_info, sampler, head_nmd, head_dt = None, None, N_MD, DTAU
+    mass_length = None
     if minv is None and not args.no_learned:
         from paper_1603_08114_gb300 import learned
         h0 = torch.tensor(s.h_true, device=dev)
@@ -525,7 +528,9 @@ def run_ours(args):
                                 lr=1e-3, seed=7 + rank)
         b_ev.record()
         b_ev.synchronize()
-        head_dt, head_nmd = learned.tune_step(ctx, h0, y, lnrv, th0, tm.minv, length=2.5)
+        m_med = float(torch.quantile((1.0 / tm.minv[::16]).float(), 0.5))
+        mass_length = N_MD * DTAU * m_med ** 0.5
+        head_dt, head_nmd = learned.tune_step(ctx, h0, y, lnrv, th0, tm.minv, length=mass_length)
         minv = tm.minv
         sampler = learned.MassSampler(ctx, minv, head_dt, head_nmd, DTAU, N_MD, window=100)
         m = (1.0 / minv).float()
@@ -536,8 +541,10 @@ def run_ours(args):
                         "loss_last": float(losses[-50:].mean()),
                         "m_quantiles": [float(v) for v in torch.quantile(
                             m[::16], torch.tensor([0.01, 0.5, 0.99], device=dev))],
-                        "dtau": head_dt, "n_md": head_nmd}
+                        "dtau": head_dt, "n_md": head_nmd, "trajectory_length": mass_length}
 
+    if minv is not None and mass_length is None:  # a mass from --mass-file
+        mass_length = N_MD * DTAU * float(torch.quantile((1.0 / minv[::16]).float(), 0.5)) ** 0.5
     clocks = Clocks(local)
     head = arm("mixed", minv, args.warmup, args.steps, clocks=clocks, timing=True,
                n_md=head_nmd, dtau=head_dt, sampler=sampler)
@@ -553,7 +560,8 @@ def run_ours(args):
         batched = batched_leg(max(3, min(args.steps, 10)))
         levr = leverage_leg(min(args.steps, 3))
         # the minimum-norm integrator (two forces per step) at the plain
-        # sampler's trajectory length (0.5; 2.5 in the learned mass's units):
+        # sampler's physical trajectory length (0.5; 0.5 sqrt(m) in the
+        # learned mass's units):
         # the fewest steps whose acceptance over 40 trial trajectories
         # reaches 0.8, identity mass and learned mass
         def tune_mn(mass, length):
@@ -569,7 +577,8 @@ def run_ours(args):
         rsv.rsv_set_integrator(ctx, "omelyan2")
         try:
             mn = {}
-            for tag, mass, length in (("identity", None, 0.5), ("learned", minv, 2.5)):
+            for tag, mass, length in (("identity", None, N_MD * DTAU),
+                                      ("learned", minv, mass_length)):
                 if tag == "learned" and mass is None:
                     continue
                 n_mn = tune_mn(mass, length)
