@@ -536,117 +536,95 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
     const float2 half = f2(0.5f, 0.5f), phi2 = f2(c.phi, c.phi), nphi2 = f2(-c.phi, -c.phi);
     const float2 zero = f2(0.0f, 0.0f);
     const float2 ndt = f2(-c.kick, -c.kick);
-    if (!LEV) {
-        // The edge exchange overlaps the interior pairs 1..P-2, which need no
-        // neighbour from another thread: the edges are published (warp
-        // shuffles, the warps' end values to shared memory), the interior
-        // pairs advance, and only then the block barrier and pairs 0 and P-1.
-        const int lane = tid & 31, warp = tid >> 5;
-        // one pair: force of eq. (7) in three-point form, then the kick and
-        // the drift, compensated
-        auto advance = [&](int q, float2 prev, float2 nxt, float2 cx, float hs) {
-            const float4 ak = s_ak[q * NT + tid];
-            const float2 xq = X[q];
-            if (EDGE) {
-                if (q == c.la) nxt.x = c.phi * xq.x;
-                if (q + P == c.la) nxt.y = c.phi * xq.y;
-            }
-            float2 f = fma2(c0, xq, f2(ak.z, ak.w));
-            f = fma2(c1, add2(prev, nxt), f);
+    // The edge exchange overlaps the interior pairs 1..P-2, which need no
+    // neighbour from another thread: the edges are published (warp shuffles,
+    // the warps' end values to shared memory), the interior pairs advance, and
+    // only then the block barrier and pairs 0 and P-1.  Per site the same
+    // operations in the same order as a pass in pair order.
+    const int lane = tid & 31, warp = tid >> 5;
+    // e^{-h/2} of a pair (leverage)
+    auto e2_of = [&](float2 xq) -> float2 {
+        const float2 t = fma2(nl2h, xq, cmh);
+        return f2(ex2_approx(t.x), ex2_approx(t.y));
+    };
+    // one pair: force of eq. (7) in three-point form, then the kick and the
+    // drift, compensated.  LEV: e2 = e^{-h/2} of the pair, prevw = w of its
+    // left neighbours; returns the pair's w.
+    auto advance = [&](int q, float2 prev, float2 nxt, float2 cx, float hs, float2 e2,
+                       float2 prevw) -> float2 {
+        const float4 ak = s_ak[q * NT + tid];
+        const float2 xq = X[q];
+        if (EDGE) {
+            if (q == c.la) nxt.x = c.phi * xq.x;
+            if (q + P == c.la) nxt.y = c.phi * xq.y;
+        }
+        float2 f = fma2(c0, xq, f2(ak.z, ak.w));
+        f = fma2(c1, add2(prev, nxt), f);
+        float2 w = zero;
+        if (LEV) {
+            f = fma2(f2(ak.x, ak.y), fma2(e2, e2, zero), f);
+            w = fma2(s_v[q * NT + tid], e2, zero);
+            const float2 g = fma2(half, fma2(nphi2, xq, nxt), phi2);
+            f = sub2(fma2(w, g, f), prevw);
+            if (q == 0) f.x = fmaf(c.cfirst, xq.x, f.x);
+        } else {
             // (y^2/2) e^{-h} = a 2^{-(x + mu) log2 e}: a small exponent argument
             const float2 t = fma2(nl2e, xq, cmu);
             f = fma2(f2(ak.x, ak.y), f2(ex2_approx(t.x), ex2_approx(t.y)), f);
-            cupd2(PH[q], PL[q], ndt, f);
-            float2 cq = cx;
-            if (MASS) {
-                const float2 dm = s_dm[q * NT + tid];
-                cq = f2(hs * dm.x, hs * dm.y);
-            }
-            cupd2(X[q], XL[q], cq, PH[q]);
-        };
-        for (int k = 0; k < c.n_sub; ++k) {
-            float* edge = s_edge + par * 2 * nw;
-            par ^= 1;
-            const float first = X[0].x, last = X[P - 1].y;
-            const float up = __shfl_up_sync(0xffffffffu, last, 1);
-            const float dn = __shfl_down_sync(0xffffffffu, first, 1);
-            if (lane == 0) edge[2 * warp] = first;
-            if (lane == 31) edge[2 * warp + 1] = last;
-            const float xP = X[0].y;       // x_P before the step
-            const float2 x1 = X[1];        // pair 1 before the step (pair 0's right neighbours)
-            const float hs = (k + 1 < c.n_sub) ? ((k & 1) ? c.r_odd : c.r_even) : c.r_last;
-            const float2 cx = f2(hs * c.dt, hs * c.dt);
-            float2 prev = X[0];  // left neighbours of pair 1, before the step
-#pragma unroll
-            for (int q = 1; q + 1 < P; ++q) {
-                const float2 xq = X[q];
-                advance(q, prev, X[q + 1], cx, hs);
-                prev = xq;
-            }
-            __syncthreads();
-            const bool has_l = warp > 0, has_r = warp + 1 < nw;
-            const float el = edge[2 * (has_l ? warp - 1 : warp) + 1];
-            const float er = edge[2 * (has_r ? warp + 1 : warp)];
-            float xL = lane == 0 ? (has_l ? el : first) : up;
-            float xR = lane == 31 ? (has_r ? er : last) : dn;
-            if (c.first) xL = c.phi * X[0].x;
-            if (!EDGE && c.la == J - 1) xR = c.phi * X[P - 1].y;
-            // pair 0 (X[P-1] is still the state before the step), then P-1
-            advance(0, f2(xL, X[P - 1].x), x1, cx, hs);
-            advance(P - 1, prev, f2(xP, xR), cx, hs);
         }
-        return;
-    }
+        cupd2(PH[q], PL[q], ndt, f);
+        float2 cq = cx;
+        if (MASS) {
+            const float2 dm = s_dm[q * NT + tid];
+            cq = f2(hs * dm.x, hs * dm.y);
+        }
+        cupd2(X[q], XL[q], cq, PH[q]);
+        return w;
+    };
     for (int k = 0; k < c.n_sub; ++k) {
-        float xL, xR;
-        exchange(X[0].x, X[P - 1].y, xL, xR, s_edge + par * 2 * nw, nw);
+        float* edge = s_edge + par * 2 * nw;
         par ^= 1;
-        if (c.first) xL = c.phi * X[0].x;
-        if (!EDGE && c.la == J - 1) xR = c.phi * X[P - 1].y;
+        const float first = X[0].x, last = X[P - 1].y;
+        const float up = __shfl_up_sync(0xffffffffu, last, 1);
+        const float dn = __shfl_down_sync(0xffffffffu, first, 1);
+        if (lane == 0) edge[2 * warp] = first;
+        if (lane == 31) edge[2 * warp + 1] = last;
         const float xP = X[0].y;  // x_P before the step
-        float2 prev = f2(xL, X[P - 1].x);  // left neighbours of pair 0, before the step
-        float2 prevw = zero;               // their w (leverage)
-        if (LEV) {
-            const float2 vP = s_v[(P - 1) * NT + tid];
-            prevw = f2(c.vL * ex2_approx(fmaf(-0.5f * kLog2e, xL, 0.5f * c.cmu)),
-                       vP.x * ex2_approx(fmaf(-0.5f * kLog2e, X[P - 1].x, 0.5f * c.cmu)));
-        }
+        const float2 x1 = X[1];   // pair 1 before the step (pair 0's right neighbours)
         const float hs = (k + 1 < c.n_sub) ? ((k & 1) ? c.r_odd : c.r_even) : c.r_last;
         const float2 cx = f2(hs * c.dt, hs * c.dt);
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const float4 ak = s_ak[q * NT + tid];
-            const float2 xq = X[q];
-            float2 nxt = (q + 1 < P) ? X[q + 1] : f2(xP, xR);
-            if (EDGE) {
-                if (q == c.la) nxt.x = c.phi * xq.x;
-                if (q + P == c.la) nxt.y = c.phi * xq.y;
-            }
-            float2 f = fma2(c0, xq, f2(ak.z, ak.w));
-            f = fma2(c1, add2(prev, nxt), f);
-            if (LEV) {
-                const float2 t = fma2(nl2h, xq, cmh);
-                const float2 e2 = f2(ex2_approx(t.x), ex2_approx(t.y));  // e^{-h/2}
-                f = fma2(f2(ak.x, ak.y), fma2(e2, e2, zero), f);
-                const float2 w = fma2(s_v[q * NT + tid], e2, zero);
-                const float2 g = fma2(half, fma2(nphi2, xq, nxt), phi2);
-                f = sub2(fma2(w, g, f), prevw);
-                prevw = w;
-                if (q == 0) f.x = fmaf(c.cfirst, xq.x, f.x);
-            } else {
-                // (y^2/2) e^{-h} = a 2^{-(x + mu) log2 e}: a small exponent argument
-                const float2 t = fma2(nl2e, xq, cmu);
-                f = fma2(f2(ak.x, ak.y), f2(ex2_approx(t.x), ex2_approx(t.y)), f);
-            }
-            prev = xq;
-            cupd2(PH[q], PL[q], ndt, f);
-            float2 cq = cx;
-            if (MASS) {
-                const float2 dm = s_dm[q * NT + tid];
-                cq = f2(hs * dm.x, hs * dm.y);
-            }
-            cupd2(X[q], XL[q], cq, PH[q]);
+        // leverage: e^{-h/2} of pairs 0 and P-1 before the step, and w of pair 0
+        float2 e2_0 = zero, e2_last = zero, prevw = zero;
+        if (LEV) {
+            e2_0 = e2_of(X[0]);
+            e2_last = e2_of(X[P - 1]);
+            prevw = fma2(s_v[tid], e2_0, zero);
         }
+        float2 prev = X[0];  // left neighbours of pair 1, before the step
+#pragma unroll
+        for (int q = 1; q + 1 < P; ++q) {
+            const float2 xq = X[q];
+            const float2 w = advance(q, prev, X[q + 1], cx, hs, LEV ? e2_of(xq) : zero, prevw);
+            prev = xq;
+            prevw = w;
+        }
+        __syncthreads();
+        const bool has_l = warp > 0, has_r = warp + 1 < nw;
+        const float el = edge[2 * (has_l ? warp - 1 : warp) + 1];
+        const float er = edge[2 * (has_r ? warp + 1 : warp)];
+        float xL = lane == 0 ? (has_l ? el : first) : up;
+        float xR = lane == 31 ? (has_r ? er : last) : dn;
+        if (c.first) xL = c.phi * X[0].x;
+        if (!EDGE && c.la == J - 1) xR = c.phi * X[P - 1].y;
+        // pair 0 (X[P-1] is still the state before the step), then P-1
+        float2 prevw0 = zero;
+        if (LEV) {
+            const float2 vP = s_v[(P - 1) * NT + tid];
+            prevw0 = f2(c.vL * ex2_approx(fmaf(-0.5f * kLog2e, xL, 0.5f * c.cmu)),
+                        vP.x * e2_last.x);
+        }
+        advance(0, f2(xL, X[P - 1].x), x1, cx, hs, e2_0, prevw0);
+        advance(P - 1, prev, f2(xP, xR), cx, hs, e2_last, prevw);
     }
 }
 
