@@ -267,8 +267,11 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
     p.mixed = mixed;
     p.mass = mass;
     p.lev = lev;
-    int bps = blocks_per_sm(mixed, mass, lev, j, nt, p.smem);
-    if (bps < 1) bps = 1;
+    const int bps = blocks_per_sm(mixed, mass, lev, j, nt, p.smem);
+    if (bps < 1) {  // a fixed schedule whose block does not fit on an SM
+        *why = "the block shape does not fit on one SM (shared memory or registers)";
+        return false;
+    }
     p.grid = std::min(nbins, num_sms * bps);
 
     // ---- device copy -----------------------------------------------------------

@@ -451,7 +451,8 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
 // slot j of thread tid at [j][tid]):
 //   s_ak  float4 [J/2][NT]  (a_j, k_j, a_{j+1}, k_{j+1}): a = y^2/2,
 //                           k = 1/2 - c'/s_u^2
-//   s_dm  float4 [J/4][NT]  dtau/m of 4 consecutive slots (with a mass only)
+//   s_dm  float2 [J/2][NT]  -kick/m of the pair (with a mass only; the state
+//                           then holds the velocity v = p/m)
 //   s_x0h, s_x0l, s_p0h  float [J][NT]  start of the trajectory, for dH (p0
 //                           enters with lo = 0: drawn in FP32 or rounded from p_in)
 // ---------------------------------------------------------------------------
@@ -511,7 +512,10 @@ __device__ __forceinline__ void cupd2(float2& hi, float2& lo, float2 c, float2 u
 // site takes x_P from before the step.
 // EDGE: some thread of the warp ends a series before its last slot; the ghost
 // replaces the right neighbour there by a select.
-// s_ak: float4 [P][NT] = (-a_p, -a_{p+P}, k_p, k_{p+P}); s_dm: float2 [P][NT].
+// s_ak: float4 [P][NT] = (-a_p, -a_{p+P}, k_p, k_{p+P}); s_dm: float2 [P][NT]
+// of -kick/m: with a diagonal mass the state carries the velocity v = p/m, so
+// that the drift x += c dtau v is the same for every site and the mass enters
+// the kick v -= kick F/m alone.
 //
 // LEV (leverage): with B in c0 and c1, the force gains
 //   w_t (phi + (x_{t+1} - phi x_t)/2) - w_{t-1},  w_t = v_t e^{-h_t/2},
@@ -572,13 +576,10 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
             const float2 t = fma2(nl2e, xq, cmu);
             f = fma2(f2(ak.x, ak.y), f2(ex2_approx(t.x), ex2_approx(t.y)), f);
         }
-        cupd2(PH[q], PL[q], ndt, f);
-        float2 cq = cx;
-        if (MASS) {
-            const float2 dm = s_dm[q * NT + tid];
-            cq = f2(hs * dm.x, hs * dm.y);
-        }
-        cupd2(X[q], XL[q], cq, PH[q]);
+        // with a mass the state holds the velocity v = p/m: the kick takes
+        // the per-site -kick/m, the drift is the same for every site
+        cupd2(PH[q], PL[q], MASS ? s_dm[q * NT + tid] : ndt, f);
+        cupd2(X[q], XL[q], cx, PH[q]);
         return w;
     };
     for (int k = 0; k < c.n_sub; ++k) {
@@ -652,14 +653,16 @@ __device__ __forceinline__ ff hparts_total(const HParts& a, const MixedTheta& mt
 // xn: next site's x (used only if has_next).
 // LEV: Q is d_t^2 = (x_{t+1} - phi x_t - rs_y e^{-h_t/2})^2, rs_y = rho s_eta y_t
 // (weighted by B/2 in he).
-template <bool LEV>
-__device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, float mi, ff cp, float a,
+// With a mass, p is the velocity v = p/m and mw the double-float mass m, so
+// that K = m v^2 (see mass_weight).
+template <bool LEV, bool MASS>
+__device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, ff mw, ff cp, float a,
                                             ff xn, bool has_next, const MixedTheta& mt,
                                             const float2* tab, float rs_y = 0.0f)
 {
     ff p2 = two_prod(p.hi, p.hi);  // (hi + lo)^2 to ~2^-48
     p2.lo = fmaf(2.0f * p.hi, p.lo, p2.lo);
-    ff_acc(acc.K, mi == 1.0f ? p2 : ff_mul_f(p2, mi));
+    ff_acc(acc.K, MASS ? ff_mul(p2, mw) : p2);
     ff_acc(acc.L, x);
     const ff r = ff_sub(x, cp);
     ff_acc(acc.R, ff_mul(r, r));
@@ -679,6 +682,17 @@ __device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, float mi, f
         const ff E = ff_exp(nh, tab);
         ff_acc(acc.E, ff_mul_f(E, a));
     }
+}
+
+// The mass m' = -kick / km that the kick v -= km F (km = -kick/m in FP32)
+// integrates, in double-float: one reciprocal and a Newton correction, so that
+// K = m' v^2 is the kinetic energy of exactly the dynamics the kick applies.
+__device__ __forceinline__ ff mass_weight(float kick, float km)
+{
+    const float t = __frcp_rn(km);
+    const float q = -kick * t;
+    const float r = fmaf(-q, km, -kick);  // -kick - q km, exact
+    return fast_two_sum(q, r * t);
 }
 
 // The stationary term (1 - phi^2) x_1^2 / (2 s_eta^2) of S, into Q (weighted
@@ -715,7 +729,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
     constexpr int P = J / 2;
     float4* s_ak = reinterpret_cast<float4*>(smem_raw);  // [P][NT] (-a, -a', k, k') of (p, p+P)
     float* s_ak1 = reinterpret_cast<float*>(smem_raw);
-    float2* s_dm = reinterpret_cast<float2*>(s_ak + P * NT);  // [P][NT] dtau/m of (p, p+P)
+    float2* s_dm = reinterpret_cast<float2*>(s_ak + P * NT);  // [P][NT] -kick/m of (p, p+P)
     float* s_dm1 = reinterpret_cast<float*>(s_dm);
     float2* s_v = s_dm + (MASS ? P * NT : 0);  // [P][NT] leverage v of (p, p+P)
     float* s_v1 = reinterpret_cast<float*>(s_v);
@@ -724,7 +738,6 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
     float* s_ph = s_xl + W;
     const bool mass_on = MASS && (A.mass_on == nullptr || *A.mass_on != 0);
     const float dt = (float)A.dtau;
-    const float inv_dt = 1.0f / dt;  // 1/m_t = (dtau/m_t) / dtau, the same at both ends of dH
     // slot j is lane j / P of pair j % P
     // slot j of thread t
     auto na_t = [&](int j, int t) -> float& { return s_ak1[((j % P) * NT + t) * 4 + j / P]; };
@@ -828,17 +841,21 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                     }
                     na_t(j, to) = na;
                     k_t(j, to) = fmaf(-mt.iu, cp.hi + cp.lo, 0.5f);
-                    float dmv = dt;
+                    float kmv = -mc.kick;
                     float p0 = s_ph[j * NT + to];
                     if (MASS) {
                         const float mi = (act && mass_on) ? A.minv[s] : 1.0f;
-                        dmv = dt * mi;
-                        dm_t(j, to) = dmv;
-                        // p ~ N(0, m_t): the drawn normal over sqrt(1/m_t)
-                        if (!A.p_in) {
-                            p0 = p0 / sqrtf(mi);
-                            s_ph[j * NT + to] = p0;
-                        }
+                        kmv = -mc.kick * mi;
+                        dm_t(j, to) = kmv;
+                        // the velocity v = p/m: p ~ N(0, m_t) is the drawn normal
+                        // times sqrt(m_t), so v is the normal times sqrt(1/m_t); a
+                        // given p is divided by the mass the kick integrates
+                        if (A.p_in)
+                            p0 = act ? (float)(A.p_in[s] * ((double)kmv / -(double)mc.kick))
+                                     : 0.0f;
+                        else
+                            p0 = p0 * sqrtf(mi);
+                        s_ph[j * NT + to] = p0;
                     }
                     s_xh[j * NT + to] = x.hi;
                     s_xl[j * NT + to] = x.lo;
@@ -853,10 +870,10 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
                             xn.lo += hn.y - mt.mu.lo;
                             xn = fast_two_sum(xn.hi, xn.lo);
                         }
-                        const float mi = MASS ? dmv * inv_dt : 1.0f;
+                        const ff mw = MASS ? mass_weight(mc.kick, kmv) : ff{1.f, 0.f};
                         const float ah = (LEV && has_next) ? -na * mt.omr : -na;
-                        hparts_site<LEV>(acc, x, ff{p0, 0.f}, mi, cp, ah, xn, has_next, mt,
-                                         s_exptab, LEV ? vv * mt.ibf : 0.0f);
+                        hparts_site<LEV, MASS>(acc, x, ff{p0, 0.f}, mw, cp, ah, xn, has_next, mt,
+                                               s_exptab, LEV ? vv * mt.ibf : 0.0f);
                         if (sg == 0) stationary_part<LEV>(acc, x, mt);
                     }
                 }
@@ -875,11 +892,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             }
             const float r0 = A.integrator == 1 ? (float)A.lambda : 0.5f;  // first drift
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                const float2 c0 = MASS ? f2(r0 * dm_at(q), r0 * dm_at(q + P))
-                                       : f2(r0 * dt, r0 * dt);
-                cupd2(X[q], XL[q], c0, PH[q]);
-            }
+            for (int q = 0; q < P; ++q) cupd2(X[q], XL[q], f2(r0 * dt, r0 * dt), PH[q]);
         }
 
         int par = 0;
@@ -923,11 +936,11 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             const float2 lr = A.lr_f[off + sg];
             ff cp = two_sum(lr.x, -mt.ximu.hi);
             cp.lo += lr.y - mt.ximu.lo;
-            const float mi = MASS ? dm_at(j) * inv_dt : 1.0f;
+            const ff mw = MASS ? mass_weight(mc.kick, dm_at(j)) : ff{1.f, 0.f};
             const bool has_next = sg + 1 < v.si.T;
             const float a = (LEV && has_next) ? -na_at(j) * mt.omr : -na_at(j);
-            hparts_site<LEV>(acc, x, ff{s_ph[j * NT + tid], k_at(j)}, mi, cp, a, xn, has_next, mt,
-                             s_exptab, LEV ? v_at(j) * mt.ibf : 0.0f);
+            hparts_site<LEV, MASS>(acc, x, ff{s_ph[j * NT + tid], k_at(j)}, mw, cp, a, xn, has_next,
+                                   mt, s_exptab, LEV ? v_at(j) * mt.ibf : 0.0f);
         }
         if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
             stationary_part<LEV>(acc, ff{s_xh[tid], s_xl[tid]}, mt);
@@ -962,7 +975,8 @@ __global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajAr
             for (int j = 0; j < J; ++j) {
                 const int64_t sg = wlo + base + j;
                 if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi)
-                    A.p_out[off + sg] = (double)s_ph[j * NT + tid] + (double)k_at(j);
+                    A.p_out[off + sg] = ((double)s_ph[j * NT + tid] + (double)k_at(j)) *
+                                        (MASS ? -(double)mc.kick / (double)dm_at(j) : 1.0);
             }
         }
         if (v.g.split) finish_split_ff(A, v, s_splitf, &s_flag);

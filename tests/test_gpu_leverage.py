@@ -227,3 +227,22 @@ def test_rho_zero_restores_the_plain_model(rsv, ctx, lev, prec):
         rsv.rsv_sync_status(ctx)
         outs.append((h.cpu().numpy(), dH.item()))
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+def test_block_that_does_not_fit_is_refused(rsv, ctx, lev):
+    """Leverage and a mass add two per-site arrays to shared memory: a forced
+    block of 512 x 16 sites no longer fits on an SM and the call returns
+    RSV_EINVAL before any launch (the automatic planner skips such shapes)."""
+    T = 20000
+    s = synth.rsv_series_leverage(T, TH, RHO, seed=2)
+    minv = dev(np.ones(T), torch.float32)
+    lev()
+    rsv.rsv_set_schedule(ctx, 512, 16, 512 * 16 - 2 * 11 - 3)
+    h = dev(s.h_true)
+    with pytest.raises(rsv.RSVError, match="RSV_EINVAL"):
+        rsv.rsv_hmc_trajectory(ctx, h, None, dev(s.y), dev(s.lnrv), TH, 10, 0.02,
+                               prec="mixed", minv=minv)
+    rsv.rsv_set_schedule(ctx)
+    rsv.rsv_hmc_trajectory(ctx, h, None, dev(s.y), dev(s.lnrv), TH, 10, 0.02, prec="mixed",
+                           minv=minv)
+    rsv.rsv_sync_status(ctx)
