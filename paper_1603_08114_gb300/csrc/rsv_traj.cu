@@ -685,11 +685,13 @@ __device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, ff mw, ff c
 }
 
 // The mass m' = -kick / km that the kick v -= km F (km = -kick/m in FP32)
-// integrates, in double-float: one reciprocal and a Newton correction, so that
-// K = m' v^2 is the kinetic energy of exactly the dynamics the kick applies.
+// integrates, in double-float: an approximate reciprocal (rcp.approx, ~2^-23)
+// and one correction with the exact residual, so that K = m' v^2 is the
+// kinetic energy of exactly the dynamics the kick applies (~2^-46).
 __device__ __forceinline__ ff mass_weight(float kick, float km)
 {
-    const float t = __frcp_rn(km);
+    float t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(km));
     const float q = -kick * t;
     const float r = fmaf(-q, km, -kick);  // -kick - q km, exact
     return fast_two_sum(q, r * t);
