@@ -15,3 +15,27 @@ def test_paper_table2_matches_its_stated_gain():
     import bench
     t = bench.PAPER_TABLE2
     assert abs(t["cpu"]["C"] / t["gpu"]["C"] - t["gain_limit"]) < 0.05
+
+
+def _golden_table2():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_table2.txt")
+    rows = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        rows[parts[0]] = [float(v) for v in parts[1:]]
+    return rows
+
+
+def test_golden_table2_is_self_consistent_and_matches_bench():
+    """The Table 2 fixture reproduces the gain Sec. 5 states, and bench.py's
+    copy of it (printed with the --table2 sweep) is the same."""
+    import bench
+    g = _golden_table2()
+    gpu, cpu = g["gpu_cuda_fortran_gtx760"], g["cpu_i7_4770_3.4GHz"]
+    assert abs(cpu[1] / gpu[1] - g["gain_limit"][0]) < 0.05
+    t = bench.PAPER_TABLE2
+    assert (t["gpu"]["A"], t["gpu"]["C"]) == tuple(gpu)
+    assert (t["cpu"]["A"], t["cpu"]["C"]) == tuple(cpu)
