@@ -44,7 +44,7 @@ bool valid_j(bool mixed, int j)
     return false;
 }
 
-int ntmax(bool mixed, int j) { return mixed ? mixed_max_threads(j) : 256; }
+int ntmax(bool mixed, bool mass, int j) { return mixed ? mixed_max_threads(j, mass) : 256; }
 
 }  // namespace
 
@@ -82,7 +82,7 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
     int nt = 0, j = 0;
     int64_t tile = 0;
     if (sched_nt > 0) {
-        if (!valid_j(mixed, sched_j) || sched_nt % 32 || sched_nt > ntmax(mixed, sched_j) ||
+        if (!valid_j(mixed, sched_j) || sched_nt % 32 || sched_nt > ntmax(mixed, mass, sched_j) ||
             sched_tile < 1 || sched_tile + 2 * K + 3 > (int64_t)sched_nt * sched_j ||
             smem_for(mixed, mass, lev, sched_nt, sched_j) > smem_cap) {
             *why = "the fixed schedule does not fit this call";
@@ -99,7 +99,7 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
         const int* js = mixed ? kJ_mixed : kJ_fp64;
         const int nj = mixed ? kNJ_mixed : kNJ_fp64;
         for (int ji = 0; ji < nj; ++ji) {
-            const int tmax = ntmax(mixed, js[ji]);
+            const int tmax = ntmax(mixed, mass, js[ji]);
             for (int t = 32; t <= tmax; t += 32) {
                 const int64_t cap = (int64_t)t * js[ji];
                 if (smem_for(mixed, mass, lev, t, js[ji]) > smem_cap) continue;
@@ -153,7 +153,7 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
     } else {
         // many series: the largest window, so that most series are whole
         j = mixed ? 20 : 28;
-        nt = ntmax(mixed, j);
+        nt = ntmax(mixed, mass, j);
         tile = (int64_t)nt * j - 2 * K - 3;
         if (tile < 1) {
             *why = "n_md too large for an on-chip window";

@@ -456,10 +456,12 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
 //   s_x0h, s_x0l, s_p0h  float [J][NT]  start of the trajectory, for dH (p0
 //                           enters with lo = 0: drawn in FP32 or rounded from p_in)
 // ---------------------------------------------------------------------------
-template <int J>
+// (with a mass and J = 4 at most 768 threads: its load pass needs more than
+// the 64 registers a 1024-thread block leaves)
+template <int J, bool MASS>
 constexpr int mixed_ntmax()
 {
-    return J <= 4 ? 1024 : J <= 8 ? 768 : J <= 12 ? 640 : J <= 16 ? 512 : 384;
+    return J <= 4 ? (MASS ? 768 : 1024) : J <= 8 ? 768 : J <= 12 ? 640 : J <= 16 ? 512 : 384;
 }
 
 // 2^(j/32), j = 0..31, as double-float pairs, written by the theta prep kernel
@@ -715,7 +717,7 @@ __device__ __forceinline__ void stationary_part(HParts& acc, ff x1, const MixedT
 // unrolled over J slots they are thousands of instructions per thread, more
 // than the instruction caches hold).
 template <int J, bool MASS, bool LEV>
-__global__ void __launch_bounds__(mixed_ntmax<J>(), 1) k_traj_mixed(const TrajArgs A)
+__global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const TrajArgs A)
 {
     static_assert(J % 4 == 0, "J must be a multiple of 4");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1124,14 +1126,14 @@ cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, doub
     return cudaGetLastError();
 }
 
-int mixed_max_threads(int j)
+int mixed_max_threads(int j, bool mass)
 {
     switch (j) {
-        case 4: return mixed_ntmax<4>();
-        case 8: return mixed_ntmax<8>();
-        case 12: return mixed_ntmax<12>();
-        case 16: return mixed_ntmax<16>();
-        case 20: return mixed_ntmax<20>();
+        case 4: return mass ? mixed_ntmax<4, true>() : mixed_ntmax<4, false>();
+        case 8: return mixed_ntmax<8, false>();
+        case 12: return mixed_ntmax<12, false>();
+        case 16: return mixed_ntmax<16, false>();
+        case 20: return mixed_ntmax<20, false>();
         default: return 0;
     }
 }

@@ -158,9 +158,9 @@ cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st);
 // of 2^(j/32).
 cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, double rho,
                               MixedTheta* theta_f, cudaStream_t st);
-// Largest block (threads) of the mixed kernel with `j` sites per thread (0 if
-// j is not instantiated).
-int mixed_max_threads(int j);
+// Largest block (threads) of the mixed kernel with `j` sites per thread, with
+// or without a mass (0 if j is not instantiated).
+int mixed_max_threads(int j, bool mass);
 // Resident blocks per SM of a trajectory kernel configuration (0 if invalid).
 int blocks_per_sm(bool mixed, bool mass, bool lev, int j, int nt, size_t smem);
 
