@@ -8,11 +8,15 @@ rsv_hmc_chain call that also records every trajectory's h and theta for ESS.  Th
 chain continues from step to step (the warm-up steps are its burn-in).
 
 Headline sampler: mixed precision with the learned diagonal mass (trained
-before timing from 10^4 plain-sampler snapshots; its step size and trajectory
-length tuned to ~0.8 acceptance; identity-mass fallback).  Reported:
-leapfrog site-updates/s (T * n_md * trajectories / time) and ESS/s of h
-(per-site ESS over the step's 200 draws / step time) and of theta, beside the
-plain mixed and plain FP64 samplers (identity mass, 100 x 0.005).
+before timing from 10^4 plain-sampler snapshots; its step size tuned to ~0.8
+acceptance at the plain sampler's physical trajectory length; identity-mass
+fallback).  Reported: leapfrog site-updates/s (T * n_md * trajectories /
+time) and ESS/s of h (per-site ESS over the step's 200 draws / step time) and
+of theta, beside the plain mixed and plain FP64 samplers (identity mass,
+100 x 0.005), the 4096-series batched workload, the RSV model with leverage
+and the minimum-norm integrator (identity and learned mass); the MD-only
+rate, the end-to-end rate from pinned host buffers, the trajectory kernel's
+roofline and the CPU oracle's rate.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -45,8 +49,9 @@ WORKLOAD = ("rsv-hmc single chain T=2^20, theta sampled, 200 trajectories per st
             "learned mass (tuned dtau, n_md) vs identity 100 x 0.005")
 # Algorithmic FP32 operations per site and leapfrog step of the mixed kernel:
 # the three-point force (neighbour sum 1, two stencil FMAs 2, exponent argument
-# 1, the y^2/2 e^-h term 1), the compensated p update (4) and the compensated
-# h update (4).  The exp2 itself runs on the special-function unit.
+# 1, the y^2/2 e^-h term 1), the compensated p update (4; the velocity p/m
+# with a mass) and the compensated h update (4).  The exp2 itself runs on the
+# special-function unit.
 OPS_PER_SITE_STEP_MIXED = 13
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_traj_mixed launch of
 # the headline workload (learned mass, T = 2^20), from the capture summarised in
