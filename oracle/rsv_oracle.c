@@ -65,6 +65,14 @@ static double sum_get(const orc_sum* a) { return a->s + a->c; }
 /* the marginal of eta_t, hence the stationary law of h_1, is unchanged.      */
 /* rho = 0 gives the d_t = x_{t+1} - phi x_t of eq. (3).                      */
 /* ------------------------------------------------------------------------ */
+/* rho s_eta eps_t, the leverage shift of eta_t's conditional mean (exactly
+ * 0 for rho = 0, where the exponential is not needed). */
+static double lev_shift(const double* h, const double* y, orc_theta th, long t)
+{
+    if (th.rho == 0.0) return 0.0;
+    return th.rho * sqrt(th.sig_eta2) * (y[t] * exp(-0.5 * h[t]));
+}
+
 double orc_site_action(const double* h, const double* y, const double* lnrv,
                        long T, orc_theta th, long t)
 {
@@ -78,8 +86,7 @@ double orc_site_action(const double* h, const double* y, const double* lnrv,
      * leverage: N(mu + phi (h_t - mu) + rho s_eta eps_t, s_eta^2 (1 - rho^2)) */
     double x = ht - th.mu;
     if (t + 1 < T) {
-        double eps = y[t] * exp(-0.5 * ht);
-        double d = (h[t + 1] - th.mu) - th.phi * x - th.rho * sqrt(th.sig_eta2) * eps;
+        double d = (h[t + 1] - th.mu) - th.phi * x - lev_shift(h, y, th, t);
         s += d * d / (2.0 * th.sig_eta2 * (1.0 - th.rho * th.rho));
     }
     /* stationary law of h_1: N(mu, s_eta^2 / (1 - phi^2)) */
@@ -114,22 +121,19 @@ double orc_action(const double* h, const double* y, const double* lnrv,
 /* ------------------------------------------------------------------------ */
 static double innovation(const double* h, const double* y, orc_theta th, long t)
 {
-    double eps = y[t] * exp(-0.5 * h[t]);
-    return (h[t + 1] - th.mu) - th.phi * (h[t] - th.mu) - th.rho * sqrt(th.sig_eta2) * eps;
+    return (h[t + 1] - th.mu) - th.phi * (h[t] - th.mu) - lev_shift(h, y, th, t);
 }
 
 void orc_force(const double* h, const double* y, const double* lnrv,
                long T, orc_theta th, double* F)
 {
-    const double phi = th.phi, mu = th.mu, rs = th.rho * sqrt(th.sig_eta2);
+    const double phi = th.phi, mu = th.mu;
     const double B = 1.0 / (th.sig_eta2 * (1.0 - th.rho * th.rho));
     for (long t = 0; t < T; ++t) {
         double x = h[t] - mu, ar = 0.0;
         if (t == 0) ar += (1.0 - phi * phi) * x / th.sig_eta2;
-        if (t + 1 < T) {
-            double eps = y[t] * exp(-0.5 * h[t]);
-            ar += B * innovation(h, y, th, t) * (0.5 * rs * eps - phi);
-        }
+        if (t + 1 < T)  /* d d_t / d h_t = -phi + (rho s_eta eps_t) / 2 */
+            ar += B * innovation(h, y, th, t) * (0.5 * lev_shift(h, y, th, t) - phi);
         if (t > 0) ar += B * innovation(h, y, th, t - 1);
         F[t] = 0.5 - 0.5 * y[t] * y[t] * exp(-h[t])
              - (lnrv[t] - th.xi - h[t]) / th.sig_u2 + ar;
