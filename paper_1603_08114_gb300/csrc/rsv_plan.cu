@@ -27,12 +27,15 @@ const int kJ_mixed[] = {4, 8, 12, 16, 20};
 const int kNJ_fp64 = 4, kNJ_mixed = 5;
 
 // mixed: (a, k) float2 + x0 (hi, lo) + p0 per site (+ dtau/m with a mass,
-// + the leverage v with leverage); FP64: a' (or y e^{-mu/2}), kc (+ 1/m) per site
+// + the leverage v with leverage), the start state in j rows of
+// mixed_row(nt, j) slots each; FP64:
+// a' (or y e^{-mu/2}), kc (+ 1/m) per site
 size_t smem_for(bool mixed, bool mass, bool lev, int nt, int j)
 {
-    const size_t W = (size_t)nt * (size_t)j;
-    return mixed ? (5 + (mass ? 1 : 0) + (lev ? 1 : 0)) * W * sizeof(float)
-                 : (2 + (mass ? 1 : 0)) * W * sizeof(double);
+    if (mixed)
+        return ((2 + (mass ? 1 : 0) + (lev ? 1 : 0)) * (size_t)nt + 3 * (size_t)mixed_row(nt, j)) *
+               (size_t)j * sizeof(float);
+    return (2 + (mass ? 1 : 0)) * (size_t)nt * (size_t)j * sizeof(double);
 }
 
 bool valid_j(bool mixed, int j)

@@ -235,10 +235,18 @@ __device__ void finish_split_ff(const TrajArgs& A, const View& v, float2 part, i
     __syncthreads();
     if (!last || threadIdx.x >= 32) return;
     __threadfence();
+    // lane l sums partials l, l + 32, ... in that order; the loads of eight
+    // of them are issued together (one L2 round trip, not eight)
     ff s = {0.f, 0.f};
-    for (int i = threadIdx.x; i < v.si.nseg; i += 32) {
-        const float2 w = __ldcg(pf + v.si.seg0 + i);
-        s = ff_add(s, ff{w.x, w.y});
+    for (int i0 = threadIdx.x; i0 < v.si.nseg; i0 += 32 * 8) {
+        float2 w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            w[u] = i0 + 32 * u < v.si.nseg ? __ldcg(pf + v.si.seg0 + i0 + 32 * u)
+                                           : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (i0 + 32 * u < v.si.nseg) s = ff_add(s, ff{w[u].x, w[u].y});
     }
     s = warp_sum_ff(s);
     if (threadIdx.x == 0) {
@@ -442,19 +450,27 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
 // ---------------------------------------------------------------------------
 // Mixed path: FP32 leapfrog on compensated (hi, lo) FP32 pairs for both the
 // position and the momentum (a random walk of their FP32 roundings over n_md
-// steps would otherwise dominate dH at 2^22 sites); dH from double-float
-// per-site differences, accumulated in FP64 across threads.
+// steps would otherwise dominate dH at 2^22 sites); dH as the difference of
+// the energies at both ends, each summed per thread in double-float, then
+// across warps and tiles in double-float, with one FP64 conversion for the
+// Metropolis test.
 //
 // Registers hold only the evolving state (x and p as (hi, lo), 4 J floats), so
 // that a block can run up to 32 warps; the per-site constants of the force sit
 // in shared memory and are read as float4.  Dynamic shared memory (slot-major:
-// slot j of thread tid at [j][tid]):
-//   s_ak  float4 [J/2][NT]  (a_j, k_j, a_{j+1}, k_{j+1}): a = y^2/2,
-//                           k = 1/2 - c'/s_u^2
-//   s_dm  float2 [J/2][NT]  -kick/m of the pair (with a mass only; the state
-//                           then holds the velocity v = p/m)
-//   s_x0h, s_x0l, s_p0h  float [J][NT]  start of the trajectory, for dH (p0
-//                           enters with lo = 0: drawn in FP32 or rounded from p_in)
+// slot j of thread tid at [j][tid]; pairs (p, p + P), P = J/2):
+//   s_ak  float4 [P][NT]  (-a_p, -a_{p+P}, k_p, k_{p+P}): a = y^2/2,
+//                         k = 1/2 - c'/s_u^2
+//   s_dm  float2 [P][NT]  -kick/m of the pair (with a mass only; the state
+//                         then holds the velocity v = p/m)
+//   s_v   float2 [P][NT]  the leverage weights v of the pair (leverage only)
+//   s_xh, s_xl, s_ph  float [J][NS]  x (hi, lo) and p hi at the start of the
+//                         trajectory and again at its end (p lo then over k);
+//                         rows NS = mixed_row(NT, J) slots apart
+// The arrays the leapfrog reads every step keep rows of NT slots: a warp's
+// float4 (float2) row segment is then four (two) whole 128-byte lines; the
+// rows of the start and end state, which only the load and write passes and
+// the energies touch, are padded against bank conflicts instead.
 // ---------------------------------------------------------------------------
 // (with a mass and J = 4 at most 768 threads: its load pass needs more than
 // the 64 registers a 1024-thread block leaves)
@@ -726,7 +742,8 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
     __shared__ float2 s_exptab[32];
     __shared__ MixedTheta s_mt[NWMAX];
     __shared__ float2 s_wpf[NWMAX], s_splitf;
-    const int NT = blockDim.x, W = NT * J, nw = NT >> 5, tid = threadIdx.x;
+    const int NT = blockDim.x, NS = mixed_row(NT, J), WS = NS * J, nw = NT >> 5;
+    const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     float* s_edge = reinterpret_cast<float*>(s_edge_d);
     if (tid < 32) s_exptab[tid] = g_exptab[tid];
@@ -737,9 +754,9 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
     float* s_dm1 = reinterpret_cast<float*>(s_dm);
     float2* s_v = s_dm + (MASS ? P * NT : 0);  // [P][NT] leverage v of (p, p+P)
     float* s_v1 = reinterpret_cast<float*>(s_v);
-    float* s_xh = reinterpret_cast<float*>(s_v + (LEV ? P * NT : 0));  // [J][NT]
-    float* s_xl = s_xh + W;
-    float* s_ph = s_xl + W;
+    float* s_xh = reinterpret_cast<float*>(s_v + (LEV ? P * NT : 0));  // [J][NS]
+    float* s_xl = s_xh + WS;
+    float* s_ph = s_xl + WS;
     const bool mass_on = MASS && (A.mass_on == nullptr || *A.mass_on != 0);
     const float dt = (float)A.dtau;
     // slot j is lane j / P of pair j % P
@@ -793,7 +810,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
 #pragma unroll 1
                 for (int j = 0; j < J; ++j) {
                     const int ii = base + j;
-                    s_ph[j * NT + tid] = ii < v.n ? (float)A.p_in[off + wlo + ii] : 0.0f;
+                    s_ph[j * NS + tid] = ii < v.n ? (float)A.p_in[off + wlo + ii] : 0.0f;
                 }
             } else {
 #pragma unroll 2
@@ -805,7 +822,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                     box_muller_f(u01_23(r.w[0]), u01_23(r.w[1]), z[0], z[1]);
                     box_muller_f(u01_23(r.w[2]), u01_23(r.w[3]), z[2], z[3]);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) s_ph[(4 * q + i) * NT + tid] = z[i];
+                    for (int i = 0; i < 4; ++i) s_ph[(4 * q + i) * NS + tid] = z[i];
                 }
             }
             // pass 1b: site constants, x, mass -> shared memory, and H at the
@@ -846,7 +863,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                     na_t(j, to) = na;
                     k_t(j, to) = fmaf(-mt.iu, cp.hi + cp.lo, 0.5f);
                     float kmv = -mc.kick;
-                    float p0 = s_ph[j * NT + to];
+                    float p0 = s_ph[j * NS + to];
                     if (MASS) {
                         const float mi = (act && mass_on) ? A.minv[s] : 1.0f;
                         kmv = -mc.kick * mi;
@@ -859,10 +876,10 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                                      : 0.0f;
                         else
                             p0 = p0 * sqrtf(mi);
-                        s_ph[j * NT + to] = p0;
+                        s_ph[j * NS + to] = p0;
                     }
-                    s_xh[j * NT + to] = x.hi;
-                    s_xl[j * NT + to] = x.lo;
+                    s_xh[j * NS + to] = x.hi;
+                    s_xl[j * NS + to] = x.lo;
                     // H at the start of this site if the segment owns it
                     const int64_t sg = wlo + ii;
                     if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
@@ -889,9 +906,9 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
             // registers <- shared memory, then the first half step of eq. (6)
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                X[q] = f2(s_xh[q * NT + tid], s_xh[(q + P) * NT + tid]);
-                XL[q] = f2(s_xl[q * NT + tid], s_xl[(q + P) * NT + tid]);
-                PH[q] = f2(s_ph[q * NT + tid], s_ph[(q + P) * NT + tid]);
+                X[q] = f2(s_xh[q * NS + tid], s_xh[(q + P) * NS + tid]);
+                XL[q] = f2(s_xl[q * NS + tid], s_xl[(q + P) * NS + tid]);
+                PH[q] = f2(s_ph[q * NS + tid], s_ph[(q + P) * NS + tid]);
                 PL[q] = f2(0.0f, 0.0f);
             }
             const float r0 = A.integrator == 1 ? (float)A.lambda : 0.5f;  // first drift
@@ -913,12 +930,12 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
         __syncthreads();  // every warp is done reading k and the start state
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            s_xh[q * NT + tid] = X[q].x;
-            s_xh[(q + P) * NT + tid] = X[q].y;
-            s_xl[q * NT + tid] = XL[q].x;
-            s_xl[(q + P) * NT + tid] = XL[q].y;
-            s_ph[q * NT + tid] = PH[q].x;
-            s_ph[(q + P) * NT + tid] = PH[q].y;
+            s_xh[q * NS + tid] = X[q].x;
+            s_xh[(q + P) * NS + tid] = X[q].y;
+            s_xl[q * NS + tid] = XL[q].x;
+            s_xl[(q + P) * NS + tid] = XL[q].y;
+            s_ph[q * NS + tid] = PH[q].x;
+            s_ph[(q + P) * NS + tid] = PH[q].y;
             k_at(q) = PL[q].x;
             k_at(q + P) = PL[q].y;
         }
@@ -934,8 +951,8 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
         for (int j = 0; j < J; ++j) {
             const int64_t sg = wlo + base + j;
             if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
-            const ff x = {s_xh[j * NT + tid], s_xl[j * NT + tid]};
-            const int nidx = j + 1 < J ? (j + 1) * NT + tid : tid + 1;
+            const ff x = {s_xh[j * NS + tid], s_xl[j * NS + tid]};
+            const int nidx = j + 1 < J ? (j + 1) * NS + tid : tid + 1;
             const ff xn = {s_xh[nidx], s_xl[nidx]};
             const float2 lr = A.lr_f[off + sg];
             ff cp = two_sum(lr.x, -mt.ximu.hi);
@@ -943,7 +960,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
             const ff mw = MASS ? mass_weight(mc.kick, dm_at(j)) : ff{1.f, 0.f};
             const bool has_next = sg + 1 < v.si.T;
             const float a = (LEV && has_next) ? -na_at(j) * mt.omr : -na_at(j);
-            hparts_site<LEV, MASS>(acc, x, ff{s_ph[j * NT + tid], k_at(j)}, mw, cp, a, xn, has_next,
+            hparts_site<LEV, MASS>(acc, x, ff{s_ph[j * NS + tid], k_at(j)}, mw, cp, a, xn, has_next,
                                    mt, s_exptab, LEV ? v_at(j) * mt.ibf : 0.0f);
         }
         if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
@@ -966,7 +983,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                 const int ol = k / J, j = k - ol * J;
                 const int64_t sg = wbase + k;
                 if (sg >= v.g.lo && sg < v.g.hi) {
-                    const int idx = j * NT + warp * 32 + ol;
+                    const int idx = j * NS + warp * 32 + ol;
                     ff hh = two_sum(s_xh[idx], mt.mu.hi);
                     hh.lo += s_xl[idx] + mt.mu.lo;
                     hh = fast_two_sum(hh.hi, hh.lo);
@@ -979,7 +996,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
             for (int j = 0; j < J; ++j) {
                 const int64_t sg = wlo + base + j;
                 if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi)
-                    A.p_out[off + sg] = ((double)s_ph[j * NT + tid] + (double)k_at(j)) *
+                    A.p_out[off + sg] = ((double)s_ph[j * NS + tid] + (double)k_at(j)) *
                                         (MASS ? -(double)mc.kick / (double)dm_at(j) : 1.0);
             }
         }

@@ -158,6 +158,14 @@ cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st);
 // of 2^(j/32).
 cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, double rho,
                               MixedTheta* theta_f, cudaStream_t st);
+// Row stride (in floats) of the mixed kernel's state rows [j][.]: nt threads
+// plus a pad of ceil(32 / j).  A warp files and reads its 32 j consecutive
+// sites with consecutive lanes, so one instruction touches j slots of each of
+// about 32 / j owner threads; with rows a multiple of 32 words apart those
+// all fall in the owners' few banks (j-way conflicts), with the pad the slots
+// of one owner land in different banks (2- to 3-way at most).
+__host__ __device__ constexpr int mixed_row_pad(int j) { return (32 + j - 1) / j; }
+__host__ __device__ constexpr int mixed_row(int nt, int j) { return nt + mixed_row_pad(j); }
 // Largest block (threads) of the mixed kernel with `j` sites per thread, with
 // or without a mass (0 if j is not instantiated).
 int mixed_max_threads(int j, bool mass);
