@@ -95,7 +95,7 @@ rsv_status ctx_begin(rsv_ctx* c, void* stream)
 
 rsv_status ctx_ensure_partials(rsv_ctx* c, int64_t n)
 {
-    return c->partials.ensure((size_t)n * sizeof(double));
+    return c->partials.ensure((size_t)n * kPartialWords * sizeof(double));
 }
 
 // Count a kernel launch made through launcher f.
@@ -167,6 +167,7 @@ rsv_status rsv_reserve(rsv_ctx* c, int64_t max_T, int64_t max_series)
     if ((st = c->ser_dh.ensure(n * sizeof(double))) != RSV_OK) return st;
     if ((st = c->ser_acc.ensure(n * sizeof(int))) != RSV_OK) return st;
     if ((st = c->theta_f.ensure(n * sizeof(MixedTheta))) != RSV_OK) return st;
+    if ((st = c->rstats.ensure(n * 2 * sizeof(StatsRec))) != RSV_OK) return st;
     if ((st = c->gibbs.ensure((size_t)gibbs_grid(max_T) * 8 * sizeof(double))) != RSV_OK) return st;
     return RSV_OK;
 }

@@ -92,6 +92,7 @@ rsv_status ensure_plan_ws(rsv_ctx* c, const Plan& p, bool mixed, bool need_p)
         if ((st = c->a_f.ensure(N * 4)) != RSV_OK) return st;
         if ((st = c->lr_f.ensure(N * 8)) != RSV_OK) return st;
         if ((st = c->theta_f.ensure(n * sizeof(MixedTheta))) != RSV_OK) return st;
+        if ((st = c->rstats.ensure(n * 2 * sizeof(StatsRec))) != RSV_OK) return st;
     } else {
         if ((st = c->dbuf0.ensure(N * 8)) != RSV_OK) return st;
     }
@@ -185,6 +186,18 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
         if ((e = counted(c, launch_h_to_ff, (const double*)o.h, c->fbuf0.as<float2>(), P.total,
                          s)) != cudaSuccess)
             return cuda_fail(e, "state split kernel");
+        // without leverage dH takes the start's potential energy from the
+        // statistics of the state; the kernel keeps them for both buffers
+        a.rstats = c->rstats.as<StatsRec>();
+        if (!P.lev) {
+            c->launches += 1;  // two kernels
+            if ((e = counted(c, launch_state_stats, P, (const float2*)c->fbuf0.as<float2>(),
+                             (const float*)c->a_f.as<float>(),
+                             (const float2*)c->lr_f.as<float2>(),
+                             (const MixedTheta*)c->theta_f.as<MixedTheta>(),
+                             c->partials.as<double>(), c->rstats.as<StatsRec>(), s)) != cudaSuccess)
+                return cuda_fail(e, "state statistics kernels");
+        }
     } else {
         a.h0d = o.h;
         a.h1d = c->dbuf0.as<double>();

@@ -77,13 +77,14 @@ struct rsv_ctx {
     rsv::Buf fbuf0, fbuf1;  // (hi, lo) FP32 state double buffer
     rsv::Buf a_f, lr_f;  // mixed-path per-site constants
     rsv::Buf theta_f;    // mixed-path per-series theta constants
+    rsv::Buf rstats;     // mixed-path statistics of each series' two state buffers
     rsv::Buf gibbs;     // theta-update partial sums
     rsv::Buf batch;     // batched-path scratch
     rsv::Buf extra;     // other kernels' scratch
     std::vector<rsv::Buf*> all_bufs()
     {
         return {&ints, &scalars, &partials, &dbuf0, &dbuf1, &fbuf0, &fbuf1, &a_f, &lr_f, &theta_f,
-                &gibbs, &batch, &extra, &ser_cur, &ser_cnt, &ser_dh, &ser_acc};
+                &rstats, &gibbs, &batch, &extra, &ser_cur, &ser_cnt, &ser_dh, &ser_acc};
     }
 };
 

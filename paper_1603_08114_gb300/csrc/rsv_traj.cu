@@ -150,17 +150,26 @@ __device__ __forceinline__ void load_bin(const TrajArgs& A, int b, int* s_wseg, 
 
 // Metropolis decision of one series (Sec. 3): accept iff ln u < -dH; a
 // non-finite dH rejects and raises ST_NONFINITE.
+// ln u of a drawn u is taken first in FP32 (logf of u rounded to FP32: off by
+// at most 2^-24 + a few ulp of ln u, |ln u| < 37); only when that lies within
+// 1e-6 (1 + |ln u|) of -dH, where the comparison could go either way, is it
+// taken in FP64, so the decision is the FP64 comparison's at the cost of one
+// FP64 logarithm in about a million trajectories.
 __device__ int decide(const TrajArgs& A, int series, double dH, int cur, bool flip)
 {
-    double lu;
+    const bool fin = isfinite(dH);
+    int acc;
     if (A.log_u) {
-        lu = A.log_u[series];
+        acc = (fin && A.log_u[series] < -dH) ? 1 : 0;
     } else {
         const u64x4 w = philox_block(A.seed, (uint64_t)series, A.traj, STREAM_MH, 0);
-        lu = log(u01_53(w.w[0]));
+        const double u = u01_53(w.w[0]);
+        const float lf = logf((float)u);
+        const double gap = (double)lf + dH;  // ln u - (-dH), to within the margin
+        if (!fin) acc = 0;
+        else if (fabs(gap) > 1e-6 * (1.0 + fabs((double)lf))) acc = gap < 0.0 ? 1 : 0;
+        else acc = log(u) < -dH ? 1 : 0;
     }
-    const bool fin = isfinite(dH);
-    const int acc = (fin && lu < -dH) ? 1 : 0;
     if (!fin) atomicOr(A.status, ST_NONFINITE);
     if (A.dH_out) A.dH_out[series] = dH;
     if (A.acc_out) A.acc_out[series] = acc;
@@ -673,14 +682,20 @@ __device__ __forceinline__ ff hparts_total(const HParts& a, const MixedTheta& mt
 // (weighted by B/2 in he).
 // With a mass, p is the velocity v = p/m and mw the double-float mass m, so
 // that K = m v^2 (see mass_weight).
+// K of one site: p^2, or m v^2 with a mass (p the velocity, mw the mass).
+template <bool MASS>
+__device__ __forceinline__ ff kinetic(ff p, ff mw)
+{
+    ff p2 = two_prod(p.hi, p.hi);  // (hi + lo)^2 to ~2^-48
+    p2.lo = fmaf(2.0f * p.hi, p.lo, p2.lo);
+    return MASS ? ff_mul(p2, mw) : p2;
+}
 template <bool LEV, bool MASS>
 __device__ __forceinline__ void hparts_site(HParts& acc, ff x, ff p, ff mw, ff cp, float a,
                                             ff xn, bool has_next, const MixedTheta& mt,
                                             const float2* tab, float rs_y = 0.0f)
 {
-    ff p2 = two_prod(p.hi, p.hi);  // (hi + lo)^2 to ~2^-48
-    p2.lo = fmaf(2.0f * p.hi, p.lo, p2.lo);
-    ff_acc(acc.K, MASS ? ff_mul(p2, mw) : p2);
+    ff_acc(acc.K, kinetic<MASS>(p, mw));
     ff_acc(acc.L, x);
     const ff r = ff_sub(x, cp);
     ff_acc(acc.R, ff_mul(r, r));
@@ -726,6 +741,169 @@ __device__ __forceinline__ void stationary_part(HParts& acc, ff x1, const MixedT
     ff_acc(acc.Q, ff_mul(om, ff_mul(x1, x1)));
 }
 
+// ---- statistics of a state (model without leverage; see StateStats) ----
+constexpr int kStatsFF = 7;
+__device__ __forceinline__ ff* stats_ff(StateStats& s) { return reinterpret_cast<ff*>(&s); }
+__device__ __forceinline__ void stats_zero(StateStats& s)
+{
+#pragma unroll
+    for (int i = 0; i < kStatsFF; ++i) stats_ff(s)[i] = ff{0.f, 0.f};
+}
+// One owned site: x = h - mu, xn = x_{t+1} (read only if has_next), lr =
+// lnRV, a = y^2/2 (x0 and xT are set by the caller).
+__device__ __forceinline__ void stats_site(StateStats& s, ff x, ff xn, bool has_next, ff lr,
+                                           float a, const MixedTheta& mt, const float2* tab)
+{
+    ff_acc(s.sx, x);
+    ff_acc(s.sxx, ff_mul(x, x));
+    if (has_next) ff_acc(s.sxn, ff_mul(x, xn));
+    ff_acc(s.sxl, ff_mul(x, lr));
+    const ff nh = ff_sub(ff{-mt.mu.hi, -mt.mu.lo}, x);  // -h
+    ff_acc(s.e, ff_mul_f(ff_exp(nh, tab), a));
+}
+
+// dH of a trajectory of a series of length T (model without leverage) from
+//   dk = sum m v'^2 - sum m v^2 (twice the kinetic difference),
+//   s1 = the end state's statistics, centred at the current theta mt,
+//   r0 = the start state's record, centred wherever it was taken.
+// The energy of eqs. (1)-(3) without its site-independent constants is
+//   H = K/2 + sum x / 2 + R / (2 s_u^2) + Q / (2 s_eta^2) + sum (y^2/2) e^{-h},
+//   R = sum (x - c')^2 = sxx - 2 sxl + 2 (xi + mu) sx + (terms of the data alone),
+//   Q = sum_{t<T-1} (x_{t+1} - phi x_t)^2 + (1 - phi^2) x_0^2
+//     = (1 + phi^2) sxx - phi^2 (x_0^2 + x_{T-1}^2) - 2 phi sxn;
+// the start's sums are moved to the current centre (x' = x + dmu) and the
+// differences taken before they are weighted.  Double-float throughout, one
+// FP64 conversion at the end.
+__device__ double stats_dH(ff dk, const StateStats& s1, const StatsRec& r0, const MixedTheta& mt,
+                           int64_t T)
+{
+    const StateStats& s0 = r0.s;
+    const float th = (float)T;
+    const ff Tf = {th, (float)(T - (int64_t)th)};
+    const ff T1 = ff_add(Tf, ff{-1.f, 0.f});
+    const ff dmu = ff_sub(r0.mu, mt.mu);
+    const ff dmu2 = ff_mul(dmu, dmu);
+    const ff sx0 = ff_add(s0.sx, ff_mul(Tf, dmu));
+    const ff sxx0 = ff_add(ff_add(s0.sxx, ff_mul(ff_mul_f(dmu, 2.f), s0.sx)), ff_mul(Tf, dmu2));
+    const ff sxn0 = ff_add(
+        ff_add(s0.sxn, ff_mul(dmu, ff_sub(ff_mul_f(s0.sx, 2.f), ff_add(s0.x0, s0.xT)))),
+        ff_mul(T1, dmu2));
+    const ff sxl0 = ff_add(s0.sxl, ff_mul(dmu, r0.sl));
+    const ff x00 = ff_add(s0.x0, dmu), xT0 = ff_add(s0.xT, dmu);
+    const ff dsx = ff_sub(s1.sx, sx0), dsxx = ff_sub(s1.sxx, sxx0), dsxn = ff_sub(s1.sxn, sxn0);
+    const ff dsxl = ff_sub(s1.sxl, sxl0);
+    const ff dx0 = ff_mul(ff_sub(s1.x0, x00), ff_add(s1.x0, x00));  // x_0'^2 - x_0^2
+    const ff dxT = ff_mul(ff_sub(s1.xT, xT0), ff_add(s1.xT, xT0));
+    const ff dr = ff_add(ff_sub(dsxx, ff_mul_f(dsxl, 2.f)), ff_mul(ff_mul_f(mt.ximu, 2.f), dsx));
+    const ff p2 = ff_mul(mt.phi_ff, mt.phi_ff);
+    ff dq = ff_mul(ff_add(ff{1.f, 0.f}, p2), dsxx);
+    dq = ff_sub(dq, ff_mul(p2, ff_add(dx0, dxT)));
+    dq = ff_sub(dq, ff_mul(ff_mul_f(mt.phi_ff, 2.f), dsxn));
+    ff dh = ff_mul_f(ff_add(dk, dsx), 0.5f);
+    dh = ff_add(dh, ff_mul(mt.hu, dr));
+    dh = ff_add(dh, ff_mul(mt.he, dq));
+    dh = ff_add(dh, ff_sub(s1.e, s0.e));
+    return ff_to_double(dh);
+}
+
+// The decisions with the statistics (model without leverage).  s_wrec[w]:
+// warp w's (dk, statistics of its owned sites) as kPartialWords double-floats.
+// A whole series sums its warps in warp order, decides and, on accept, files
+// its new state's statistics in place of the old; a tile of a split series
+// hands its sums to finish_split_stats in *split_rec.
+__device__ __forceinline__ void rec_from(const float2* w, ff& dk, StateStats& st)
+{
+    dk = ff{w[0].x, w[0].y};
+#pragma unroll
+    for (int i = 0; i < kStatsFF; ++i) stats_ff(st)[i] = ff{w[1 + i].x, w[1 + i].y};
+}
+__device__ __forceinline__ void segment_decisions_stats(const TrajArgs& A, const View& v,
+                                                        const float2 (*s_wrec)[kPartialWords],
+                                                        int* s_wacc, float2* split_rec,
+                                                        const MixedTheta& mt)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (v.sid < 0 || warp != v.g.warp0) return;
+    // lane i < kPartialWords sums value i over the segment's warps in warp order
+    ff di = {0.f, 0.f};
+    if (lane < kPartialWords)
+        for (int w = v.g.warp0; w < v.g.warp0 + v.g.nwarp; ++w)
+            di = ff_add(di, ff{s_wrec[w][lane].x, s_wrec[w][lane].y});
+    if (v.g.split) {
+        if (lane < kPartialWords) split_rec[lane] = make_float2(di.hi, di.lo);
+        return;
+    }
+    ff d[kPartialWords];
+#pragma unroll
+    for (int i = 0; i < kPartialWords; ++i)
+        d[i] = ff{__shfl_sync(0xffffffffu, di.hi, i), __shfl_sync(0xffffffffu, di.lo, i)};
+    if (lane == 0) {
+        StatsRec* rec = A.rstats + 2 * (int64_t)v.g.series + v.cur;
+        StatsRec r1;
+        r1.mu = mt.mu;
+        r1.ximu = mt.ximu;
+        r1.sl = rec->sl;
+#pragma unroll
+        for (int i = 0; i < kStatsFF; ++i) stats_ff(r1.s)[i] = d[1 + i];
+        const double dH = stats_dH(d[0], r1.s, *rec, mt, v.si.T);
+        const int acc = decide(A, v.g.series, dH, v.cur, false);
+        s_wacc[v.g.warp0] = acc;
+        if (acc) *rec = r1;  // the state is overwritten in place
+    }
+}
+// The last tile of a split series to arrive sums every tile's sums in tile
+// order (warp f takes value f, lane l tiles l, l + 32, ...), decides, flips
+// the series' buffer on accept and files the proposal's statistics with it.
+__device__ void finish_split_stats(const TrajArgs& A, const View& v, const float2* split_rec,
+                                   int* s_flag, float2* s_red, const MixedTheta& mt)
+{
+    float2* pf = reinterpret_cast<float2*>(A.partials);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid < kPartialWords) {
+        pf[(int64_t)v.sid * kPartialWords + tid] = split_rec[tid];
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned prev = atomicAdd(A.ser_cnt + v.g.series, 1u);
+        *s_flag = (prev == (unsigned)v.si.nseg - 1u);
+    }
+    __syncthreads();
+    if (!*s_flag) return;
+    __threadfence();
+    const int nseg = v.si.nseg;
+    for (int f = warp; f < kPartialWords; f += nw) {
+        ff sum = {0.f, 0.f};
+        for (int i0 = lane; i0 < nseg; i0 += 32 * 8) {
+            float2 w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                w[u] = i0 + 32 * u < nseg
+                           ? __ldcg(pf + (int64_t)(v.si.seg0 + i0 + 32 * u) * kPartialWords + f)
+                           : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + 32 * u < nseg) sum = ff_add(sum, ff{w[u].x, w[u].y});
+        }
+        sum = warp_sum_ff(sum);
+        if (lane == 0) s_red[f] = make_float2(sum.hi, sum.lo);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        ff dk;
+        StatsRec r1;
+        StatsRec* rec = A.rstats + 2 * (int64_t)v.g.series;
+        rec_from(s_red, dk, r1.s);
+        r1.mu = mt.mu;
+        r1.ximu = mt.ximu;
+        r1.sl = rec[v.cur].sl;
+        const double dH = stats_dH(dk, r1.s, rec[v.cur], mt, v.si.T);
+        A.ser_cnt[v.g.series] = 0u;
+        if (decide(A, v.g.series, dH, v.cur, true)) rec[v.cur ^ 1] = r1;
+        __threadfence();
+    }
+}
+
 // Per-site work outside the leapfrog goes through shared memory: each warp
 // loads its sites' inputs and writes their new state with consecutive lanes
 // (coalesced), filing each site to or from its owner thread's slots; momenta
@@ -742,6 +920,8 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
     __shared__ float2 s_exptab[32];
     __shared__ MixedTheta s_mt[NWMAX];
     __shared__ float2 s_wpf[NWMAX], s_splitf;
+    // without leverage: per-warp (dk, statistics) and a split tile's sums
+    __shared__ float2 s_wrec[LEV ? 1 : NWMAX][kPartialWords], s_splitrec[kPartialWords];
     const int NT = blockDim.x, NS = mixed_row(NT, J), WS = NS * J, nw = NT >> 5;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -880,29 +1060,35 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                     }
                     s_xh[j * NS + to] = x.hi;
                     s_xl[j * NS + to] = x.lo;
-                    // H at the start of this site if the segment owns it
+                    // H at the start of this site if the segment owns it; without
+                    // leverage only K: the potential part comes from the state's
+                    // stored statistics (stats_dH)
                     const int64_t sg = wlo + ii;
                     if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
-                        const bool has_next = sg + 1 < v.si.T;
-                        ff xn = {0.f, 0.f};
-                        if (has_next) {  // inside the window: owned sites are not its last
-                            const float2 hn = hin[s + 1];
-                            xn = two_sum(hn.x, -mt.mu.hi);
-                            xn.lo += hn.y - mt.mu.lo;
-                            xn = fast_two_sum(xn.hi, xn.lo);
-                        }
                         const ff mw = MASS ? mass_weight(mc.kick, kmv) : ff{1.f, 0.f};
-                        const float ah = (LEV && has_next) ? -na * mt.omr : -na;
-                        hparts_site<LEV, MASS>(acc, x, ff{p0, 0.f}, mw, cp, ah, xn, has_next, mt,
-                                               s_exptab, LEV ? vv * mt.ibf : 0.0f);
-                        if (sg == 0) stationary_part<LEV>(acc, x, mt);
+                        if (LEV) {
+                            const bool has_next = sg + 1 < v.si.T;
+                            ff xn = {0.f, 0.f};
+                            if (has_next) {  // inside the window: owned sites are not its last
+                                const float2 hn = hin[s + 1];
+                                xn = two_sum(hn.x, -mt.mu.hi);
+                                xn.lo += hn.y - mt.mu.lo;
+                                xn = fast_two_sum(xn.hi, xn.lo);
+                            }
+                            const float ah = has_next ? -na * mt.omr : -na;
+                            hparts_site<LEV, MASS>(acc, x, ff{p0, 0.f}, mw, cp, ah, xn, has_next,
+                                                   mt, s_exptab, vv * mt.ibf);
+                            if (sg == 0) stationary_part<LEV>(acc, x, mt);
+                        } else {
+                            ff_acc(acc.K, kinetic<MASS>(ff{p0, 0.f}, mw));
+                        }
                     }
                 }
             }
             __syncthreads();
             mc.vL = (LEV && !v.first) ? s_v1[((P - 1) * NT + tid - 1) * 2 + 1] : 0.0f;
             mc.cfirst = (LEV && v.first) ? mt.cst : 0.0f;
-            h0 = hparts_total(acc, mt);
+            h0 = LEV ? hparts_total(acc, mt) : ff_add(acc.K, ff{0.f, 0.f});
             // registers <- shared memory, then the first half step of eq. (6)
 #pragma unroll
             for (int q = 0; q < P; ++q) {
@@ -947,6 +1133,8 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
         const int64_t off = v.si.off, wlo = v.g.wlo;
         HParts acc;
         hparts_zero(acc);
+        StateStats st;
+        stats_zero(st);
 #pragma unroll 1
         for (int j = 0; j < J; ++j) {
             const int64_t sg = wlo + base + j;
@@ -955,21 +1143,47 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
             const int nidx = j + 1 < J ? (j + 1) * NS + tid : tid + 1;
             const ff xn = {s_xh[nidx], s_xl[nidx]};
             const float2 lr = A.lr_f[off + sg];
-            ff cp = two_sum(lr.x, -mt.ximu.hi);
-            cp.lo += lr.y - mt.ximu.lo;
             const ff mw = MASS ? mass_weight(mc.kick, dm_at(j)) : ff{1.f, 0.f};
             const bool has_next = sg + 1 < v.si.T;
-            const float a = (LEV && has_next) ? -na_at(j) * mt.omr : -na_at(j);
-            hparts_site<LEV, MASS>(acc, x, ff{s_ph[j * NS + tid], k_at(j)}, mw, cp, a, xn, has_next,
-                                   mt, s_exptab, LEV ? v_at(j) * mt.ibf : 0.0f);
+            const ff pv = {s_ph[j * NS + tid], k_at(j)};
+            if (LEV) {
+                ff cp = two_sum(lr.x, -mt.ximu.hi);
+                cp.lo += lr.y - mt.ximu.lo;
+                const float a = has_next ? -na_at(j) * mt.omr : -na_at(j);
+                hparts_site<LEV, MASS>(acc, x, pv, mw, cp, a, xn, has_next, mt, s_exptab,
+                                       v_at(j) * mt.ibf);
+            } else {
+                ff_acc(acc.K, kinetic<MASS>(pv, mw));
+                stats_site(st, x, xn, has_next, ff{lr.x, lr.y}, -na_at(j), mt, s_exptab);
+            }
         }
-        if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
-            stationary_part<LEV>(acc, ff{s_xh[tid], s_xl[tid]}, mt);
-        ff dh = ff_sub(hparts_total(acc, mt), h0);
-        dh = warp_sum_ff(dh);
-        if (lane == 0) s_wpf[warp] = make_float2(dh.hi, dh.lo);
+        if (!LEV && v.sid >= 0) {  // the series' first and last sites, where owned
+            const int64_t s0 = wlo + base;
+            if (s0 == 0 && v.g.lo == 0) st.x0 = ff{s_xh[tid], s_xl[tid]};
+            const int64_t jl = v.si.T - 1 - s0;
+            if (jl >= 0 && jl < J && v.si.T - 1 >= v.g.lo && v.si.T - 1 < v.g.hi)
+                st.xT = ff{s_xh[(int)jl * NS + tid], s_xl[(int)jl * NS + tid]};
+        }
+        if (LEV) {
+            if (v.sid >= 0 && wlo + base == 0 && v.g.lo == 0)
+                stationary_part<LEV>(acc, ff{s_xh[tid], s_xl[tid]}, mt);
+            ff dh = ff_sub(hparts_total(acc, mt), h0);
+            dh = warp_sum_ff(dh);
+            if (lane == 0) s_wpf[warp] = make_float2(dh.hi, dh.lo);
+        } else {
+            // (dk, statistics) of the warp's owned sites, each summed in a
+            // fixed order
+            ff r = warp_sum_ff(ff_sub(ff_add(acc.K, ff{0.f, 0.f}), h0));
+            if (lane == 0) s_wrec[warp][0] = make_float2(r.hi, r.lo);
+#pragma unroll
+            for (int i = 0; i < kStatsFF; ++i) {
+                r = warp_sum_ff(ff_add(stats_ff(st)[i], ff{0.f, 0.f}));
+                if (lane == 0) s_wrec[warp][1 + i] = make_float2(r.hi, r.lo);
+            }
+        }
         __syncthreads();
-        segment_decisions_ff(A, v, s_wpf, s_wacc, &s_splitf);
+        if (LEV) segment_decisions_ff(A, v, s_wpf, s_wacc, &s_splitf);
+        else segment_decisions_stats(A, v, s_wrec, s_wacc, s_splitrec, mt);
         __syncthreads();
         const bool write_h = v.sid >= 0 && (v.g.split || s_wacc[v.g.warp0]);
         float2* hout = v.g.split ? (v.cur ? A.h0f : A.h1f) : (v.cur ? A.h1f : A.h0f);
@@ -1000,7 +1214,10 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                                         (MASS ? -(double)mc.kick / (double)dm_at(j) : 1.0);
             }
         }
-        if (v.g.split) finish_split_ff(A, v, s_splitf, &s_flag);
+        if (v.g.split) {
+            if (LEV) finish_split_ff(A, v, s_splitf, &s_flag);
+            else finish_split_stats(A, v, s_splitrec, &s_flag, s_wrec[0], s_mt[v.g.warp0]);
+        }
     }
 }
 
@@ -1069,6 +1286,86 @@ __global__ void k_finalize(const SerInfo* __restrict__ ser, int n, int64_t total
             h[t] = h1d[t];
         }
     }
+}
+
+// The statistics (StateStats) of the state hf: one block per segment over its
+// owned sites (a thread's sites in order, then a butterfly in each warp and
+// the warps in order), written as kPartialWords double-floats per segment
+// (sum lnRV, then the statistics); then one thread per series adds its tiles
+// in tile order and files the record as buffer 0's.
+constexpr int kStatsThreads = 256;
+__global__ void __launch_bounds__(kStatsThreads) k_state_stats(
+    const Seg* __restrict__ segs, const SerInfo* __restrict__ ser, const float2* __restrict__ hf,
+    const float* __restrict__ a_f, const float2* __restrict__ lr_f,
+    const MixedTheta* __restrict__ theta_f, double* __restrict__ scratch)
+{
+    __shared__ float2 s_tab[32];
+    __shared__ float2 s_red[kStatsThreads / 32][kPartialWords];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 32) s_tab[tid] = g_exptab[tid];
+    __syncthreads();
+    const Seg g = segs[blockIdx.x];
+    const SerInfo si = ser[g.series];
+    const MixedTheta& mt = theta_f[g.series];
+    StateStats st;
+    stats_zero(st);
+    ff sl = {0.f, 0.f};
+    for (int64_t t = g.lo + tid; t < g.hi; t += kStatsThreads) {
+        const int64_t s = si.off + t;
+        const float2 hv = hf[s];
+        ff x = two_sum(hv.x, -mt.mu.hi);  // x = h - mu as the trajectory kernel forms it
+        x.lo += hv.y - mt.mu.lo;
+        x = fast_two_sum(x.hi, x.lo);
+        const bool has_next = t + 1 < si.T;
+        ff xn = {0.f, 0.f};
+        if (has_next) {
+            const float2 hn = hf[s + 1];
+            xn = two_sum(hn.x, -mt.mu.hi);
+            xn.lo += hn.y - mt.mu.lo;
+            xn = fast_two_sum(xn.hi, xn.lo);
+        }
+        const float2 lr = lr_f[s];
+        stats_site(st, x, xn, has_next, ff{lr.x, lr.y}, fabsf(a_f[s]), mt, s_tab);
+        ff_acc(sl, ff{lr.x, lr.y});
+        if (t == 0) st.x0 = x;
+        if (t + 1 == si.T) st.xT = x;
+    }
+    // slot 0: sum lnRV; slots 1..: the statistics
+#pragma unroll
+    for (int i = 0; i < kPartialWords; ++i) {
+        const ff r = warp_sum_ff(ff_add(i ? stats_ff(st)[i - 1] : sl, ff{0.f, 0.f}));
+        if (lane == 0) s_red[warp][i] = make_float2(r.hi, r.lo);
+    }
+    __syncthreads();
+    if (tid < kPartialWords) {
+        ff r = {0.f, 0.f};
+        for (int w = 0; w < kStatsThreads / 32; ++w)
+            r = ff_add(r, ff{s_red[w][tid].x, s_red[w][tid].y});
+        float2* out = reinterpret_cast<float2*>(scratch) + (int64_t)blockIdx.x * kPartialWords;
+        out[tid] = make_float2(r.hi, r.lo);
+    }
+}
+__global__ void k_stats_combine(const SerInfo* __restrict__ ser, int n,
+                                const MixedTheta* __restrict__ theta_f,
+                                const double* __restrict__ scratch, StatsRec* __restrict__ rstats)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const SerInfo si = ser[s];
+    const float2* rec = reinterpret_cast<const float2*>(scratch);
+    StatsRec r;
+    stats_zero(r.s);
+    r.sl = ff{0.f, 0.f};
+    for (int i = 0; i < si.nseg; ++i) {
+        const float2* w = rec + (int64_t)(si.seg0 + i) * kPartialWords;
+        r.sl = ff_add(r.sl, ff{w[0].x, w[0].y});
+#pragma unroll
+        for (int k = 0; k < kStatsFF; ++k)
+            stats_ff(r.s)[k] = ff_add(stats_ff(r.s)[k], ff{w[1 + k].x, w[1 + k].y});
+    }
+    r.mu = theta_f[s].mu;
+    r.ximu = theta_f[s].ximu;
+    rstats[2 * (int64_t)s] = r;
 }
 
 __global__ void k_snapshot(const SerInfo* __restrict__ ser, int n, int64_t total,
@@ -1221,6 +1518,19 @@ cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st)
 #undef RSV_CASE
 }
 
+cudaError_t launch_state_stats(const Plan& p, const float2* hf, const float* a_f,
+                               const float2* lr_f, const MixedTheta* theta_f, double* scratch,
+                               StatsRec* rstats, cudaStream_t st)
+{
+    if (p.nsegs < 1 || p.nsegs > 0x7fffffff) return cudaErrorInvalidValue;
+    k_state_stats<<<(unsigned)p.nsegs, kStatsThreads, 0, st>>>(p.d_segs, p.d_ser, hf, a_f, lr_f,
+                                                               theta_f, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_stats_combine<<<(p.nseries + 127) / 128, 128, 0, st>>>(p.d_ser, p.nseries, theta_f, scratch,
+                                                            rstats);
+    return cudaGetLastError();
+}
 cudaError_t launch_commit_fp64(double* h, const double* hprop, double* p, const double* pprop,
                                const int* acc, int64_t T, cudaStream_t st)
 {

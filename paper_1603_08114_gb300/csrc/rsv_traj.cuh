@@ -103,6 +103,32 @@ __device__ __forceinline__ MixedTheta mixed_theta(const ThetaD& th)
     return m;
 }
 
+// Statistics of a state that its energy under eqs. (1)-(3) needs (mixed path,
+// model without leverage), centred at the mu they were taken at: with
+// x = h - mu,
+//   sx = sum x,  sxx = sum x^2,  sxn = sum_{t<T-1} x_t x_{t+1},
+//   sxl = sum x lnRV,  e = sum (y^2/2) e^{-h},  x0 = x_0,  xT = x_{T-1},
+// in double-float, over the sites a tile owns (x0 and xT from the tiles that
+// own those sites, 0 in the others), so that the tiles of a series add up.
+// Only the centre depends on theta: under another mu' the sums follow in
+// closed form from x' = x + mu - mu' (with sl = sum lnRV of the series), and
+// the measurement term sum (x - c')^2, c' = lnRV - xi - mu, from sxx, sxl, sx
+// and data constants, so the energy of a stored state under a new theta needs
+// no pass over its sites.
+struct StateStats {
+    ff sx, sxx, sxn, sxl, e, x0, xT;
+};
+// The statistics of one series' state with their centre mu (and xi + mu of
+// the same theta), and sl = sum lnRV over the series.
+struct StatsRec {
+    ff mu, ximu, sl;
+    StateStats s;
+};
+// double values per segment in TrajArgs::partials: a tile of a split series
+// reports its kinetic-energy difference and its end state's statistics
+// (8 double-floats)
+constexpr int kPartialWords = 8;
+
 struct TrajArgs {
     const Seg* segs;
     const int* bin_first;
@@ -130,6 +156,9 @@ struct TrajArgs {
     const float* a_f;    // mixed path: y^2/2 with the sign of y, and lnRV as (hi, lo)
     const float2* lr_f;
     const MixedTheta* theta_f;  // mixed path: per-series constants (launch_theta_prep)
+    // mixed path without leverage: [nseries][2] statistics of the state in
+    // each buffer (the one ser_cur selects must hold the current state's)
+    StatsRec* rstats;
     double rho;          // leverage corr(eps_t, eta_t) of every series (0: eqs. (1)-(3))
     const float* minv;   // optional inverse mass (FP32, packed)
     const int* mass_on;  // optional flag; 0 = use m = 1
@@ -171,6 +200,12 @@ __host__ __device__ constexpr int mixed_row(int nt, int j) { return nt + mixed_r
 int mixed_max_threads(int j, bool mass);
 // Resident blocks per SM of a trajectory kernel configuration (0 if invalid).
 int blocks_per_sm(bool mixed, bool mass, bool lev, int j, int nt, size_t smem);
+
+// rstats[s][0] = the statistics of series s in the (hi, lo) state hf, for
+// every series of a mixed plan (scratch: kPartialWords doubles per segment).
+cudaError_t launch_state_stats(const Plan& p, const float2* hf, const float* a_f,
+                               const float2* lr_f, const MixedTheta* theta_f, double* scratch,
+                               StatsRec* rstats, cudaStream_t st);
 
 cudaError_t launch_commit_fp64(double* h, const double* hprop, double* p, const double* pprop,
                                const int* acc, int64_t T, cudaStream_t st);
