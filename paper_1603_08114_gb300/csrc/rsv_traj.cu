@@ -1291,9 +1291,9 @@ __global__ void k_finalize(const SerInfo* __restrict__ ser, int n, int64_t total
 // The statistics (StateStats) of the state hf: one block per segment over its
 // owned sites (a thread's sites in order, then a butterfly in each warp and
 // the warps in order), written as kPartialWords double-floats per segment
-// (sum lnRV, then the statistics); then one thread per series adds its tiles
-// in tile order and files the record as buffer 0's.
-constexpr int kStatsThreads = 256;
+// (sum lnRV, then the statistics); then one warp per series adds its tiles
+// and files the record as buffer 0's.
+constexpr int kStatsThreads = 512;
 __global__ void __launch_bounds__(kStatsThreads) k_state_stats(
     const Seg* __restrict__ segs, const SerInfo* __restrict__ ser, const float2* __restrict__ hf,
     const float* __restrict__ a_f, const float2* __restrict__ lr_f,
@@ -1349,23 +1349,35 @@ __global__ void k_stats_combine(const SerInfo* __restrict__ ser, int n,
                                 const MixedTheta* __restrict__ theta_f,
                                 const double* __restrict__ scratch, StatsRec* __restrict__ rstats)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per series: lane l adds tiles l, l + 32, ... in order, then a
+    // butterfly per value
+    const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (s >= n) return;
     const SerInfo si = ser[s];
     const float2* rec = reinterpret_cast<const float2*>(scratch);
-    StatsRec r;
-    stats_zero(r.s);
-    r.sl = ff{0.f, 0.f};
-    for (int i = 0; i < si.nseg; ++i) {
-        const float2* w = rec + (int64_t)(si.seg0 + i) * kPartialWords;
-        r.sl = ff_add(r.sl, ff{w[0].x, w[0].y});
+    ff acc[kPartialWords];
 #pragma unroll
-        for (int k = 0; k < kStatsFF; ++k)
-            stats_ff(r.s)[k] = ff_add(stats_ff(r.s)[k], ff{w[1 + k].x, w[1 + k].y});
+    for (int k = 0; k < kPartialWords; ++k) acc[k] = ff{0.f, 0.f};
+    for (int i = lane; i < si.nseg; i += 32) {
+        const float2* w = rec + (int64_t)(si.seg0 + i) * kPartialWords;
+        float2 v[kPartialWords];
+#pragma unroll
+        for (int k = 0; k < kPartialWords; ++k) v[k] = w[k];
+#pragma unroll
+        for (int k = 0; k < kPartialWords; ++k) acc[k] = ff_add(acc[k], ff{v[k].x, v[k].y});
     }
-    r.mu = theta_f[s].mu;
-    r.ximu = theta_f[s].ximu;
-    rstats[2 * (int64_t)s] = r;
+#pragma unroll
+    for (int k = 0; k < kPartialWords; ++k) acc[k] = warp_sum_ff(acc[k]);
+    if (lane == 0) {
+        StatsRec r;
+        r.sl = acc[0];
+#pragma unroll
+        for (int k = 0; k < kStatsFF; ++k) stats_ff(r.s)[k] = acc[1 + k];
+        r.mu = theta_f[s].mu;
+        r.ximu = theta_f[s].ximu;
+        rstats[2 * (int64_t)s] = r;
+    }
 }
 
 __global__ void k_snapshot(const SerInfo* __restrict__ ser, int n, int64_t total,
@@ -1527,8 +1539,8 @@ cudaError_t launch_state_stats(const Plan& p, const float2* hf, const float* a_f
                                                                theta_f, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_stats_combine<<<(p.nseries + 127) / 128, 128, 0, st>>>(p.d_ser, p.nseries, theta_f, scratch,
-                                                            rstats);
+    k_stats_combine<<<(p.nseries + 7) / 8, 256, 0, st>>>(p.d_ser, p.nseries, theta_f, scratch,
+                                                        rstats);
     return cudaGetLastError();
 }
 cudaError_t launch_commit_fp64(double* h, const double* hprop, double* p, const double* pprop,
