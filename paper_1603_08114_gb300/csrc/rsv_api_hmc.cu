@@ -202,10 +202,15 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
         a.h0d = o.h;
         a.h1d = c->dbuf0.as<double>();
     }
+    // mixed path: a snapshot that is due is written by the next trajectory's
+    // load pass (its start state is that state), the last one by its own kernel
+    float* pending_snap = nullptr;
     for (int64_t i = 0; i < o.n_traj; ++i) {
         a.traj = o.traj0 + (uint64_t)i;
         a.dH_out = o.dH_out ? o.dH_out + i * (int64_t)n : c->ser_dh.as<double>();
         a.acc_out = o.acc_out ? o.acc_out + i * (int64_t)n : c->ser_acc.as<int>();
+        a.snap_prev = pending_snap;
+        pending_snap = nullptr;
         if ((e = timed_traj(c, a, P, s)) != cudaSuccess) return cuda_fail(e, "trajectory kernel");
         const bool snap_due = o.snaps && (i + 1) % o.thin == 0;
         float* snap_dst = snap_due ? o.snaps + (size_t)((i + 1) / o.thin - 1) * N : nullptr;
@@ -230,10 +235,13 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
             g.partials = c->gibbs.as<double>();
             g.counter = reinterpret_cast<unsigned*>(ints + kGibbsCounter);
             g.theta_f = mixed ? c->theta_f.as<MixedTheta>() : nullptr;
-            // the mixed sweep reads every site of the new state: it writes this
-            // trajectory's snapshot on the way (single series: the packed state
-            // is the series)
-            if (mixed && snap_due && P.nseries == 1) {
+            // mixed, no leverage: the sweep's sums come from the state's
+            // statistics, which the trajectory kernel keeps
+            g.rstats = (mixed && !P.lev) ? c->rstats.as<StatsRec>() : nullptr;
+            // otherwise the mixed sweep reads every site of the new state: it
+            // writes this trajectory's snapshot on the way (single series: the
+            // packed state is the series)
+            if (mixed && !g.rstats && snap_due && P.nseries == 1) {
                 g.snap_out = snap_dst;
                 snap_done = true;
             }
@@ -243,6 +251,10 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
             if ((e = cudaMemcpyAsync(o.theta_out + 5 * i, o.theta, 5 * sizeof(double),
                                      cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
                 return cuda_fail(e, "theta record");
+        }
+        if (snap_due && !snap_done && mixed && i + 1 < o.n_traj) {
+            pending_snap = snap_dst;
+            snap_done = true;
         }
         if (snap_due && !snap_done) {
             if ((e = counted(c, launch_snapshot, P, (const int*)a.ser_cur, (const double*)a.h0d,

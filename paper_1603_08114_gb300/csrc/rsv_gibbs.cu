@@ -329,34 +329,6 @@ __device__ void gibbs_draws_f(const float (&S)[NSTAT], float x0, int64_t T, floa
     *acc_out = acc;
 }
 
-// MixedTheta of an FP32-valued theta in FP32 / double-float arithmetic.
-__device__ MixedTheta mixed_theta_f(const float (&t)[5])
-{
-    const float phi = t[0], mu = t[1], xi = t[2], se2 = t[3], su2 = t[4];
-    MixedTheta m;
-    m.phi = phi;
-    m.iu = 1.0f / su2;
-    m.ie = 1.0f / se2;
-    m.c0 = m.iu + (1.0f + phi * phi) * m.ie;
-    m.c1 = -phi * m.ie;
-    m.cmu = -mu * 1.4426950408889634f;
-    m.mu = ff{mu, 0.0f};
-    m.ximu = two_sum(xi, mu);
-    m.phi_ff = ff{phi, 0.0f};
-    // 1/(2 s^2) in double-float: quotient and its exact FMA residual
-    const float hu = 0.5f / su2, he = 0.5f / se2;
-    m.hu = ff{hu, fmaf(-hu, su2, 0.5f) / su2};
-    m.he = ff{he, fmaf(-he, se2, 0.5f) / se2};
-    // the leverage constants at rho = 0 (the theta update is for eqs. (1)-(3))
-    m.cst = 0.0f;
-    m.ia = 1.0f;
-    m.omr = 1.0f;
-    m.rsb = 0.0f;
-    m.ibf = se2;
-    m.st = ff_sub(ff{1.0f, 0.0f}, two_prod(phi, phi));
-    for (int i = 0; i < 9; ++i) m.pad[i] = 0.f;
-    return m;
-}
 
 // Per-site contributions, FP64 state.
 __device__ __forceinline__ void site_stats_d(const double* h, const double* lnrv, int64_t t,
@@ -547,6 +519,44 @@ __global__ void __launch_bounds__(256) k_gibbs(GibbsArgs A)
     __threadfence();
 }
 
+// theta rounded to FP32 (exact after the first mixed sweep): one conversion
+// per lane, then shared across the warp.
+__device__ __forceinline__ void theta_f32(const GibbsArgs& A, float (&th)[5])
+{
+    const int lane = threadIdx.x & 31;
+    const float mine = lane < 5 ? (float)A.theta[lane] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) th[k] = __shfl_sync(0xffffffffu, mine, k);
+}
+
+// The FP32 sweep by one warp from the statistics tot (centred at th) and
+// x0 = h_1 - mu; writes theta, its record and constants.
+__device__ void sweep_f(const GibbsArgs& A, const float (&tot)[NSTAT], float x0, float (&th)[5])
+{
+    const int lane = threadIdx.x & 31;
+    WarpDrawsF st;
+    st.seed = A.seed;
+    st.series = A.series;
+    st.traj = A.traj;
+    st.fill(A.T);
+    int acc = 0;
+    gibbs_draws_f(tot, x0, A.T, th, st, A.mask, &acc);
+    if (lane < 5) {
+        float v = th[0];
+#pragma unroll
+        for (int k = 1; k < 5; ++k)
+            if (lane == k) v = th[k];
+        A.theta[lane] = (double)v;
+        if (A.theta_out) A.theta_out[lane] = (double)v;
+    }
+    if (lane == 0) {
+        if (A.phi_acc) *A.phi_acc = acc;
+        *A.theta_f = mixed_theta_f(th);
+        if (A.counter) *A.counter = 0u;
+    }
+    __threadfence();
+}
+
 // Mixed path: the statistics in double-float (FP32 arithmetic; the FP64 pipe
 // of this GPU is slow) from (hi, lo) state, centred on the constants of
 // theta_f; the last block combines them, one warp per statistic, and warp 0
@@ -636,35 +646,62 @@ __global__ void __launch_bounds__(kGibbsMixedBlock, 2) k_gibbs_mixed(GibbsArgs A
     if (warp != 0) return;
     float tot[NSTAT];
     for (int i = 0; i < NSTAT; ++i) tot[i] = s_tot[i].x + s_tot[i].y;
-    // theta rounded to FP32 (exact after the first sweep): one conversion per
-    // lane, then shared across the warp
-    const float mine = lane < 5 ? (float)A.theta[lane] : 0.0f;
     float th[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) th[k] = __shfl_sync(0xffffffffu, mine, k);
+    theta_f32(A, th);
     const float2 hv = h[0];
     const ff x0 = ff_sub(ff{hv.x, hv.y}, mu);
-    WarpDrawsF st;
-    st.seed = A.seed;
-    st.series = A.series;
-    st.traj = A.traj;
-    st.fill(A.T);
-    int acc = 0;
-    gibbs_draws_f(tot, x0.hi + x0.lo, A.T, th, st, A.mask, &acc);
-    if (lane < 5) {
-        float v = th[0];
+    sweep_f(A, tot, x0.hi + x0.lo, th);
+}
+
+// The same sweep with its sums from the statistics of the current state (no
+// pass over the sites): one warp.  The record's sums, centred at its mu_r,
+// are moved to the sweep's FP32 theta (x = h - mu, q = lnRV - xi - h,
+// e = x_{t+1} - phi x_t) in double-float:
+//   x' = x_r + d (d = mu_r - mu):  Sx = sx + T d,  Sxx = sxx + 2 d sx + T d^2,
+//     Sxn = sxn + d (2 sx - x_0 - x_{T-1}) + (T-1) d^2,  Sxl = sxl + d sl;
+//   with c = xi + mu:  sum q = sl - T c - Sx,
+//     sum q^2 = Sxx - 2 Sxl + 2 c Sx + sll - 2 c sl + T c^2;
+//   X_a = Sx - x_{T-1},  X_b = Sx - x_0,  XX_m = Sxx - x_0^2 - x_{T-1}^2 (T > 1),
+//   XY = Sxn,  sum e = X_b - phi X_a,
+//   sum e^2 = (Sxx - x_0^2) - 2 phi Sxn + phi^2 (Sxx - x_{T-1}^2).
+__global__ void __launch_bounds__(32) k_gibbs_stats(GibbsArgs A)
+{
+    const int cur = A.cur ? *(volatile int*)A.cur : 0;
+    const StatsRec r = A.rstats[cur];
+    float th[5];
+    theta_f32(A, th);
+    const int64_t T = A.T;
+    const float thf = (float)T;
+    const ff Tf = {thf, (float)(T - (int64_t)thf)};
+    const ff T1 = ff_add(Tf, ff{-1.f, 0.f});
+    const StateStats& s = r.s;
+    const ff d = ff_sub(r.mu, ff{th[1], 0.f});
+    const ff d2 = ff_mul(d, d);
+    const ff Sx = ff_add(s.sx, ff_mul(Tf, d));
+    const ff Sxx = ff_add(ff_add(s.sxx, ff_mul(ff_mul_f(d, 2.f), s.sx)), ff_mul(Tf, d2));
+    const ff Sxn = ff_add(ff_add(s.sxn, ff_mul(d, ff_sub(ff_mul_f(s.sx, 2.f), ff_add(s.x0, s.xT)))),
+                          ff_mul(T1, d2));
+    const ff Sxl = ff_add(s.sxl, ff_mul(d, r.sl));
+    const ff x0 = ff_add(s.x0, d), xT = ff_add(s.xT, d);
+    const ff c = two_sum(th[2], th[1]);
+    const ff x0s = ff_mul(x0, x0), xTs = ff_mul(xT, xT);
+    const ff phi = {th[0], 0.f};
+    ff S[NSTAT];
+    S[0] = ff_sub(ff_sub(r.sl, ff_mul(Tf, c)), Sx);
+    S[1] = ff_add(ff_sub(Sxx, ff_mul_f(Sxl, 2.f)), ff_mul(ff_mul_f(c, 2.f), Sx));
+    S[1] = ff_add(S[1], ff_sub(r.sll, ff_mul(ff_mul_f(c, 2.f), r.sl)));
+    S[1] = ff_add(S[1], ff_mul(Tf, ff_mul(c, c)));
+    S[2] = ff_sub(Sx, xT);
+    S[3] = ff_sub(Sx, x0);
+    S[4] = T > 1 ? ff_sub(ff_sub(Sxx, x0s), xTs) : ff{0.f, 0.f};
+    S[5] = Sxn;
+    S[6] = ff_sub(S[3], ff_mul(phi, S[2]));
+    S[7] = ff_add(ff_sub(ff_sub(Sxx, x0s), ff_mul(ff_mul_f(phi, 2.f), Sxn)),
+                  ff_mul(ff_mul(phi, phi), ff_sub(Sxx, xTs)));
+    float tot[NSTAT];
 #pragma unroll
-        for (int k = 1; k < 5; ++k)
-            if (lane == k) v = th[k];
-        A.theta[lane] = (double)v;
-        if (A.theta_out) A.theta_out[lane] = (double)v;
-    }
-    if (lane == 0) {
-        if (A.phi_acc) *A.phi_acc = acc;
-        *A.theta_f = mixed_theta_f(th);
-        *A.counter = 0u;
-    }
-    __threadfence();
+    for (int i = 0; i < NSTAT; ++i) tot[i] = S[i].hi + S[i].lo;
+    sweep_f(A, tot, x0.hi + x0.lo, th);
 }
 
 }  // namespace
@@ -688,7 +725,8 @@ static int gibbs_grid_mixed(int64_t T)
 
 cudaError_t launch_gibbs(const GibbsArgs& a, bool mixed, cudaStream_t st)
 {
-    if (mixed) k_gibbs_mixed<<<gibbs_grid_mixed(a.T), kGibbsMixedBlock, 0, st>>>(a);
+    if (mixed && a.rstats) k_gibbs_stats<<<1, 32, 0, st>>>(a);
+    else if (mixed) k_gibbs_mixed<<<gibbs_grid_mixed(a.T), kGibbsMixedBlock, 0, st>>>(a);
     else k_gibbs<<<gibbs_grid(a.T), 256, 0, st>>>(a);
     return cudaGetLastError();
 }

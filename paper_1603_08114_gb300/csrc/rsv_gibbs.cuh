@@ -26,6 +26,10 @@ struct GibbsArgs {
     int* phi_acc;        // optional
     MixedTheta* theta_f; // mixed path: the current theta's constants, read and refreshed
     float* snap_out;     // mixed path, optional: h (FP32) of the state the sweep reads
+    // mixed path, optional: [2] statistics of the state in each buffer (see
+    // StateStats); when set the sweep takes its sums from the current
+    // buffer's record and reads no site (snap_out is then not written)
+    const StatsRec* rstats;
 };
 
 int gibbs_grid(int64_t T);

@@ -807,7 +807,7 @@ __device__ double stats_dH(ff dk, const StateStats& s1, const StatsRec& r0, cons
 }
 
 // The decisions with the statistics (model without leverage).  s_wrec[w]:
-// warp w's (dk, statistics of its owned sites) as kPartialWords double-floats.
+// warp w's (dk, statistics of its owned sites) as kRecWords double-floats.
 // A whole series sums its warps in warp order, decides and, on accept, files
 // its new state's statistics in place of the old; a tile of a split series
 // hands its sums to finish_split_stats in *split_rec.
@@ -818,24 +818,24 @@ __device__ __forceinline__ void rec_from(const float2* w, ff& dk, StateStats& st
     for (int i = 0; i < kStatsFF; ++i) stats_ff(st)[i] = ff{w[1 + i].x, w[1 + i].y};
 }
 __device__ __forceinline__ void segment_decisions_stats(const TrajArgs& A, const View& v,
-                                                        const float2 (*s_wrec)[kPartialWords],
+                                                        const float2 (*s_wrec)[kRecWords],
                                                         int* s_wacc, float2* split_rec,
                                                         const MixedTheta& mt)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (v.sid < 0 || warp != v.g.warp0) return;
-    // lane i < kPartialWords sums value i over the segment's warps in warp order
+    // lane i < kRecWords sums value i over the segment's warps in warp order
     ff di = {0.f, 0.f};
-    if (lane < kPartialWords)
+    if (lane < kRecWords)
         for (int w = v.g.warp0; w < v.g.warp0 + v.g.nwarp; ++w)
             di = ff_add(di, ff{s_wrec[w][lane].x, s_wrec[w][lane].y});
     if (v.g.split) {
-        if (lane < kPartialWords) split_rec[lane] = make_float2(di.hi, di.lo);
+        if (lane < kRecWords) split_rec[lane] = make_float2(di.hi, di.lo);
         return;
     }
-    ff d[kPartialWords];
+    ff d[kRecWords];
 #pragma unroll
-    for (int i = 0; i < kPartialWords; ++i)
+    for (int i = 0; i < kRecWords; ++i)
         d[i] = ff{__shfl_sync(0xffffffffu, di.hi, i), __shfl_sync(0xffffffffu, di.lo, i)};
     if (lane == 0) {
         StatsRec* rec = A.rstats + 2 * (int64_t)v.g.series + v.cur;
@@ -843,6 +843,7 @@ __device__ __forceinline__ void segment_decisions_stats(const TrajArgs& A, const
         r1.mu = mt.mu;
         r1.ximu = mt.ximu;
         r1.sl = rec->sl;
+        r1.sll = rec->sll;
 #pragma unroll
         for (int i = 0; i < kStatsFF; ++i) stats_ff(r1.s)[i] = d[1 + i];
         const double dH = stats_dH(d[0], r1.s, *rec, mt, v.si.T);
@@ -859,7 +860,7 @@ __device__ void finish_split_stats(const TrajArgs& A, const View& v, const float
 {
     float2* pf = reinterpret_cast<float2*>(A.partials);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    if (tid < kPartialWords) {
+    if (tid < kRecWords) {
         pf[(int64_t)v.sid * kPartialWords + tid] = split_rec[tid];
         __threadfence();
     }
@@ -872,7 +873,7 @@ __device__ void finish_split_stats(const TrajArgs& A, const View& v, const float
     if (!*s_flag) return;
     __threadfence();
     const int nseg = v.si.nseg;
-    for (int f = warp; f < kPartialWords; f += nw) {
+    for (int f = warp; f < kRecWords; f += nw) {
         ff sum = {0.f, 0.f};
         for (int i0 = lane; i0 < nseg; i0 += 32 * 8) {
             float2 w[8];
@@ -897,6 +898,7 @@ __device__ void finish_split_stats(const TrajArgs& A, const View& v, const float
         r1.mu = mt.mu;
         r1.ximu = mt.ximu;
         r1.sl = rec[v.cur].sl;
+        r1.sll = rec[v.cur].sll;
         const double dH = stats_dH(dk, r1.s, rec[v.cur], mt, v.si.T);
         A.ser_cnt[v.g.series] = 0u;
         if (decide(A, v.g.series, dH, v.cur, true)) rec[v.cur ^ 1] = r1;
@@ -921,7 +923,7 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
     __shared__ MixedTheta s_mt[NWMAX];
     __shared__ float2 s_wpf[NWMAX], s_splitf;
     // without leverage: per-warp (dk, statistics) and a split tile's sums
-    __shared__ float2 s_wrec[LEV ? 1 : NWMAX][kPartialWords], s_splitrec[kPartialWords];
+    __shared__ float2 s_wrec[LEV ? 1 : NWMAX][kRecWords], s_splitrec[kRecWords];
     const int NT = blockDim.x, NS = mixed_row(NT, J), WS = NS * J, nw = NT >> 5;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -1060,11 +1062,13 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                     }
                     s_xh[j * NS + to] = x.hi;
                     s_xl[j * NS + to] = x.lo;
+                    const int64_t sg = wlo + ii;
+                    const bool own = v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi;
+                    if (A.snap_prev && own) A.snap_prev[s] = hv.x + hv.y;
                     // H at the start of this site if the segment owns it; without
                     // leverage only K: the potential part comes from the state's
                     // stored statistics (stats_dH)
-                    const int64_t sg = wlo + ii;
-                    if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
+                    if (own) {
                         const ff mw = MASS ? mass_weight(mc.kick, kmv) : ff{1.f, 0.f};
                         if (LEV) {
                             const bool has_next = sg + 1 < v.si.T;
@@ -1291,8 +1295,8 @@ __global__ void k_finalize(const SerInfo* __restrict__ ser, int n, int64_t total
 // The statistics (StateStats) of the state hf: one block per segment over its
 // owned sites (a thread's sites in order, then a butterfly in each warp and
 // the warps in order), written as kPartialWords double-floats per segment
-// (sum lnRV, then the statistics); then one warp per series adds its tiles
-// and files the record as buffer 0's.
+// (sum lnRV, the statistics, sum lnRV^2); then one warp per series adds its
+// tiles and files the record as buffer 0's.
 constexpr int kStatsThreads = 512;
 __global__ void __launch_bounds__(kStatsThreads) k_state_stats(
     const Seg* __restrict__ segs, const SerInfo* __restrict__ ser, const float2* __restrict__ hf,
@@ -1309,7 +1313,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_state_stats(
     const MixedTheta& mt = theta_f[g.series];
     StateStats st;
     stats_zero(st);
-    ff sl = {0.f, 0.f};
+    ff sl = {0.f, 0.f}, sll = {0.f, 0.f};
     for (int64_t t = g.lo + tid; t < g.hi; t += kStatsThreads) {
         const int64_t s = si.off + t;
         const float2 hv = hf[s];
@@ -1327,13 +1331,15 @@ __global__ void __launch_bounds__(kStatsThreads) k_state_stats(
         const float2 lr = lr_f[s];
         stats_site(st, x, xn, has_next, ff{lr.x, lr.y}, fabsf(a_f[s]), mt, s_tab);
         ff_acc(sl, ff{lr.x, lr.y});
+        ff_acc(sll, ff_mul(ff{lr.x, lr.y}, ff{lr.x, lr.y}));
         if (t == 0) st.x0 = x;
         if (t + 1 == si.T) st.xT = x;
     }
-    // slot 0: sum lnRV; slots 1..: the statistics
+    // slot 0: sum lnRV; slots 1..7: the statistics; slot 8: sum lnRV^2
 #pragma unroll
     for (int i = 0; i < kPartialWords; ++i) {
-        const ff r = warp_sum_ff(ff_add(i ? stats_ff(st)[i - 1] : sl, ff{0.f, 0.f}));
+        const ff v = i == 0 ? sl : i <= kStatsFF ? stats_ff(st)[i - 1] : sll;
+        const ff r = warp_sum_ff(ff_add(v, ff{0.f, 0.f}));
         if (lane == 0) s_red[warp][i] = make_float2(r.hi, r.lo);
     }
     __syncthreads();
@@ -1372,6 +1378,7 @@ __global__ void k_stats_combine(const SerInfo* __restrict__ ser, int n,
     if (lane == 0) {
         StatsRec r;
         r.sl = acc[0];
+        r.sll = acc[1 + kStatsFF];
 #pragma unroll
         for (int k = 0; k < kStatsFF; ++k) stats_ff(r.s)[k] = acc[1 + k];
         r.mu = theta_f[s].mu;
@@ -1438,7 +1445,14 @@ __global__ void k_theta_prep(const double* __restrict__ theta, ThetaD th_inline,
     if (i < n) {
         ThetaD th = theta ? load_theta(theta + 5 * (int64_t)i) : th_inline;
         th.rho = rho;
-        out[i] = mixed_theta(th);
+        // an FP32-valued theta (as the mixed theta update leaves it) gets the
+        // update's own FP32 constants
+        const float tf[5] = {(float)th.phi, (float)th.mu, (float)th.xi, (float)th.se2,
+                             (float)th.su2};
+        const bool f32 = rho == 0.0 && (double)tf[0] == th.phi && (double)tf[1] == th.mu &&
+                         (double)tf[2] == th.xi && (double)tf[3] == th.se2 &&
+                         (double)tf[4] == th.su2;
+        out[i] = f32 ? mixed_theta_f(tf) : mixed_theta(th);
     }
 }
 

@@ -103,6 +103,38 @@ __device__ __forceinline__ MixedTheta mixed_theta(const ThetaD& th)
     return m;
 }
 
+// MixedTheta of an FP32-valued theta (rho = 0) in FP32 / double-float
+// arithmetic: the constants the mixed theta update derives from the theta it
+// draws, and the theta prep kernel from a theta whose components are all
+// FP32 values, so that the same theta gives the same constants either way.
+__device__ __forceinline__ MixedTheta mixed_theta_f(const float (&t)[5])
+{
+    const float phi = t[0], mu = t[1], xi = t[2], se2 = t[3], su2 = t[4];
+    MixedTheta m;
+    m.phi = phi;
+    m.iu = 1.0f / su2;
+    m.ie = 1.0f / se2;
+    m.c0 = m.iu + (1.0f + phi * phi) * m.ie;
+    m.c1 = -phi * m.ie;
+    m.cmu = -mu * 1.4426950408889634f;
+    m.mu = ff{mu, 0.0f};
+    m.ximu = two_sum(xi, mu);
+    m.phi_ff = ff{phi, 0.0f};
+    // 1/(2 s^2) in double-float: quotient and its exact FMA residual
+    const float hu = 0.5f / su2, he = 0.5f / se2;
+    m.hu = ff{hu, fmaf(-hu, su2, 0.5f) / su2};
+    m.he = ff{he, fmaf(-he, se2, 0.5f) / se2};
+    // the leverage constants at rho = 0 (the theta update is for eqs. (1)-(3))
+    m.cst = 0.0f;
+    m.ia = 1.0f;
+    m.omr = 1.0f;
+    m.rsb = 0.0f;
+    m.ibf = se2;
+    m.st = ff_sub(ff{1.0f, 0.0f}, two_prod(phi, phi));
+    for (int i = 0; i < 9; ++i) m.pad[i] = 0.f;
+    return m;
+}
+
 // Statistics of a state that its energy under eqs. (1)-(3) needs (mixed path,
 // model without leverage), centred at the mu they were taken at: with
 // x = h - mu,
@@ -119,15 +151,18 @@ struct StateStats {
     ff sx, sxx, sxn, sxl, e, x0, xT;
 };
 // The statistics of one series' state with their centre mu (and xi + mu of
-// the same theta), and sl = sum lnRV over the series.
+// the same theta), and the data sums sl = sum lnRV, sll = sum lnRV^2 over the
+// series (which the theta update needs).
 struct StatsRec {
-    ff mu, ximu, sl;
+    ff mu, ximu, sl, sll;
     StateStats s;
 };
-// double values per segment in TrajArgs::partials: a tile of a split series
-// reports its kinetic-energy difference and its end state's statistics
-// (8 double-floats)
-constexpr int kPartialWords = 8;
+// double-float values per segment in TrajArgs::partials: a tile of a split
+// series reports its kinetic-energy difference and its end state's
+// statistics (kRecWords); the statistics kernel writes sl, the statistics and
+// sll (kPartialWords)
+constexpr int kRecWords = 8;
+constexpr int kPartialWords = 9;
 
 struct TrajArgs {
     const Seg* segs;
@@ -159,6 +194,10 @@ struct TrajArgs {
     // mixed path without leverage: [nseries][2] statistics of the state in
     // each buffer (the one ser_cur selects must hold the current state's)
     StatsRec* rstats;
+    // mixed path, optional: the state the trajectory starts from as FP32
+    // (h hi + lo), written for the owned sites on the way in (the snapshot of
+    // the previous trajectory)
+    float* snap_prev;
     double rho;          // leverage corr(eps_t, eta_t) of every series (0: eqs. (1)-(3))
     const float* minv;   // optional inverse mass (FP32, packed)
     const int* mass_on;  // optional flag; 0 = use m = 1
