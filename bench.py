@@ -57,7 +57,7 @@ OPS_PER_SITE_STEP_MIXED = 13
 # the headline workload (learned mass, T = 2^20), from the capture summarised in
 # profiles/k_traj_mixed_T2p20.md (the inputs are read once per launch, so the
 # figure does not depend on n_md); valid for the kernel revision it was taken on.
-TRAFFIC = {"kernel_rev": 9, "bytes": 25265408}
+TRAFFIC = {"kernel_rev": 10, "bytes": 25271040}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 

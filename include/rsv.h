@@ -61,8 +61,12 @@ typedef enum rsv_status {
 
 /* RSV_FP64: every step in FP64.
  * RSV_MIXED: leapfrog force and updates in FP32 on a compensated (hi, lo)
- * FP32 state; dH from per-site differences in double-float, accumulated in
- * FP64; Metropolis test in FP64. */
+ * FP32 state; dH in double-float: the kinetic energy at both ends per site
+ * and, without leverage, the potential energy from double-float sums of the
+ * state kept per series and buffer (with leverage, per site at both ends);
+ * the Metropolis comparison decides as in FP64.  The theta-derived constants
+ * are prepared in FP64, or in FP32 when every component of theta is an FP32
+ * value (as the mixed theta update leaves it). */
 typedef enum rsv_precision { RSV_FP64 = 0, RSV_MIXED = 1 } rsv_precision;
 
 typedef struct rsv_ctx rsv_ctx;
@@ -263,9 +267,11 @@ rsv_status rsv_hmc_batched(rsv_ctx* ctx, rsv_plan* plan, double* h, double* p, c
  *  h [T] FP64, lnrv [T] FP64, theta device FP64 [5] in/out.
  *  mask: bit 0 xi, 1 s_u^2, 2 mu, 3 s_eta^2, 4 phi (31 = all).
  *  prec: RSV_FP64 -- statistics and draws in FP64 (53-bit uniforms);
- *        RSV_MIXED -- the sweep the mixed chain runs: h and lnRV as (hi, lo)
- *        FP32 pairs, statistics in double-float, the draws in FP32 from 23-bit
- *        uniforms of the same stream positions; theta comes out FP32-valued.
+ *        RSV_MIXED -- h and lnRV as (hi, lo) FP32 pairs, statistics in
+ *        double-float, the draws in FP32 from 23-bit uniforms of the same
+ *        stream positions (the mixed chain draws the same way, its sums taken
+ *        from the statistics of the state it keeps); theta comes out
+ *        FP32-valued.
  *  phi_acc_out: device int32 scalar (1 if the phi proposal was accepted) or NULL. */
 rsv_status rsv_gibbs_theta(rsv_ctx* ctx, const double* h, const double* lnrv, int64_t T,
                            double* theta, uint64_t seed, uint64_t series, uint64_t traj,
