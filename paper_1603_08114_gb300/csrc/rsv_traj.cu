@@ -16,7 +16,11 @@
 // what an untiled integration gives.  A whole series takes its Metropolis
 // decision inside the block and overwrites its state in place on accept; the
 // tiles of a split series write a proposal, and the last tile to finish sums
-// their partial dH in tile order, decides and flips the series' buffer.
+// their partial sums in tile order, decides and flips the series' buffer.
+// In the mixed path without leverage those partial sums are the kinetic
+// difference and the end state's statistics (StateStats): the potential
+// energy of both ends comes from statistics kept per series and buffer, so
+// the start needs only the kinetic energy.
 //
 // State is kept in x = h - mu, so that
 //   dS/dh = ie * AR + iu * x + (1/2 - c' iu) - a' e^{-x},
