@@ -1011,6 +1011,19 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                     for (int i = 0; i < 4; ++i) s_ph[(4 * q + i) * NS + tid] = z[i];
                 }
             }
+            // the previous trajectory's snapshot, which is this one's start
+            // state, in a loop of its own: a global store between the load
+            // pass's loads would keep them from being issued together
+            if (A.snap_prev) {
+                const int wb = (warp - v.g.warp0) * 32 * J;
+                for (int kk = lane; kk < 32 * J; kk += 32) {
+                    const int64_t sg = wlo + wb + kk;
+                    if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
+                        const float2 hv = hin[off + sg];
+                        A.snap_prev[off + sg] = hv.x + hv.y;
+                    }
+                }
+            }
             // pass 1b: site constants, x, mass -> shared memory, and H at the
             // start of the sites the lane loads.  The warp loads its 32 J
             // consecutive sites with consecutive lanes (coalesced) and files
@@ -1066,13 +1079,11 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                     }
                     s_xh[j * NS + to] = x.hi;
                     s_xl[j * NS + to] = x.lo;
-                    const int64_t sg = wlo + ii;
-                    const bool own = v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi;
-                    if (A.snap_prev && own) A.snap_prev[s] = hv.x + hv.y;
                     // H at the start of this site if the segment owns it; without
                     // leverage only K: the potential part comes from the state's
                     // stored statistics (stats_dH)
-                    if (own) {
+                    const int64_t sg = wlo + ii;
+                    if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
                         const ff mw = MASS ? mass_weight(mc.kick, kmv) : ff{1.f, 0.f};
                         if (LEV) {
                             const bool has_next = sg + 1 < v.si.T;
