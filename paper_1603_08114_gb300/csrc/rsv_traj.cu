@@ -747,6 +747,9 @@ __device__ __forceinline__ void stationary_part(HParts& acc, ff x1, const MixedT
 
 // ---- statistics of a state (model without leverage; see StateStats) ----
 constexpr int kStatsFF = 7;
+static_assert(sizeof(StateStats) == kStatsFF * sizeof(ff), "StateStats is kStatsFF double-floats");
+static_assert(kRecWords == 1 + kStatsFF && kPartialWords == 2 + kStatsFF,
+              "record layouts: (dk, statistics) and (sum lnRV, statistics, sum lnRV^2)");
 __device__ __forceinline__ ff* stats_ff(StateStats& s) { return reinterpret_cast<ff*>(&s); }
 __device__ __forceinline__ void stats_zero(StateStats& s)
 {
