@@ -90,6 +90,11 @@ def lib():
             L.orc_gibbs_theta.argtypes = [_D, _D, ctypes.c_long, ctypes.POINTER(Theta),
                                           ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.c_int]
+            L.orc_gibbs_theta_margin.restype = ctypes.c_int
+            L.orc_gibbs_theta_margin.argtypes = [_D, _D, ctypes.c_long, ctypes.POINTER(Theta),
+                                                 ctypes.c_uint64, ctypes.c_uint64,
+                                                 ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                                 _D]
             L.orc_chain.restype = ctypes.c_long
             L.orc_chain.argtypes = [_D, _D, _D, ctypes.c_long, ctypes.POINTER(Theta), _D,
                                     ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
@@ -231,6 +236,21 @@ def gibbs_theta(h, lnrv, th, seed, series, traj, mask=31):
     if acc < 0:
         raise ValueError("the theta conditionals assume rho = 0")
     return t.as_tuple(), acc
+
+
+def gibbs_theta_margin(h, lnrv, th, seed, series, traj, mask=31, bits=53):
+    """gibbs_theta from uniforms of `bits` bits (53, or 23 as the FP32 sweep
+    takes them), also returning the smallest distance of any accept/reject
+    decision of the sweep from its boundary, |lhs - rhs| / (1 + |rhs|)."""
+    h, lnrv = _f64(h), _f64(lnrv)
+    t = theta(th).copy()
+    m = ctypes.c_double()
+    acc = lib().orc_gibbs_theta_margin(_d(h), _d(lnrv), len(h), ctypes.byref(t), int(seed),
+                                       int(series), int(traj), int(mask), int(bits),
+                                       ctypes.byref(m))
+    if acc < 0:
+        raise ValueError("the theta conditionals assume rho = 0")
+    return t.as_tuple(), acc, m.value
 
 
 def chain(h, y, lnrv, th, n_md, dtau, seed, n_traj, traj0=0, series=0, update_theta=False,

@@ -338,15 +338,27 @@ double orc_draw_log_u(uint64_t seed, uint64_t series, uint64_t traj)
 /* Sequential draws for the theta update: words are consumed in order from   */
 /* blocks 0, 1, 2, ... of the theta stream of one trajectory.                */
 /* ------------------------------------------------------------------------ */
+/* margin: the smallest distance of any accept/reject decision taken from    */
+/* the stream to its boundary (relative to 1 + |boundary|), for tests that   */
+/* compare with a lower-precision sampler of the same stream.               */
 typedef struct {
     uint64_t seed, series, traj, block;
     uint64_t w[4];
     int pos;
+    int bits;      /* uniforms (k + 1/2) 2^-bits from the top bits of each word */
+    double margin;
 } orc_stream;
 
 static void stream_init(orc_stream* s, uint64_t seed, uint64_t series, uint64_t traj)
 {
     s->seed = seed; s->series = series; s->traj = traj; s->block = 0; s->pos = 4;
+    s->bits = 53;
+    s->margin = INFINITY;
+}
+static void stream_margin(orc_stream* s, double lhs, double rhs)
+{
+    double m = fabs(lhs - rhs) / (1.0 + fabs(rhs));
+    if (m < s->margin) s->margin = m;
 }
 static double stream_u01(orc_stream* s)
 {
@@ -354,7 +366,7 @@ static double stream_u01(orc_stream* s)
         philox_block(s->seed, s->series, s->traj, ORC_STREAM_THETA, s->block++, s->w);
         s->pos = 0;
     }
-    return orc_u01(s->w[s->pos++], 53);
+    return orc_u01(s->w[s->pos++], s->bits);
 }
 /* One standard normal per call: the cosine branch of Box-Muller. */
 static double stream_normal(orc_stream* s)
@@ -376,10 +388,13 @@ static double stream_gamma(orc_stream* s, double alpha)
     for (int it = 0; it < 1000; ++it) {
         double z = stream_normal(s);
         double v = 1.0 + c * z;
+        stream_margin(s, v, 0.0);
         if (v <= 0.0) continue;
         v = v * v * v;
         double u = stream_u01(s);
-        if (log(u) < 0.5 * z * z + d - d * v + d * log(v)) return d * v;
+        double bound = 0.5 * z * z + d - d * v + d * log(v);
+        stream_margin(s, log(u), bound);
+        if (log(u) < bound) return d * v;
     }
     return NAN;
 }
@@ -401,12 +416,14 @@ static double stream_gamma(orc_stream* s, double alpha)
 /* Returns 1 if the phi proposal was accepted, -1 (theta untouched) under   */
 /* leverage, where these conditionals are not the model's.                  */
 /* ------------------------------------------------------------------------ */
-int orc_gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
-                    uint64_t seed, uint64_t series, uint64_t traj, int mask)
+static int gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
+                       uint64_t seed, uint64_t series, uint64_t traj, int mask,
+                       int bits, double* margin_out)
 {
     if (th->rho != 0.0) return -1;
     orc_stream st;
     stream_init(&st, seed, series, traj);
+    st.bits = bits;
     double Td = (double)T;
 
     /* xi */
@@ -468,16 +485,36 @@ int orc_gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
             double prop = NAN;
             for (int it = 0; it < 1000; ++it) {
                 double c = m + sd * stream_normal(&st);
+                stream_margin(&st, fabs(c), 1.0);
                 if (c > -1.0 && c < 1.0) { prop = c; break; }
             }
             double u = stream_u01(&st);
             if (prop == prop) {
                 double lr = 0.5 * log(1.0 - prop * prop) - 0.5 * log(1.0 - th->phi * th->phi);
+                stream_margin(&st, log(u), lr);
                 if (log(u) < lr) { th->phi = prop; acc = 1; }
             }
         }
     }
+    if (margin_out) *margin_out = st.margin;
     return acc;
+}
+
+int orc_gibbs_theta(const double* h, const double* lnrv, long T, orc_theta* th,
+                    uint64_t seed, uint64_t series, uint64_t traj, int mask)
+{
+    return gibbs_theta(h, lnrv, T, th, seed, series, traj, mask, 53, NULL);
+}
+
+/* The same sweep from uniforms of `bits` bits (53, or 23 as a sampler that   */
+/* draws in FP32 takes them from the same words), also reporting the        */
+/* stream's smallest decision margin.                                       */
+int orc_gibbs_theta_margin(const double* h, const double* lnrv, long T, orc_theta* th,
+                           uint64_t seed, uint64_t series, uint64_t traj, int mask, int bits,
+                           double* margin_out)
+{
+    if (bits < 1 || bits > 53) return -2;
+    return gibbs_theta(h, lnrv, T, th, seed, series, traj, mask, bits, margin_out);
 }
 
 /* ------------------------------------------------------------------------ */
