@@ -153,7 +153,10 @@ rsv_status rsv_action(rsv_ctx* ctx, const double* h, const double* y, const doub
  *  - T must be 1 .. 8,388,608 (4096 blocks of 2048 sites); larger T returns
  *    RSV_EINVAL before any launch (use rsv_action).
  *  - The first call on a device looks up the array's device address (one-time
- *    set-up); make that first call before any stream capture.
+ *    set-up); make that first call before any stream capture.  The address
+ *    is kept with the id of the device's context: after a cudaDeviceReset the
+ *    next call looks it up again in the new context (so that call, too, must
+ *    come before any capture).
  *  - All calls share the one array: calls that can overlap on the GPU (other
  *    streams, other host threads) race and must be serialised by the caller.
  *    The arrival counter is cleared by each call before its launch.
@@ -358,6 +361,21 @@ rsv_status rsv_draw_momenta(rsv_ctx* ctx, uint64_t seed, uint64_t series, uint64
  * recorded events; reset != 0 clears the counters after reading. */
 rsv_status rsv_ess(rsv_ctx* ctx, const float* x, int64_t n, int64_t T, float* ess_out,
                    void* stream);
+/* rsv_pipe_probe: launch one probe kernel that keeps one on-chip unit busy on
+ * every SM with independent dependency chains, and set *ops_out (host) to the
+ * number of operations that launch performs; the caller times the launch on
+ * `stream` (CUDA events) and divides.  Not part of the paper's method: it
+ * measures the peaks the trajectory kernels are reported against.
+ *   RSV_PROBE_FFMA   scalar FP32 FMA               (ops = FMAs)
+ *   RSV_PROBE_FFMA2  packed FP32 FMA, 2 per instruction (ops = FMAs)
+ *   RSV_PROBE_EX2    ex2.approx.f32 on the special-function unit, each
+ *                    followed by one dependent FP32 FMA   (ops = ex2)
+ *   RSV_PROBE_LDS    16-byte shared-memory loads    (ops = bytes loaded)
+ *   RSV_PROBE_DFMA   FP64 FMA                       (ops = FMAs)
+ * iters: 1 .. 2^40 (each thread runs 16 iters x 8 chains of its kind). */
+enum { RSV_PROBE_FFMA = 0, RSV_PROBE_FFMA2 = 1, RSV_PROBE_EX2 = 2, RSV_PROBE_LDS = 3,
+       RSV_PROBE_DFMA = 4 };
+rsv_status rsv_pipe_probe(rsv_ctx* ctx, int kind, int64_t iters, double* ops_out, void* stream);
 rsv_status rsv_timing(rsv_ctx* ctx, int enable);
 rsv_status rsv_stats(rsv_ctx* ctx, int reset, int64_t* launches, int64_t* traj_launches,
                      double* traj_ms);

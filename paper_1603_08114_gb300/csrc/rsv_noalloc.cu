@@ -29,8 +29,51 @@ constexpr size_t kNoallocBytes = kNoallocMaxBlocks * sizeof(double) + 256;
 // arrival counter.  Every call on a device shares it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
+// The array's device address is looked up once per device context and
+// cached with that context's unique id: cudaDeviceReset destroys the device's
+// context, the module is loaded again into the next one and the array may move,
+// so a cached address is used only while the current context is the one it was
+// looked up in.
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[64] = {};  // device address of g_noalloc_scratch, per device
+struct NoallocSlot {
+    unsigned long long ctx_id;  // 0 = none
+    void* ptr;
+};
+NoallocSlot g_noalloc_slot[64] = {};
+
+// Driver entry points for the current context's id (cuCtxGetCurrent and
+// cuCtxGetId, CUDA >= 12.0), fetched through the runtime so that the library
+// does not link libcuda itself.  Their CUresult is returned as int (0 = OK).
+typedef int (*PfnCtxGetCurrent)(void** ctx);
+typedef int (*PfnCtxGetId)(void* ctx, unsigned long long* id);
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// Unique id of the calling thread's current context, or 0 when there is none
+// or the driver cannot tell (then the address is looked up on every call).
+unsigned long long current_ctx_id()
+{
+    if (!g_ctx_fns_tried) {
+        g_ctx_fns_tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f);
+        (void)cudaGetLastError();
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != 0 || ctx == nullptr) return 0;
+    if (g_ctx_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 __global__ void __launch_bounds__(kNoallocThreads) k_action_noalloc(
     const double* __restrict__ h, const double* __restrict__ y, const double* __restrict__ lnrv,
@@ -95,15 +138,21 @@ extern "C" rsv_status rsv_action_noalloc(const double* h, const double* y, const
     void* ptr = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            // one-time set-up on this device (the current one)
-            e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+        NoallocSlot& slot = g_noalloc_slot[dev];
+        const unsigned long long id = current_ctx_id();
+        if (id != 0 && slot.ctx_id == id) {
+            ptr = slot.ptr;
+        } else {
+            // set-up on this device (the current one): the first call, or the
+            // first in a new context (after a device reset)
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
             if (e != cudaSuccess) {
-                g_noalloc_ptr[dev] = nullptr;
+                slot = NoallocSlot{0, nullptr};
                 return cuda_fail(e, "cudaGetSymbolAddress of the fixed scratch");
             }
+            // the lookup made the device's context current if none was
+            slot = NoallocSlot{current_ctx_id(), ptr};
         }
-        ptr = g_noalloc_ptr[dev];
     }
     unsigned char* scratch = static_cast<unsigned char*>(ptr);
     cudaStream_t st = (cudaStream_t)stream;

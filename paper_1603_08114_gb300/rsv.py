@@ -79,13 +79,14 @@ def lib():
         L.rsv_hmc_batched.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_double, _U64,
                                       _U64, _I64, _P, _P, _P, _P]
         L.rsv_timing.argtypes = [_P, _INT]
+        L.rsv_pipe_probe.argtypes = [_P, _INT, _I64, ctypes.POINTER(ctypes.c_double), _P]
         L.rsv_stats.argtypes = [_P, _INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                 ctypes.POINTER(ctypes.c_double)]
         for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule",
                      "rsv_set_integrator", "rsv_set_leverage", "rsv_action", "rsv_force",
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
                      "rsv_timing", "rsv_stats", "rsv_gibbs_theta", "rsv_plan_create",
-                     "rsv_plan_info", "rsv_hmc_batched"):
+                     "rsv_plan_info", "rsv_hmc_batched", "rsv_pipe_probe"):
             getattr(L, name).restype = _INT
         _lib = L
     return _lib
@@ -261,6 +262,18 @@ def rsv_ess(ctx: Context, x):
     _check(lib().rsv_ess(ctx.handle, _ptr(x, torch.float32, n * T, "x"), int(n), int(T),
                          _ptr(out, torch.float32, T, "ess_out"), _stream()))
     return out
+
+
+PROBE_KINDS = {"ffma": 0, "ffma2": 1, "ex2": 2, "lds": 3, "dfma": 4}
+
+
+def rsv_pipe_probe(ctx: Context, kind: str, iters: int) -> float:
+    """Launch one pipe-probe kernel on the current stream; returns the number
+    of operations it performs (FMAs, ex2, or bytes for "lds")."""
+    ops = ctypes.c_double()
+    _check(lib().rsv_pipe_probe(ctx.handle, PROBE_KINDS[kind], int(iters), ctypes.byref(ops),
+                                _stream()))
+    return ops.value
 
 
 def rsv_timing(ctx: Context, enable: bool = True):

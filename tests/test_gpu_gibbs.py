@@ -97,21 +97,20 @@ def test_chain_theta_posterior_means_agree_with_oracle(rsv, ctx, prec):
 @pytest.mark.parametrize("T", [1, 2, 3, 100, 2000, 65537])
 def test_gibbs_sweep_mixed_close_to_oracle(rsv, ctx, T):
     """The mixed sweep (double-float statistics, FP32 draws from 23-bit uniforms
-    of the same stream positions) lands within FP32-level distance of the FP64
-    oracle's draw from the same state: a 23-bit uniform is within 2^-24 of the
-    53-bit one, so every variate moves by ~1e-7 relative, except when a
-    rejection decision lies that close to its boundary (allowed once in 8).
-    theta comes out FP32-valued."""
+    of the same stream positions) against the FP64 oracle's sweep from the
+    same 23-bit uniforms: every variate agrees to FP32-level distance (1e-4
+    relative), unless one of the sweep's accept/reject decisions lies within
+    1e-4 of its boundary in the oracle (its smallest decision margin), where
+    FP32 rounding may take the other branch.  theta comes out FP32-valued."""
     s = synth.rsv_series(T, TH, seed=T)
     h = s.h_true + 0.05 * synth.standard_normals(T, 1)
-    far = 0
     for traj in range(8):
         th = dev(TH)
         rsv.rsv_gibbs_theta(ctx, dev(h), dev(s.lnrv), th, seed=5, series=0, traj=traj,
                             prec="mixed")
         got = th.cpu().numpy()
-        ref, _ = oracle.gibbs_theta(h, s.lnrv, TH, seed=5, series=0, traj=traj)
+        ref, _, margin = oracle.gibbs_theta_margin(h, s.lnrv, TH, seed=5, series=0, traj=traj,
+                                                   bits=23)
         assert np.array_equal(got.astype(np.float32).astype(np.float64), got)
-        rel = np.abs(got - ref) / np.abs(ref)
-        far += int(rel.max() > 1e-4)
-    assert far <= 1, far
+        rel = np.abs(got - np.array(ref)) / np.abs(np.array(ref))
+        assert rel.max() <= 1e-4 or margin < 1e-4, (traj, rel, margin)

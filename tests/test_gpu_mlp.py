@@ -105,6 +105,41 @@ def test_forward_matches_reference(rsv, ctx, problem, scaled):
     assert np.allclose(minv, 1 / m_gpu.cpu().numpy(), rtol=1e-6)
 
 
+@pytest.mark.parametrize("scaled", [False, True])
+def test_forward_against_fp64_network_within_bf16_bound(rsv, ctx, problem, scaled):
+    """The GPU network (BF16 operands, FP32 accumulation) against the plain
+    FP64 network, with a per-site bound derived from BF16 rounding alone:
+    round-to-nearest BF16 (8 significant bits) moves each operand by at most
+    u = 2^-8 relative, so to first order
+      |dz1_j| <= 2u sum_i |f_i W1_ji|                  (features and W1 rounded)
+      |dz2_k| <= sum_j |W2_kj| (|dz1_j| + 2u |a1_j|)     (tanh' <= 1; a1, W2 rounded)
+      |dz3|   <= sum_k |W3_k| |dz2_k|                  (W3 and a2 stay FP32)
+      |d ln m| <= sigmoid(z3) / (softplus(z3) + eps) |dz3|,
+    taken with 10 % for second-order terms plus 1e-5 for FP32 accumulation
+    and the FP32 tanh, exp and log1p."""
+    P = unflat(flat(problem["P"]))   # the FP32 parameters the GPU holds
+    params = dev(flat(problem["P"]), torch.float32)
+    m_gpu = torch.empty(problem["T"], dtype=torch.float32, device="cuda")
+    s = problem["series"]
+    ls = problem["log_s"] if scaled else 0.0
+    rsv.rsv_mlp_mass(ctx, problem["F"], params, dev(s.y), dev(s.h_true), TH, m_out=m_gpu,
+                     log_scale=problem["log_s_dev"] if scaled else None)
+    F = problem["Fnp"]
+    ref = mlp.forward(P, F, bf=False, log_s=ls)
+    u = 2.0 ** -8
+    dz1 = 2 * u * (np.abs(F) @ np.abs(P["W1"]).T)
+    dz2 = (dz1 + 2 * u * np.abs(ref["a1"])) @ np.abs(P["W2"]).T
+    dz3 = dz2 @ np.abs(P["W3"])
+    sig = 1.0 / (1.0 + np.exp(-ref["z3"]))
+    bound = 1.1 * sig / ref["u"] * dz3 + 1e-5
+    lo, hi = mlp.mass_bounds(s.y, s.h_true, TH)
+    m_ref = np.clip(ref["m"], lo, hi)   # the clamp is 1-Lipschitz in ln m
+    err = np.abs(np.log(m_gpu.cpu().numpy().astype(np.float64)) - np.log(m_ref))
+    assert np.all(err <= bound), (err.max(), bound[np.argmax(err - bound)])
+    # the bound is not vacuous: BF16 rounding is visible against FP64
+    assert np.median(bound) < 0.1 and np.max(err) > 1e-5
+
+
 @pytest.mark.parametrize("batch,scaled", [(64, False), (4096, False), (4096, True)])
 def test_gradient_matches_reference(rsv, ctx, problem, batch, scaled):
     params = dev(flat(problem["P"]), torch.float32)

@@ -73,23 +73,24 @@ def test_recentred_statistics_match_a_fresh_record(rsv, ctx, T, mass):
 def test_sweep_from_statistics_close_to_oracle(rsv, ctx, T):
     """One mixed trajectory, then the theta sweep, which takes its sums from
     the statistics of the state the trajectory left (no pass over the sites):
-    theta lands within FP32-level distance of the FP64 oracle's sweep of that
-    state from the same stream positions (23-bit against 53-bit uniforms, FP32
-    against FP64 draws), allowing one rejection decision in 8 that close to
-    its boundary.  theta comes out FP32-valued."""
+    theta lands within FP32-level distance (1e-4 relative) of the FP64
+    oracle's sweep of that state from the same 23-bit uniforms, unless one of
+    the sweep's accept/reject decisions lies within 1e-4 of its boundary in
+    the oracle, where FP32 rounding may take the other branch.  theta comes
+    out FP32-valued."""
     import oracle
     s = synth.rsv_series(T, TH, seed=T)
-    far = 0
     for traj in range(8):
         h, th = dev(s.h_true), dev(TH)
         rsv.rsv_hmc_chain(ctx, h, dev(s.y), dev(s.lnrv), th, 20, 0.02, 1, prec="mixed", seed=5,
                           traj0=traj, update_theta=True)
         rsv.rsv_sync_status(ctx)
         got = th.cpu().numpy()
-        ref, _ = oracle.gibbs_theta(h.cpu().numpy(), s.lnrv, TH, seed=5, series=0, traj=traj)
+        ref, _, margin = oracle.gibbs_theta_margin(h.cpu().numpy(), s.lnrv, TH, seed=5, series=0,
+                                                   traj=traj, bits=23)
         assert np.array_equal(got.astype(np.float32).astype(np.float64), got)
-        far += int((np.abs(got - ref) / np.abs(ref)).max() > 1e-4)
-    assert far <= 1, far
+        rel = (np.abs(got - np.array(ref)) / np.abs(np.array(ref))).max()
+        assert rel <= 1e-4 or margin < 1e-4, (traj, rel, margin)
 
 
 @pytest.mark.parametrize("T,update_theta", [(3000, True), (1 << 17, False), (1 << 17, True)])
@@ -110,3 +111,48 @@ def test_mixed_chain_snapshots_are_the_states(rsv, ctx, T, update_theta):
                           update_theta=update_theta)
         rsv.rsv_sync_status(ctx)
         assert torch.equal(snaps[k - 1], hk.float()), k
+
+
+@pytest.mark.parametrize("n,thin", [(6, 3), (7, 3), (8, 3)])
+@pytest.mark.parametrize("T", [3000, 1 << 17])
+def test_mixed_chain_thinned_snapshots_are_the_states(rsv, ctx, T, n, thin):
+    """Snapshots every thin-th trajectory, n not always a multiple of thin: a
+    due snapshot is written by the next trajectory's load pass when there is
+    one, the last due one by its own kernel; snapshot k is the state after
+    (k + 1) thin trajectories, bit for bit."""
+    s = synth.rsv_series(T, TH, seed=5)
+    y, lr = dev(s.y), dev(s.lnrv)
+    snaps = torch.full((n // thin, T), float("nan"), dtype=torch.float32, device="cuda")
+    h, th = dev(s.h_true), dev(TH)
+    rsv.rsv_hmc_chain(ctx, h, y, lr, th, 10, 0.02, n, prec="mixed", seed=19,
+                      update_theta=True, snaps=snaps, thin=thin)
+    for k in range(n // thin):
+        hk, thk = dev(s.h_true), dev(TH)
+        rsv.rsv_hmc_chain(ctx, hk, y, lr, thk, 10, 0.02, (k + 1) * thin, prec="mixed",
+                          seed=19, update_theta=True)
+        rsv.rsv_sync_status(ctx)
+        assert torch.equal(snaps[k], hk.float()), k
+
+
+@pytest.mark.parametrize("T", [3000, 1 << 17])
+def test_mixed_leverage_chain_snapshots_are_the_states(rsv, ctx, T):
+    """The same with leverage (rho = -0.4, theta fixed), whose kernel keeps H
+    at both ends per site and writes the deferred snapshot from its own
+    instantiation of the load pass."""
+    s = synth.rsv_series_leverage(T, TH, synth.RHO_STD, seed=6)
+    y, lr = dev(s.y), dev(s.lnrv)
+    n, thin = 5, 2
+    snaps = torch.full((n // thin, T), float("nan"), dtype=torch.float32, device="cuda")
+    rsv.rsv_set_leverage(ctx, synth.RHO_STD)
+    try:
+        h, th = dev(s.h_true), dev(TH)
+        rsv.rsv_hmc_chain(ctx, h, y, lr, th, 10, 0.02, n, prec="mixed", seed=23, snaps=snaps,
+                          thin=thin)
+        for k in range(n // thin):
+            hk, thk = dev(s.h_true), dev(TH)
+            rsv.rsv_hmc_chain(ctx, hk, y, lr, thk, 10, 0.02, (k + 1) * thin, prec="mixed",
+                              seed=23)
+            rsv.rsv_sync_status(ctx)
+            assert torch.equal(snaps[k], hk.float()), k
+    finally:
+        rsv.rsv_set_leverage(ctx, 0.0)
