@@ -11,12 +11,16 @@ Headline sampler: mixed precision with the learned diagonal mass (trained
 before timing from 10^4 plain-sampler snapshots; its step size tuned to ~0.8
 acceptance at the plain sampler's physical trajectory length; identity-mass
 fallback).  Reported: leapfrog site-updates/s (T * n_md * trajectories /
-time) and ESS/s of h (per-site ESS over the step's 200 draws / step time) and
-of theta, beside the plain mixed and plain FP64 samplers (identity mass,
-100 x 0.005), the 4096-series batched workload, the RSV model with leverage
-and the minimum-norm integrator (identity and learned mass); the MD-only
-rate, the end-to-end rate from pinned host buffers, the trajectory kernel's
-roofline and the CPU oracle's rate.
+time) and ESS/s of h and theta (Geyer ESS over the whole timed chain / its
+time), beside the plain mixed and plain FP64 samplers (identity mass,
+100 x 0.005) with a check that the learned and identity chains reach the same
+per-site posterior moments, the T = 2000 FP64 workload, the T = 2^22 mixed
+workload with its error against the FP64 path, the elementary-step sweep of
+the paper's Table 2 (B = 1 ... 2048), the 4096-series batched workload, the
+RSV model with leverage and the minimum-norm integrator (identity and learned
+mass); the MD-only rate, the end-to-end rate from pinned host buffers, the
+trajectory kernel's roofline against FP32 and ex2 peaks measured in the same
+run, and the CPU oracle's rate.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -47,17 +51,21 @@ UNIT = "site-updates/s"
 THETA_NAMES = ("phi", "mu", "xi", "sig_eta2", "sig_u2")
 WORKLOAD = ("rsv-hmc single chain T=2^20, theta sampled, 200 trajectories per step; "
             "learned mass (tuned dtau, n_md) vs identity 100 x 0.005")
-# Algorithmic FP32 operations per site and leapfrog step of the mixed kernel:
-# the three-point force (neighbour sum 1, two stencil FMAs 2, exponent argument
-# 1, the y^2/2 e^-h term 1), the compensated p update (4; the velocity p/m
-# with a mass) and the compensated h update (4).  The exp2 itself runs on the
-# special-function unit.
-OPS_PER_SITE_STEP_MIXED = 13
+# The method's algorithmic work per site and leapfrog step (eqs. (6)-(8)):
+# two half-step drifts of h (2), the force of eq. (7) -- neighbour sum, the
+# (1+phi^2) x and phi (x_{t-1} + x_{t+1}) terms with the RV term folded in, the
+# exponent argument and the y^2/2 e^{-h} term (5), the kick of p (1), and
+# the two FMAs of a diagonal mass (2): 10 FP operations and one exp.
+ALG_OPS_PER_SITE_STEP = 10
+# What the mixed kernel issues for the same step: the three-point force (5),
+# the compensated kick (4) and the compensated drift (4; the two half drifts
+# merged), i.e. 3 operations of compensation beyond the method's 10.
+IMPL_OPS_PER_SITE_STEP_MIXED = 13
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_traj_mixed launch of
 # the headline workload (learned mass, T = 2^20), from the capture summarised in
 # profiles/k_traj_mixed_T2p20.md (the inputs are read once per launch, so the
 # figure does not depend on n_md); valid for the kernel revision it was taken on.
-TRAFFIC = {"kernel_rev": 10, "bytes": 25271040}
+TRAFFIC = {"kernel_rev": 11, "bytes": 25270272}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -68,6 +76,34 @@ def _peaks():
         with open(path) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# launches of the pipe probes sized to ~5 ms each on this GPU
+PROBE_ITERS = {"ffma": 5000, "ffma2": 5000, "ex2": 600, "lds": 2500, "dfma": 75}
+
+
+def measure_pipe_peaks(ctx, rsv, torch):
+    """On-chip peaks the trajectory kernels are bound by, measured here: each
+    rsv_pipe_probe launch keeps one unit busy on every SM; its operations /
+    its CUDA-event time, best of 3 after one warm-up.  Units: op/s (an FMA is
+    one operation), bytes/s for shared-memory loads."""
+    out = {}
+    for kind, it in PROBE_ITERS.items():
+        best = None
+        for r in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ops = rsv.rsv_pipe_probe(ctx, kind, it)
+            b.record()
+            b.synchronize()
+            if r:
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+        out[kind] = ops / (best * 1e-3)
+    out["fp32"] = max(out["ffma"], out["ffma2"])
+    out["how"] = ("rsv_pipe_probe: 152 x 4 blocks of 512 threads, 8 independent chains per "
+                  "thread of one instruction kind; operations / CUDA-event time, best of 3")
+    return out
 
 
 class Clocks:
@@ -281,65 +317,83 @@ def run_ours(args):
     acc = torch.empty(N_TRAJ, dtype=torch.int32, device=dev)
     dH = torch.empty(N_TRAJ, dtype=torch.float64, device=dev)
     rsv.rsv_reserve(ctx, T_SITES)
+    pipe = measure_pipe_peaks(ctx, rsv, torch)
     minv = None
     if args.mass_file:
         minv = torch.tensor(np.load(args.mass_file).astype(np.float32), device=dev)
 
-    thetas = torch.empty(N_TRAJ, 5, dtype=torch.float64, device=dev)
-
-    def run_chain(prec, mass, n_md, dtau, sampler, h, th, traj, record):
+    def run_chain(prec, mass, n_md, dtau, sampler, h, th, traj, rec=None):
+        """One step: N_TRAJ trajectories, each followed by a theta sweep; rec =
+        (snapshots [N_TRAJ][T], theta records [N_TRAJ][5], accept [N_TRAJ])."""
+        sn, tho, ac = rec if rec is not None else (None, None, None)
         if sampler is not None:
-            if record:
-                sampler.run(h, y, lnrv, th, N_TRAJ, seed=11 + rank, traj0=traj, snaps=snaps,
-                            theta_out=thetas, accept_out=acc)
-            else:
-                sampler.run(h, y, lnrv, th, N_TRAJ, seed=11 + rank, traj0=traj)
-        elif record:
-            rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, n_md, dtau, N_TRAJ, prec=prec, minv=mass,
-                              seed=11 + rank, traj0=traj, snaps=snaps, thin=1, accept_out=acc,
-                              dH_out=dH, update_theta=True, theta_out=thetas)
+            sampler.run(h, y, lnrv, th, N_TRAJ, seed=11 + rank, traj0=traj, snaps=sn,
+                        theta_out=tho, accept_out=ac)
         else:
             rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, n_md, dtau, N_TRAJ, prec=prec, minv=mass,
-                              seed=11 + rank, traj0=traj, update_theta=True)
+                              seed=11 + rank, traj0=traj, snaps=sn, thin=1, accept_out=ac,
+                              update_theta=True, theta_out=tho)
+
+    def site_moments(snaps_all, ess):
+        """Per-site posterior mean and variance of h over the chain, with their
+        Monte-Carlo standard errors (sd / sqrt(ESS); the variance's from the
+        squared deviations' own sd)."""
+        n = snaps_all.shape[0]
+        m = torch.zeros(T_SITES, dtype=torch.float64, device=dev)
+        for i in range(0, n, 250):
+            m += snaps_all[i:i + 250].double().sum(0)
+        m /= n
+        v = torch.zeros_like(m)
+        q = torch.zeros_like(m)
+        for i in range(0, n, 250):
+            d2 = (snaps_all[i:i + 250].double() - m) ** 2
+            v += d2.sum(0)
+            q += (d2 ** 2).sum(0)
+        v /= n
+        sd_d2 = torch.sqrt(torch.clamp(q / n - v * v, min=0.0))
+        e = torch.clamp(ess.double(), min=1.0)
+        return dict(mean=m, var=v, mcse_mean=torch.sqrt(v / e), mcse_var=sd_d2 / torch.sqrt(e))
 
     def arm(prec, mass, warmup, steps, clocks=None, timing=False, n_md=N_MD, dtau=DTAU,
-            sampler=None):
+            sampler=None, moments=False, nvtx=False):
         # the chain starts from the generator's latent path, a posterior-typical
         # state (from lnRV - xi the first trajectories are all rejected); every
-        # trajectory is followed by a Gibbs sweep of theta
+        # trajectory is followed by a Gibbs sweep of theta.  The warm-up steps
+        # are its burn-in; ESS is taken over the whole timed chain (steps x
+        # N_TRAJ draws), after the timed region.
         h = torch.tensor(s.h_true, device=dev)
         th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
         traj = 0
         for _ in range(warmup):
-            run_chain(prec, mass, n_md, dtau, sampler, h, th, traj, False)
+            run_chain(prec, mass, n_md, dtau, sampler, h, th, traj)
             traj += N_TRAJ
         nonfinite = rsv.rsv_sync_status(ctx, allow_nonfinite=True) == rsv.RSV_ENONFINITE
+        n_all = steps * N_TRAJ
+        snaps_all = torch.empty(n_all, T_SITES, dtype=torch.float32, device=dev)
+        thetas_all = torch.empty(n_all, 5, dtype=torch.float64, device=dev)
+        acc_all = torch.empty(n_all, dtype=torch.int32, device=dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
-        ess_med, ess_min, ess_th, acc_rate = [], [], [], []
         rsv.rsv_stats(ctx, reset=True)
         rsv.rsv_timing(ctx, timing)
         _barrier(ws)
         if clocks:
             clocks.__enter__()
-        if timing:  # marks the headline's timed kernels for ncu (--nvtx-include "timed/")
+        if nvtx:  # marks the headline's timed kernels for ncu (--nvtx-include "timed/")
             torch.cuda.nvtx.range_push("timed")
         launches = 0
         md0 = sampler.md_steps if sampler is not None else 0
         for k in range(steps):
             flush.zero_()
             l0 = rsv.rsv_stats(ctx, reset=False)[0]
+            sl = slice(k * N_TRAJ, (k + 1) * N_TRAJ)
             ev[k][0].record()
-            run_chain(prec, mass, n_md, dtau, sampler, h, th, traj, True)
+            run_chain(prec, mass, n_md, dtau, sampler, h, th, traj,
+                      (snaps_all[sl], thetas_all[sl], acc_all[sl]))
             ev[k][1].record()
             traj += N_TRAJ
             launches += rsv.rsv_stats(ctx, reset=False)[0] - l0
-            e = rsv.rsv_ess(ctx, snaps)
-            ess_med.append(e.median())
-            ess_min.append(e.min())
-            ess_th.append(rsv.rsv_ess(ctx, thetas.float().contiguous()))
-            acc_rate.append(acc.float().mean())
-        if timing:
+        if nvtx:
             torch.cuda.nvtx.range_pop()
         _barrier(ws)
         if clocks:
@@ -349,30 +403,30 @@ def run_ours(args):
         # a non-finite dH is a rejected trajectory, not a failure; it is reported
         nonfinite |= rsv.rsv_sync_status(ctx, allow_nonfinite=True) == rsv.RSV_ENONFINITE
         ms = [a.elapsed_time(b) for a, b in ev]
-        total_s = sum(ms) / 1e3
-        total_s = _barrier_max(ws, total_s)
+        total_s = _barrier_max(ws, sum(ms) / 1e3)
         sec_per_step = total_s / steps
         # leapfrog steps per site actually run per step (the mass sampler may
         # have fallen back to the plain settings part-way)
         md_per_step = ((sampler.md_steps - md0) / steps if sampler is not None
                        else n_md * N_TRAJ)
-        ess_med = [float(x) for x in ess_med]
-        ess_min = [float(x) for x in ess_min]
-        ess_th = torch.stack(ess_th).mean(0).cpu().numpy()
+        ess = rsv.rsv_ess(ctx, snaps_all)
+        ess_th = rsv.rsv_ess(ctx, thetas_all.float().contiguous()).cpu().numpy()
+        ess_med, ess_min = float(ess.median()), float(ess.min())
+        mom = site_moments(snaps_all, ess) if moments else None
+        del snaps_all
         return dict(
             site_updates_per_s=job_rate(ws, T_SITES * md_per_step, sec_per_step),
             md_steps_per_step=md_per_step,
             n_md=n_md, dtau=dtau,
-            ms_per_step=1e3 * sec_per_step,
-            ess_h_median_per_s=ws * statistics.mean(ess_med) / sec_per_step,
-            ess_h_min_per_s=ws * statistics.mean(ess_min) / sec_per_step,
-            ess_h_median=statistics.mean(ess_med), ess_h_min=statistics.mean(ess_min),
-            ess_theta_per_s={n: ws * float(v) / sec_per_step
-                             for n, v in zip(THETA_NAMES, ess_th)},
-            ess_theta_per_step={n: float(v) for n, v in zip(THETA_NAMES, ess_th)},
-            accept_rate=float(statistics.mean(float(a) for a in acc_rate)),
+            ms_per_step=1e3 * sec_per_step, timed_s=total_s, draws=n_all,
+            ess_h_median_per_s=ws * ess_med / total_s,
+            ess_h_min_per_s=ws * ess_min / total_s,
+            ess_h_median=ess_med, ess_h_min=ess_min,
+            ess_theta_per_s={n: ws * float(v) / total_s for n, v in zip(THETA_NAMES, ess_th)},
+            ess_theta={n: float(v) for n, v in zip(THETA_NAMES, ess_th)},
+            accept_rate=float(acc_all.float().mean()),
             launches=launches, traj_launches=traj_launches, traj_ms=traj_ms,
-            nonfinite_dH_seen=bool(nonfinite))
+            nonfinite_dH_seen=bool(nonfinite), moments=mom, h_end=h, theta_end=th)
 
     def step_kernel_us(yv, lv, h0, n_hi, n=10):
         """Per-step time of the mixed trajectory kernel (identity mass, theta
@@ -509,6 +563,107 @@ def run_ours(args):
                 "schedule": {"threads": sched["threads"], "sites_per_thread":
                              sched["sites_per_thread"], "cached": sched["cached"], **info}}
 
+    def c1_leg():
+        """The T = 2000 workload: plain FP64 HMC, theta held at its true values,
+        1000 trajectories of 50 x 0.02 in one rsv_hmc_chain call (seed 0
+        series, Philox momenta and uniforms); two calls, the second timed."""
+        sc = synth.rsv_series(2000, synth.THETA_STD, seed=0)
+        yc, lc = torch.tensor(sc.y, device=dev), torch.tensor(sc.lnrv, device=dev)
+        hc = torch.tensor(sc.h_true, device=dev)
+        thc = torch.tensor(sc.theta, dtype=torch.float64, device=dev)
+        n = 1000
+        snc = torch.empty(n, 2000, dtype=torch.float32, device=dev)
+        acc_c = torch.empty(n, dtype=torch.int32, device=dev)
+        rsv.rsv_hmc_chain(ctx, hc, yc, lc, thc, 50, 0.02, n, prec="fp64", seed=41)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        rsv.rsv_hmc_chain(ctx, hc, yc, lc, thc, 50, 0.02, n, prec="fp64", seed=41, traj0=n,
+                          snaps=snc, thin=1, accept_out=acc_c)
+        b.record()
+        b.synchronize()
+        rsv.rsv_sync_status(ctx)
+        sec = _barrier_max(ws, a.elapsed_time(b) / 1e3)
+        e = rsv.rsv_ess(ctx, snc)
+        return {"T": 2000, "n_md": 50, "dtau": 0.02, "trajectories": n, "precision": "fp64",
+                "theta": "held at its true values", "site_updates_per_s": ws * 2000 * 50 * n / sec,
+                "ms_per_1000_trajectories": 1e3 * sec,
+                "ess_h_median_per_s": ws * float(e.median()) / sec,
+                "ess_h_min_per_s": ws * float(e.min()) / sec,
+                "accept_rate": float(acc_c.float().mean())}
+
+    def c4_leg(n_cmp=10, n_rate=20):
+        """T = 2^22 (phi 0.97, s_eta^2 0.03, seed 3), 100 x 0.003: the mixed
+        path's rate (a chain of n_rate trajectories, theta fixed) and its
+        error against the FP64 GPU path (itself at 1e-12 of the FP64 oracle in
+        the tests) on n_cmp trajectories from the same start, momenta and
+        uniforms: h' error, dH error, accept agreement."""
+        T4 = 1 << 22
+        s4 = synth.rsv_series(T4, synth.THETA_LARGE, seed=3)
+        y4, l4 = torch.tensor(s4.y, device=dev), torch.tensor(s4.lnrv, device=dev)
+        rsv.rsv_reserve(ctx, T4)
+        h4 = torch.tensor(s4.h_true, device=dev)
+        th4 = torch.tensor(s4.theta, dtype=torch.float64, device=dev)
+        rsv.rsv_hmc_chain(ctx, h4, y4, l4, th4, 100, 0.003, 2, prec="mixed", seed=51)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        acc4 = torch.empty(n_rate, dtype=torch.int32, device=dev)
+        a.record()
+        rsv.rsv_hmc_chain(ctx, h4, y4, l4, th4, 100, 0.003, n_rate, prec="mixed", seed=51,
+                          traj0=2, accept_out=acc4)
+        b.record()
+        b.synchronize()
+        sec = _barrier_max(ws, a.elapsed_time(b) / 1e3)
+        err_h, err_dh, agree, marginal = 0.0, 0.0, 0, 0
+        for k in range(n_cmp):
+            p0 = torch.tensor(synth.standard_normals(T4, 300 + k), device=dev)
+            lu = torch.tensor(synth.log_uniforms(1, 400 + k), device=dev)
+            out = {}
+            for prec in ("fp64", "mixed"):
+                hh, pp = h4.clone(), p0.clone()
+                dHk, ak = rsv.rsv_hmc_trajectory(ctx, hh, pp, y4, l4, s4.theta, 100, 0.003,
+                                                 prec=prec, log_u=lu)
+                out[prec] = (hh, float(dHk.item()), int(ak.item()))
+            (h64, d64, a64), (h32, d32, a32) = out["fp64"], out["mixed"]
+            if a64 and a32:
+                err_h = max(err_h, float(((h32 - h64).abs() / h64.abs().clamp(min=1.0)).max()))
+            err_dh = max(err_dh, abs(d32 - d64))
+            if abs(d64 + float(lu.item())) > 1e-2:
+                agree += int(a64 == a32)
+            else:
+                marginal += 1
+        rsv.rsv_sync_status(ctx)
+        return {"T": T4, "n_md": 100, "dtau": 0.003, "theta": list(synth.THETA_LARGE),
+                "precision": "mixed (FP32 leapfrog, double-float dH)",
+                "site_updates_per_s": ws * T4 * 100 * n_rate / sec,
+                "ms_per_trajectory": 1e3 * sec / n_rate,
+                "accept_rate": float(acc4.float().mean()),
+                "vs_fp64_gpu": {"trajectories": n_cmp, "h_rel_err_max": err_h,
+                                "dH_abs_err_max": err_dh, "accept_agree": agree,
+                                "accept_compared": n_cmp - marginal,
+                                "marginal_skipped": marginal,
+                                "bounds": {"h": 1e-4, "dH": 1e-3, "gap": 1e-2}}}
+
+    def c5_compare(head_r, ident_r):
+        """Learned vs identity mass at equal posterior accuracy: per-site
+        posterior means and variances of the two timed chains agree within
+        their combined Monte-Carlo errors (z = |difference| / combined MCSE;
+        under equal moments about 0.05 % of 2^20 sites exceed 3.5)."""
+        a, b = head_r["moments"], ident_r["moments"]
+        if a is None or b is None:
+            return None
+        z_m = (a["mean"] - b["mean"]).abs() / torch.sqrt(a["mcse_mean"] ** 2 + b["mcse_mean"] ** 2)
+        z_v = (a["var"] - b["var"]).abs() / torch.sqrt(a["mcse_var"] ** 2 + b["mcse_var"] ** 2)
+        q = torch.tensor([0.5, 0.999], dtype=torch.float64, device=dev)
+        return {"sites": T_SITES,
+                "mean_z_median_p999": [float(v) for v in torch.quantile(z_m[::8], q)],
+                "mean_frac_z_over_3.5": float((z_m > 3.5).double().mean()),
+                "var_z_median_p999": [float(v) for v in torch.quantile(z_v[::8], q)],
+                "var_frac_z_over_3.5": float((z_v > 3.5).double().mean()),
+                "expected_frac_z_over_3.5": 4.65e-4,
+                "how": "per-site mean and variance of h over each arm's whole timed chain; "
+                       "MCSE = sd / sqrt(ESS) (the variance's from the squared deviations)"}
+
     # headline: mixed precision (diagonal mass when given)
     # learned diagonal mass (untimed set-up): moments of the plain sampler over
     # n_snap trajectories, 2000 Adam steps, inverse mass, step tuned to ~0.8
@@ -535,7 +690,10 @@ def run_ours(args):
         b_ev.synchronize()
         m_med = float(torch.quantile((1.0 / tm.minv[::16]).float(), 0.5))
         mass_length = N_MD * DTAU * m_med ** 0.5
+        t1 = time.perf_counter()
         head_dt, head_nmd = learned.tune_step(ctx, h0, y, lnrv, th0, tm.minv, length=mass_length)
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - t1
         minv = tm.minv
         sampler = learned.MassSampler(ctx, minv, head_dt, head_nmd, DTAU, N_MD, window=100)
         m = (1.0 / minv).float()
@@ -546,88 +704,112 @@ def run_ours(args):
                         "loss_last": float(losses[-50:].mean()),
                         "m_quantiles": [float(v) for v in torch.quantile(
                             m[::16], torch.tensor([0.01, 0.5, 0.99], device=dev))],
+                        "tune_s": t_tune,
+                        "setup_s": t_snap + a_ev.elapsed_time(b_ev) / 1e3 + t_tune,
                         "dtau": head_dt, "n_md": head_nmd, "trajectory_length": mass_length}
 
     if minv is not None and mass_length is None:  # a mass from --mass-file
         mass_length = N_MD * DTAU * float(torch.quantile((1.0 / minv[::16]).float(), 0.5)) ** 0.5
     clocks = Clocks(local)
     head = arm("mixed", minv, args.warmup, args.steps, clocks=clocks, timing=True,
-               n_md=head_nmd, dtau=head_dt, sampler=sampler)
+               n_md=head_nmd, dtau=head_dt, sampler=sampler, moments=minv is not None,
+               nvtx=True)
     if learned_info is not None:
         learned_info["fell_back"] = bool(sampler.fell_back)
         learned_info["window_accept"] = [round(r, 3) for r in sampler.history]
     # comparisons: plain mixed and plain FP64 samplers (identity mass, 100 x 0.005)
-    ident = fp64 = batched = mn = levr = None
+    ident = fp64 = batched = mn = mn4 = levr = c1 = c4 = t2gpu = c5 = None
     if args.only != "mixed":
         if minv is not None:
-            ident = arm("mixed", None, min(args.warmup, 3), min(args.steps, 3))
-        fp64 = arm("fp64", None, min(args.warmup, 3), min(args.steps, 3))
+            ident = arm("mixed", None, min(args.warmup, 3), min(args.steps, 3), moments=True)
+            c5 = c5_compare(head, ident)
+        fp64 = arm("fp64", None, min(args.warmup, 3), min(args.steps, 3), timing=True)
         batched = batched_leg(max(3, min(args.steps, 10)))
         levr = leverage_leg(min(args.steps, 3))
+        c1 = c1_leg()
+        c4 = c4_leg()
+        t2gpu = table2_gpu(ctx, rsv, synth, torch, TABLE2_B_SHORT)
         # the minimum-norm integrator (two forces per step) at the plain
         # sampler's physical trajectory length (0.5; 0.5 sqrt(m) in the
         # learned mass's units):
         # the fewest steps whose acceptance over 40 trial trajectories
         # reaches 0.8, identity mass and learned mass
-        def tune_mn(mass, length):
+        def tune_mn(mass, length, tries):
             h_t = torch.tensor(s.h_true, device=dev)
             th_t = torch.tensor(s.theta, dtype=torch.float64, device=dev)
             acc_t = torch.empty(40, dtype=torch.int32, device=dev)
-            for n_try in (3, 4, 5, 6, 8, 10, 12, 15, 20, 30):
+            for n_try in tries:
                 rsv.rsv_hmc_chain(ctx, h_t.clone(), y, lnrv, th_t.clone(), n_try, length / n_try,
                                   40, prec="mixed", minv=mass, seed=123, accept_out=acc_t)
                 if float(acc_t.float().mean()) >= 0.8:
                     return n_try
-            return 30
-        rsv.rsv_set_integrator(ctx, "omelyan2")
-        try:
-            mn = {}
-            for tag, mass, length in (("identity", None, N_MD * DTAU),
-                                      ("learned", minv, mass_length)):
-                if tag == "learned" and mass is None:
-                    continue
-                n_mn = tune_mn(mass, length)
-                r = arm("mixed", mass, min(args.warmup, 3), min(args.steps, 3), n_md=n_mn,
-                        dtau=length / n_mn)
-                r["n_md"], r["dtau"] = n_mn, length / n_mn
-                mn[tag] = r
-        finally:
-            rsv.rsv_set_integrator(ctx, "leapfrog")
+            return tries[-1]
+        mn, mn4 = {}, {}
+        for integ, out, tries in (("omelyan2", mn, (3, 4, 5, 6, 8, 10, 12, 15, 20, 30)),
+                                  ("omelyan4", mn4, (2, 3, 4, 5, 6, 8, 10, 15))):
+            rsv.rsv_set_integrator(ctx, integ)
+            try:
+                for tag, mass, length in (("identity", None, N_MD * DTAU),
+                                          ("learned", minv, mass_length)):
+                    if tag == "learned" and mass is None:
+                        continue
+                    n_mn = tune_mn(mass, length, tries)
+                    r = arm("mixed", mass, min(args.warmup, 3), min(args.steps, 3), n_md=n_mn,
+                            dtau=length / n_mn)
+                    r["n_md"], r["dtau"] = n_mn, length / n_mn
+                    out[tag] = r
+            finally:
+                rsv.rsv_set_integrator(ctx, "leapfrog")
 
-    # end to end through the public API with host buffers: H2D of the step's
-    # inputs (h, y, lnRV, theta) from pinned memory, the chain, D2H of h' and
-    # the accept/dH records
+    # end to end through the public API with host buffers: the headline's own
+    # call (the same sampler, snapshots and theta records), its inputs (the
+    # chain state h and theta carried on the host between steps, y, lnRV)
+    # copied from pinned memory before and its results (h', theta and accept
+    # records) copied back after, every step inside the timed region; L2
+    # flushed between steps outside it, as for `value`
+    import dataclasses
+    e2e_sampler = dataclasses.replace(sampler, history=[], md_steps=0) if sampler else None
     h_host = torch.tensor(s.h_true).pin_memory()
     y_host = torch.tensor(s.y).pin_memory()
     l_host = torch.tensor(s.lnrv).pin_memory()
     th_host = torch.tensor(s.theta, dtype=torch.float64).pin_memory()
-    out_h = torch.empty_like(h_host).pin_memory()
+    out_th = torch.empty(N_TRAJ, 5, dtype=torch.float64).pin_memory()
     out_a = torch.empty(N_TRAJ, dtype=torch.int32).pin_memory()
-    out_d = torch.empty(N_TRAJ, dtype=torch.float64).pin_memory()
     hd = torch.empty(T_SITES, dtype=torch.float64, device=dev)
     yd = torch.empty_like(hd)
     ld = torch.empty_like(hd)
     thd = torch.empty(5, dtype=torch.float64, device=dev)
+    th_rec = torch.empty(N_TRAJ, 5, dtype=torch.float64, device=dev)
     e2e_steps = max(1, min(args.steps, 5))
+    e2e_ms, e2e_md = 0.0, 0
     _barrier(ws)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
     for k in range(e2e_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        md0 = e2e_sampler.md_steps if e2e_sampler else 0
+        e0.record()
         hd.copy_(h_host, non_blocking=True)
         yd.copy_(y_host, non_blocking=True)
         ld.copy_(l_host, non_blocking=True)
         thd.copy_(th_host, non_blocking=True)
-        rsv.rsv_hmc_chain(ctx, hd, yd, ld, thd, head_nmd, head_dt, N_TRAJ, prec="mixed",
-                          minv=minv, seed=99, traj0=k * N_TRAJ, accept_out=acc, dH_out=dH,
-                          update_theta=True)
-        out_h.copy_(hd, non_blocking=True)
+        if e2e_sampler is not None:
+            e2e_sampler.run(hd, yd, ld, thd, N_TRAJ, seed=99 + rank, traj0=k * N_TRAJ,
+                            snaps=snaps, theta_out=th_rec, accept_out=acc)
+        else:
+            rsv.rsv_hmc_chain(ctx, hd, yd, ld, thd, head_nmd, head_dt, N_TRAJ, prec="mixed",
+                              minv=minv, seed=99 + rank, traj0=k * N_TRAJ, snaps=snaps, thin=1,
+                              accept_out=acc, update_theta=True, theta_out=th_rec)
+        h_host.copy_(hd, non_blocking=True)
+        th_host.copy_(thd, non_blocking=True)
+        out_th.copy_(th_rec, non_blocking=True)
         out_a.copy_(acc, non_blocking=True)
-        out_d.copy_(dH, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_s = _barrier_max(ws, e0.elapsed_time(e1) / 1e3) / e2e_steps
+        e1.record()
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_md += (e2e_sampler.md_steps - md0) if e2e_sampler else head_nmd * N_TRAJ
+    e2e_s = _barrier_max(ws, e2e_ms / 1e3)
     h2d = 3 * T_SITES * 8 + 5 * 8
-    d2h = T_SITES * 8 + N_TRAJ * (4 + 8)
+    d2h = T_SITES * 8 + 5 * 8 + N_TRAJ * (5 * 8 + 4)
 
     # MD-only rate (the paper's elementary step): trajectory-kernel time at the
     # headline length minus that at one step, per leapfrog step, no theta update
@@ -662,19 +844,62 @@ def run_ours(args):
           "schedule": {"threads": nt_, "sites_per_thread": j_},
           "how": "k_traj_mixed time at n_md minus at n_md = 1, per step (CUDA events)"}
 
-    peaks, peak_kind = _peaks()
-    sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_clock_mhz * 1e6 / 1e12  # Top/s
+    # roofline of the headline's trajectory kernel: the method's algorithmic
+    # work (ALG_OPS FP32 operations + 1 exp per site and leapfrog step) over
+    # the launch's event time, against the FP32 and ex2 peaks measured above
     per_launch_s = head["traj_ms"] / 1e3 / max(head["traj_launches"], 1)
-    ops_per_launch = OPS_PER_SITE_STEP_MIXED * T_SITES * head_nmd
-    achieved = ops_per_launch / per_launch_s / 1e12
+    site_steps = T_SITES * head_nmd
+    achieved = ALG_OPS_PER_SITE_STEP * site_steps / per_launch_s
+    fp32_peak = pipe["fp32"]
+    ex2_rate = site_steps / per_launch_s
     # DRAM bytes (read + write) of one headline launch from the ncu capture in
     # profiles/, valid only for the kernel revision it was taken on
     from paper_1603_08114_gb300 import autotune as _at
     traffic = TRAFFIC["bytes"] if TRAFFIC["kernel_rev"] == _at.KERNEL_REV else None
+    fp64_roof = None
+    if fp64 is not None:
+        f_launch = fp64["traj_ms"] / 1e3 / max(fp64["traj_launches"], 1)
+        fp64_ach = ALG_OPS_PER_SITE_STEP * T_SITES * N_MD / f_launch
+        fp64_roof = {"bound": "fp64", "achieved": fp64_ach / 1e12, "peak": pipe["dfma"] / 1e12,
+                     "unit": "Top/s", "frac": fp64_ach / pipe["dfma"],
+                     "per_launch_ms": f_launch * 1e3, "peak_kind": "measured DFMA rate"}
 
     if rank == 0:
         cpu = cpu_baseline() if (ws == 1 and not args.no_cpu) else None
+        t2 = None
+        if t2gpu is not None:
+            t2cpu = table2_cpu(TABLE2_B_SHORT) if (ws == 1 and not args.no_cpu) else None
+            t2 = table2_summary(TABLE2_B_SHORT, t2gpu, t2cpu)
+
+        def arm_summary(r, extra=None):
+            if r is None:
+                return None
+            d = {"site_updates_per_s": r["site_updates_per_s"], "n_md": r["n_md"],
+                 "dtau": r["dtau"], "ms_per_step": r["ms_per_step"], "draws": r["draws"],
+                 "ess_h_median_per_s": r["ess_h_median_per_s"],
+                 "ess_h_min_per_s": r["ess_h_min_per_s"],
+                 "ess_theta_per_s": r["ess_theta_per_s"], "accept_rate": r["accept_rate"]}
+            d.update(extra or {})
+            return d
+
+        learned_cmp = None
+        if learned_info is not None and ident is not None:
+            setup = learned_info["setup_s"]
+            ess_l = head["ess_h_median_per_s"] * head["timed_s"]
+            learned_cmp = {
+                "ess_h_median_per_s": {"learned": head["ess_h_median_per_s"],
+                                       "identity": ident["ess_h_median_per_s"]},
+                "ess_theta_per_s": {"learned": head["ess_theta_per_s"],
+                                    "identity": ident["ess_theta_per_s"]},
+                "equal_posterior_moments": c5,
+                "setup_s": setup,
+                "learned_ess_h_median_per_s_with_setup_over_timed_chain":
+                    ess_l / (head["timed_s"] + setup),
+                "learned_ess_h_median_per_s_with_setup_over_1e5_trajectories":
+                    ess_l / (head["timed_s"] + setup * head["draws"] / 1e5),
+                "gain_h_median": head["ess_h_median_per_s"] / ident["ess_h_median_per_s"],
+                "note": "the learned mass gains only if gain_h_median > 1: the posterior "
+                        "variance of this workload is nearly the same at every site"}
         line = {
             "metric": METRIC, "value": head["site_updates_per_s"], "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -687,46 +912,51 @@ def run_ours(args):
                        "parallelism": f"replicas{ws}"},
             "ess": {"h_median_per_s": head["ess_h_median_per_s"],
                     "h_min_per_s": head["ess_h_min_per_s"],
-                    "h_median_per_step": head["ess_h_median"],
-                    "h_min_per_step": head["ess_h_min"],
-                    "theta_per_s": head["ess_theta_per_s"],
-                    "theta_per_step": head["ess_theta_per_step"],
-                    "accept_rate": head["accept_rate"]},
-            "fp64_plain": None if fp64 is None else {
-                "site_updates_per_s": fp64["site_updates_per_s"],
-                "ms_per_step": fp64["ms_per_step"],
-                "ess_h_median_per_s": fp64["ess_h_median_per_s"],
-                "ess_h_min_per_s": fp64["ess_h_min_per_s"],
-                "ess_theta_per_s": fp64["ess_theta_per_s"],
-                "accept_rate": fp64["accept_rate"]},
-            "batched": batched,
+                    "h_median": head["ess_h_median"], "h_min": head["ess_h_min"],
+                    "theta_per_s": head["ess_theta_per_s"], "theta": head["ess_theta"],
+                    "draws": head["draws"], "accept_rate": head["accept_rate"],
+                    "how": "Geyer ESS over the whole timed chain (steps x 200 draws) / the "
+                           "chain's summed step time"},
+            "fp64_plain": arm_summary(fp64, {"roofline": fp64_roof}),
+            "mixed_identity": arm_summary(ident),
             "learned": learned_info,
-            "mixed_identity": None if ident is None else {
-                "site_updates_per_s": ident["site_updates_per_s"], "n_md": N_MD, "dtau": DTAU,
-                "ms_per_step": ident["ms_per_step"],
-                "ess_h_median_per_s": ident["ess_h_median_per_s"],
-                "ess_h_min_per_s": ident["ess_h_min_per_s"],
-                "ess_theta_per_s": ident["ess_theta_per_s"],
-                "accept_rate": ident["accept_rate"]},
+            "learned_vs_identity": learned_cmp,
+            "c1": c1, "c4": c4, "table2": t2,
+            "batched": batched,
             "leverage": levr,
             "mixed_omelyan2": None if mn is None else {
-                tag: {"integrator": "minimum-norm (Omelyan), 2 force evaluations per step",
-                      "mass": tag, "n_md": r["n_md"], "dtau": r["dtau"],
-                      "force_evaluations_per_trajectory": 2 * r["n_md"],
-                      "ms_per_step": r["ms_per_step"],
-                      "ess_h_median_per_s": r["ess_h_median_per_s"],
-                      "ess_h_min_per_s": r["ess_h_min_per_s"],
-                      "ess_theta_per_s": r["ess_theta_per_s"],
-                      "accept_rate": r["accept_rate"]} for tag, r in mn.items()},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
-                         "frac": achieved / alu_peak, "traffic": traffic,
-                         "kernel": "k_traj_mixed", "peak_kind": "nominal FP32-lane issue "
-                         f"rate 152 SM x 128 x {sm_clock_mhz:.0f} MHz",
-                         "per_launch_ms": per_launch_s * 1e3},
+                tag: arm_summary(r, {"integrator": "minimum-norm (Omelyan), 2 force "
+                                                   "evaluations per step", "mass": tag,
+                                     "force_evaluations_per_trajectory": 2 * r["n_md"]})
+                for tag, r in mn.items()},
+            "mixed_omelyan4": None if mn4 is None else {
+                tag: arm_summary(r, {"integrator": "fourth-order minimum-norm (Omelyan), 4 "
+                                                   "force evaluations per step", "mass": tag,
+                                     "force_evaluations_per_trajectory": 4 * r["n_md"]})
+                for tag, r in mn4.items()},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
+                         "unit": "Top/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                         "kernel": "k_traj_mixed",
+                         "peak_kind": "measured FP32 FMA rate (rsv_pipe_probe, the larger of "
+                                      "FFMA and FFMA2), this run",
+                         "per_launch_ms": per_launch_s * 1e3,
+                         "algorithmic_ops_per_site_step": ALG_OPS_PER_SITE_STEP,
+                         "site_steps_per_launch": site_steps,
+                         "issued_ops_per_site_step": IMPL_OPS_PER_SITE_STEP_MIXED,
+                         "issued_frac": achieved / fp32_peak * IMPL_OPS_PER_SITE_STEP_MIXED
+                         / ALG_OPS_PER_SITE_STEP,
+                         "ex2": {"achieved": ex2_rate / 1e12, "peak": pipe["ex2"] / 1e12,
+                                 "frac": ex2_rate / pipe["ex2"]},
+                         "md_only_frac": ALG_OPS_PER_SITE_STEP * T_SITES
+                         / (md["us_per_step"] * 1e-6) / fp32_peak},
+            "pipe_peaks": {"unit": "T op/s (lds: TB/s)",
+                           **{k: (v / 1e12 if isinstance(v, float) else v)
+                              for k, v in pipe.items()}},
             "cpu_baseline": cpu,
             "md_only": md,
-            "e2e": {"value": ws * T_SITES * head_nmd * N_TRAJ / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": ws * T_SITES * e2e_md / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
             "gpu_launches": head["launches"],
             "clocks": clocks.summary(),
         }
@@ -744,6 +974,7 @@ def run_ours(args):
 PAPER_TABLE2 = {"gpu": {"A": 1.13e-5, "C": 2.25e-7}, "cpu": {"A": -1.42e-6, "C": 3.87e-6},
                 "gain_limit": 17.2, "hardware": "GTX 760 / i7-4770 3.4 GHz, FP32"}
 TABLE2_B = (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048)
+TABLE2_B_SHORT = (1, 8, 64, 512, 2048)   # the ladder of the default run
 
 
 def fit_linear(B, f):
@@ -754,20 +985,13 @@ def fit_linear(B, f):
     return float(A), float(C)
 
 
-def run_table2(args):
-    """Time per elementary step vs B on this GPU (mixed and FP64 paths: the
-    trajectory kernel's time at two lengths on one tiling, per extra step) and
-    for the oracle's leapfrog on one host core; both fitted like Table 2."""
-    import torch
-
-    from paper_1603_08114_gb300 import rsv, synth
-    import oracle
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    ctx = rsv.Context(0)
-    n_lo, n_hi = 10, 110
-    res = {"B": list(TABLE2_B), "gpu_mixed": [], "gpu_fp64": [], "cpu_oracle": []}
-    for B in TABLE2_B:
+def table2_gpu(ctx, rsv, synth, torch, B_list, n_lo=10, n_hi=110):
+    """Seconds per elementary MD step (one leapfrog step over all T = 512 B
+    sites) of the mixed and FP64 trajectory kernels: the kernel's time at
+    n_hi steps minus at n_lo on one tiling, over n_hi - n_lo (CUDA events)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    res = {"gpu_mixed": [], "gpu_fp64": []}
+    for B in B_list:
         T = 512 * B
         s = synth.rsv_series(T, synth.THETA_STD, seed=1)
         y = torch.tensor(s.y, device=dev)
@@ -780,44 +1004,74 @@ def run_table2(args):
             if T > nt * j - 2 * (n_hi + 1) - 3:  # a tiled series: one tile size for both lengths
                 rsv.rsv_set_schedule(ctx, nt, j, nt * j - 2 * (n_hi + 1) - 3)
             times = []
-            for n_md in (n_lo, n_hi):
-                h = torch.tensor(s.h_true, device=dev)
-                th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
-                n = 10 if prec == "mixed" else 2
-                rsv.rsv_hmc_chain(ctx, h, y, lr, th, n_md, 0.005, 2, prec=prec, seed=1)
-                torch.cuda.synchronize()
-                rsv.rsv_stats(ctx, reset=True)
-                rsv.rsv_timing(ctx, True)
-                rsv.rsv_hmc_chain(ctx, h, y, lr, th, n_md, 0.005, n, prec=prec, seed=2)
-                torch.cuda.synchronize()
-                rsv.rsv_timing(ctx, False)
-                _, nl, ms = rsv.rsv_stats(ctx, reset=True)
-                times.append(ms / 1e3 / max(nl, 1))
-            rsv.rsv_set_schedule(ctx)
+            try:
+                for n_md in (n_lo, n_hi):
+                    h = torch.tensor(s.h_true, device=dev)
+                    th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
+                    n = 10 if prec == "mixed" else 2
+                    rsv.rsv_hmc_chain(ctx, h, y, lr, th, n_md, 0.005, 2, prec=prec, seed=1)
+                    torch.cuda.synchronize()
+                    rsv.rsv_stats(ctx, reset=True)
+                    rsv.rsv_timing(ctx, True)
+                    rsv.rsv_hmc_chain(ctx, h, y, lr, th, n_md, 0.005, n, prec=prec, seed=2)
+                    torch.cuda.synchronize()
+                    rsv.rsv_timing(ctx, False)
+                    _, nl, ms = rsv.rsv_stats(ctx, reset=True)
+                    times.append(ms / 1e3 / max(nl, 1))
+            finally:
+                rsv.rsv_set_schedule(ctx)
             res["gpu_" + prec].append((times[1] - times[0]) / (n_hi - n_lo))
-        # oracle: leapfrog steps on the host, one core
+    return res
+
+
+def table2_cpu(B_list):
+    """Seconds per elementary step of the FP64 oracle's leapfrog on one host
+    core, T = 512 B (part of the CPU baseline: the oracle as it stands)."""
+    import oracle
+    from paper_1603_08114_gb300 import synth
+    out = []
+    for B in B_list:
+        T = 512 * B
+        s = synth.rsv_series(T, synth.THETA_STD, seed=1)
         p0 = synth.standard_normals(T, 5)
         n_steps = max(2, min(200, int(2e6 // T)))
         t0 = time.perf_counter()
         oracle.leapfrog(s.h_true, p0, s.y, s.lnrv, s.theta, n_steps, 0.005)
-        res["cpu_oracle"].append((time.perf_counter() - t0) / n_steps)
-    fits = {k: dict(zip(("A", "C"), fit_linear(res["B"], res[k])))
-            for k in ("gpu_mixed", "gpu_fp64", "cpu_oracle")}
-    line = {
-        "table2": {
-            "T": [512 * b for b in TABLE2_B], **res,
-            "unit": "seconds per elementary step (one leapfrog step over all T sites)",
-            "fit": fits,
-            "gain_limit_mixed_vs_oracle": fits["cpu_oracle"]["C"] / fits["gpu_mixed"]["C"],
-            "gain_limit_fp64_vs_oracle": fits["cpu_oracle"]["C"] / fits["gpu_fp64"]["C"],
-            "site_updates_per_s_at_2048": 512 * 2048 / res["gpu_mixed"][-1],
-            "paper": PAPER_TABLE2,
-            "how": "GPU: k_traj_mixed / k_traj_fp64 time at n_md = 110 minus at n_md = 10 "
-                   "(one tiling, CUDA events) / 100; oracle: FP64 leapfrog in plain C on "
-                   "one host core; FP64 oracle vs the paper's FP32 CPU code",
-        }
-    }
-    print(json.dumps(line))
+        out.append((time.perf_counter() - t0) / n_steps)
+    return out
+
+
+def table2_summary(B_list, gpu, cpu):
+    res = {"B": list(B_list), "T": [512 * b for b in B_list], **gpu}
+    keys = ["gpu_mixed", "gpu_fp64"]
+    if cpu is not None:
+        res["cpu_oracle"] = cpu
+        keys.append("cpu_oracle")
+    fits = {k: dict(zip(("A", "C"), fit_linear(B_list, res[k]))) for k in keys}
+    res.update({
+        "unit": "seconds per elementary step (one leapfrog step over all T sites)",
+        "fit": fits,
+        "site_updates_per_s_at_largest_B": 512 * B_list[-1] / res["gpu_mixed"][-1],
+        "paper": PAPER_TABLE2,
+        "how": "GPU: k_traj_mixed / k_traj_fp64 time at n_md = 110 minus at n_md = 10 "
+               "(one tiling, CUDA events) / 100; oracle: FP64 leapfrog in plain C on one "
+               "host core; fitted f(B) = A + C B like the paper's Table 2"})
+    if cpu is not None:
+        res["gain_limit_mixed_vs_oracle"] = fits["cpu_oracle"]["C"] / fits["gpu_mixed"]["C"]
+        res["gain_limit_fp64_vs_oracle"] = fits["cpu_oracle"]["C"] / fits["gpu_fp64"]["C"]
+    return res
+
+
+def run_table2(args):
+    """The full B ladder of the elementary-step sweep (1 ... 2048)."""
+    import torch
+
+    from paper_1603_08114_gb300 import rsv, synth
+    torch.cuda.set_device(0)
+    ctx = rsv.Context(0)
+    gpu = table2_gpu(ctx, rsv, synth, torch, TABLE2_B)
+    cpu = table2_cpu(TABLE2_B)
+    print(json.dumps({"table2": table2_summary(TABLE2_B, gpu, cpu)}))
     ctx.close()
     return 0
 

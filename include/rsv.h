@@ -110,9 +110,21 @@ rsv_status rsv_set_schedule(rsv_ctx* ctx, int threads, int sites_per_thread, int
  *                force step split in two.
  * With RSV_OMELYAN2 a tile's halo and the `tile` bound of rsv_set_schedule
  * count 2 n_md force evaluations instead of n_md.  lambda > 1/2 or NaN gives
- * RSV_EINVAL. */
-typedef enum rsv_integrator { RSV_LEAPFROG = 0, RSV_OMELYAN2 = 1 } rsv_integrator;
+ * RSV_EINVAL (RSV_OMELYAN2 only). */
+typedef enum rsv_integrator { RSV_LEAPFROG = 0, RSV_OMELYAN2 = 1, RSV_OMELYAN4 = 2 } rsv_integrator;
 #define RSV_OMELYAN2_LAMBDA 0.19318332750378357
+/* RSV_OMELYAN4: the fourth-order force-gradient-free integrator of Omelyan,
+ * Mryglod and Folk (Comput. Phys. Commun. 146, 188, 2002), their minimum-norm
+ * position-extended Forest-Ruth-like scheme: per step
+ *   h += XI dtau p/m;  p -= (1 - 2 LAMBDA)/2 dtau dS/dh;  h += CHI dtau p/m;
+ *   p -= LAMBDA dtau dS/dh;  h += (1 - 2 (CHI + XI)) dtau p/m;  p -= LAMBDA dtau dS/dh;
+ *   h += CHI dtau p/m;  p -= (1 - 2 LAMBDA)/2 dtau dS/dh;  h += XI dtau p/m
+ * with the constants below -- four force evaluations per step, energy error
+ * O(dtau^4).  Its `lambda` argument is ignored; a tile's halo and the `tile`
+ * bound of rsv_set_schedule count 4 n_md force evaluations. */
+#define RSV_OMELYAN4_XI 0.1786178958448091
+#define RSV_OMELYAN4_LAMBDA (-0.2123418310626054)
+#define RSV_OMELYAN4_CHI (-0.06626458266981849)
 rsv_status rsv_set_integrator(rsv_ctx* ctx, rsv_integrator kind, double lambda);
 
 /* ---- model: leverage -------------------------------------------------------

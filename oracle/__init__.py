@@ -70,6 +70,8 @@ def lib():
                                        ctypes.c_double]
             L.orc_omelyan2.argtypes = [_D, _D, _D, _D, ctypes.c_long, Theta, _D, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double]
+            L.orc_omelyan4.argtypes = [_D, _D, _D, _D, ctypes.c_long, Theta, _D, ctypes.c_int,
+                                       ctypes.c_double]
             L.orc_delta_H.restype = ctypes.c_double
             L.orc_delta_H.argtypes = [_D, _D, _D, _D, _D, _D, ctypes.c_long, Theta, _D]
             L.orc_metropolis.restype = ctypes.c_int
@@ -170,7 +172,13 @@ def metropolis(dH, log_u) -> int:
 # c = (2 sqrt(326) + 36)^(1/3), of its error-norm minimisation
 LAMBDA_2MN = 0.19318332750378357
 
-_INTEGRATORS = {"leapfrog": 0, "omelyan2": 1}
+_INTEGRATORS = {"leapfrog": 0, "omelyan2": 1, "omelyan4": 2}
+
+# The fourth-order minimum-norm scheme of Omelyan, Mryglod and Folk, Comput.
+# Phys. Commun. 146, 188 (2002): drift coefficients (xi, chi, 1 - 2(chi + xi),
+# chi, xi), kick coefficients ((1 - 2 lambda)/2, lambda, lambda, (1 - 2 lambda)/2).
+PEFRL = {"xi": 0.1786178958448091, "lambda": -0.2123418310626054,
+         "chi": -0.06626458266981849}
 
 
 def omelyan2(h, p, y, lnrv, th, n_md, dtau, lam=LAMBDA_2MN, minv=None):
@@ -180,6 +188,16 @@ def omelyan2(h, p, y, lnrv, th, n_md, dtau, lam=LAMBDA_2MN, minv=None):
     mv = None if minv is None else _f64(minv)
     lib().orc_omelyan2(_d(h), _d(p), _d(y), _d(lnrv), len(h), theta(th), _d(mv), int(n_md),
                        float(dtau), float(lam))
+    return h, p
+
+
+def omelyan4(h, p, y, lnrv, th, n_md, dtau, minv=None):
+    """n_md steps of the fourth-order scheme (four forces per step); returns (h', p')."""
+    h, p = _f64(h).copy(), _f64(p).copy()
+    y, lnrv = _f64(y), _f64(lnrv)
+    mv = None if minv is None else _f64(minv)
+    lib().orc_omelyan4(_d(h), _d(p), _d(y), _d(lnrv), len(h), theta(th), _d(mv), int(n_md),
+                       float(dtau))
     return h, p
 
 

@@ -185,13 +185,48 @@ void orc_omelyan2(double* h, double* p, const double* y, const double* lnrv,
     free(F);
 }
 
+/* n_md steps of the fourth-order force-gradient-free integrator of Omelyan,
+ * Mryglod and Folk (Comput. Phys. Commun. 146, 188 (2002)), their
+ * position-extended Forest-Ruth-like scheme with the minimum error norm,
+ * taken literally: per step five drifts and four kicks
+ *   h += xi dtau p/m;  p -= (1 - 2 lambda)/2 dtau dS/dh;  h += chi dtau p/m;
+ *   p -= lambda dtau dS/dh;  h += (1 - 2 (chi + xi)) dtau p/m;
+ *   p -= lambda dtau dS/dh;  h += chi dtau p/m;
+ *   p -= (1 - 2 lambda)/2 dtau dS/dh;  h += xi dtau p/m,
+ * with their published constants xi, lambda, chi (the drifts and the kicks
+ * each sum to 1; the scheme is symmetric, so reversible). */
+#define ORC_PEFRL_XI 0.1786178958448091
+#define ORC_PEFRL_LAMBDA (-0.2123418310626054)
+#define ORC_PEFRL_CHI (-0.06626458266981849)
+void orc_omelyan4(double* h, double* p, const double* y, const double* lnrv,
+                  long T, orc_theta th, const double* minv, int n_md, double dtau)
+{
+    double* F = (double*)malloc(sizeof(double) * (size_t)(T > 0 ? T : 1));
+    const double xi = ORC_PEFRL_XI, lam = ORC_PEFRL_LAMBDA, chi = ORC_PEFRL_CHI;
+    const double a[5] = {xi, chi, 1.0 - 2.0 * (chi + xi), chi, xi};
+    const double b[4] = {0.5 * (1.0 - 2.0 * lam), lam, lam, 0.5 * (1.0 - 2.0 * lam)};
+    for (int k = 0; k < n_md; ++k) {
+        for (int s = 0; s < 5; ++s) {
+            const double cd = a[s] * dtau;
+            for (long t = 0; t < T; ++t) h[t] = h[t] + cd * (minv ? minv[t] * p[t] : p[t]);
+            if (s == 4) break;
+            orc_force(h, y, lnrv, T, th, F);
+            const double ck = b[s] * dtau;
+            for (long t = 0; t < T; ++t) p[t] = p[t] - ck * F[t];
+        }
+    }
+    free(F);
+}
+
 /* The integrator of a trajectory: 0 = leapfrog (eqs. (6)-(8)), 1 = the
- * minimum-norm integrator above with the given lambda. */
+ * minimum-norm integrator above with the given lambda, 2 = the fourth-order
+ * scheme above. */
 static void orc_integrate(double* h, double* p, const double* y, const double* lnrv, long T,
                           orc_theta th, const double* minv, int n_md, double dtau,
                           int integrator, double lambda)
 {
-    if (integrator == 1) orc_omelyan2(h, p, y, lnrv, T, th, minv, n_md, dtau, lambda);
+    if (integrator == 2) orc_omelyan4(h, p, y, lnrv, T, th, minv, n_md, dtau);
+    else if (integrator == 1) orc_omelyan2(h, p, y, lnrv, T, th, minv, n_md, dtau, lambda);
     else orc_leapfrog(h, p, y, lnrv, T, th, minv, n_md, dtau);
 }
 

@@ -180,6 +180,11 @@ rsv_status rsv_set_integrator(rsv_ctx* c, rsv_integrator kind, double lambda)
         c->lambda = 0.0;
         return RSV_OK;
     }
+    if (kind == RSV_OMELYAN4) {
+        c->integrator = 2;
+        c->lambda = 0.0;
+        return RSV_OK;
+    }
     if (kind != RSV_OMELYAN2) return fail(RSV_EINVAL, "unknown integrator");
     if (!(lambda <= 0.5) || lambda != lambda) return fail(RSV_EINVAL, "lambda must be <= 1/2");
     c->integrator = 1;

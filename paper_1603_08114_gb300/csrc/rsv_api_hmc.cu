@@ -165,6 +165,8 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
     a.n_md = P.n_md;
     a.integrator = P.integrator;
     a.lambda = P.lambda;
+    a.sch = make_scheme(P.integrator, P.lambda);
+    a.msch = make_mixed_scheme(P.integrator, P.lambda, o.dtau);
     a.rho = c->rho;
     a.dtau = o.dtau;
     a.seed = o.seed;

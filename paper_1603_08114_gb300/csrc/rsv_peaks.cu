@@ -92,6 +92,8 @@ __global__ void __launch_bounds__(kProbeThreads, kProbeBlocksPerSm)
 // Shared-memory loads: each thread reads 16-byte words from a block-wide
 // array at an index that moves with the iteration (consecutive lanes,
 // consecutive words: no bank conflicts), adding them with packed FP32 adds.
+// The loads are volatile: the same four addresses repeat, and plain loads of
+// an unchanged address may be merged by the compiler.
 __global__ void __launch_bounds__(kProbeThreads, kProbeBlocksPerSm)
     k_probe_lds(int64_t iters, float a, float b, float* sink)
 {
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(kProbeThreads, kProbeBlocksPerSm)
             const int idx = (threadIdx.x + (int)((i * 16 + k) & (kLdsFloat4PerThread - 1)) *
                                                kProbeThreads);
             float4 v;
-            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+            asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                          : "r"((unsigned)__cvta_generic_to_shared(buf + idx)));
             s0 = __fadd2_rn(s0, make_float2(v.x, v.y));

@@ -65,7 +65,7 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
                Plan& P, const char** why)
 {
     // one site of staleness per force evaluation
-    const int64_t K = (int64_t)n_md * (integrator == 1 ? 2 : 1) + 1;
+    const int64_t K = (int64_t)n_md * make_scheme(integrator, lambda).nk + 1;
     const size_t smem_cap = 227 * 1024;
     if (n < 1) {
         *why = "no series";

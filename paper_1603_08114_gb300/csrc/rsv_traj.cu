@@ -393,19 +393,16 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
         double E0 = 0.0, E1 = 0.0;
         owned_energy(E0);
 
-        // Per step, drifts and kicks in the literal order: leapfrog eqs. (6)-(8)
-        // (drift dtau/2, kick dtau, drift dtau/2) or the minimum-norm integrator
-        // (drift lambda dtau, kick dtau/2, drift (1-2 lambda) dtau, kick dtau/2,
-        // drift lambda dtau).
-        const double dt = A.dtau, hd = 0.5 * A.dtau;
-        const bool mn = A.integrator == 1;
-        const int nk = mn ? 2 : 1;
-        const double d_end = mn ? A.lambda * dt : hd, d_mid = (1.0 - 2.0 * A.lambda) * dt;
-        const double kick = mn ? hd : dt;
+        // Per step, drifts and kicks in the literal order of the scheme: the
+        // leapfrog eqs. (6)-(8) (drift dtau/2, kick dtau, drift dtau/2) or a
+        // minimum-norm integrator (Scheme: drift a_0 dtau, then {kick b_k
+        // dtau; drift a_{k+1} dtau}).
+        const double dt = A.dtau;
+        const int nk = A.sch.nk;
         for (int k = 0; k < A.n_md; ++k) {
             for (int st = 0; st <= nk; ++st) {
                 // eq. (6)/(8): h += c dtau p / m
-                const double cd = (st == 0 || st == nk) ? d_end : d_mid;
+                const double cd = A.sch.a[st] * dt;
 #pragma unroll
                 for (int j = 0; j < J; ++j)
                     x[j] = fma(MASS ? cd * s_mi[j * NT + tid] : cd, p[j], x[j]);
@@ -422,6 +419,7 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
                     if (!v.first) eprev = fma(-rs, yL * exp(-0.5 * xL), eprev);
                 }
                 // eq. (7): p -= kick dS/dh
+                const double kick = A.sch.b[st] * dt;
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     double f = fma(iu, x[j], s_kc[j * NT + tid]);
@@ -500,10 +498,11 @@ __device__ float2 g_exptab[32];
 // Per-block constants of the leapfrog of one segment.
 struct MixedConst {
     float phi, c0, c1, cmu, dt;
-    // integrator as substeps {kick; drift}: kick size, drift ratios (to dtau)
-    // of even / odd / last substeps, substep count (see mixed_steps)
-    float kick, r_even, r_odd, r_last;
-    int n_sub;
+    // integrator as substeps {kick; drift} (MixedScheme): kick sizes kq (a
+    // mass's -kick/m holds kick = kq[0], scaled by kr), drift ratios (to
+    // dtau) r, the last substep's r_last; nk substeps per step, n_sub in all
+    float kick, kq[4], kr[4], r[4], r_last;
+    int nk, n_sub;
     int la;        // slot of the series' last site in this thread (or out of [0, J))
     bool first;    // this thread holds the series' first site in slot 0
     // leverage: v of the left neighbour site (0 at a window start), and the
@@ -555,7 +554,7 @@ __device__ __forceinline__ void cupd2(float2& hi, float2& lo, float2 c, float2 u
 // d_t^2), and cst x_0 at the series' first site, where the stationary row
 // (1-phi^2) x_0/s_eta^2 differs from the ghost's B (1-phi^2) x_0.
 // e^{-h} is taken as (e^{-h/2})^2 from one ex2.  s_v: float2 [P][NT] of v.
-template <int J, bool MASS, bool EDGE, bool LEV>
+template <int J, bool MASS, bool EDGE, bool LEV, bool KV>
 __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J / 2],
                                             float2 (&PH)[J / 2], float2 (&PL)[J / 2],
                                             const float4* __restrict__ s_ak,
@@ -571,6 +570,9 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
     const float2 half = f2(0.5f, 0.5f), phi2 = f2(c.phi, c.phi), nphi2 = f2(-c.phi, -c.phi);
     const float2 zero = f2(0.0f, 0.0f);
     const float2 ndt = f2(-c.kick, -c.kick);
+    // KV (kick sizes vary within a step): this substep's -kick, or with a
+    // mass the ratio of its kick to the one -kick/m in s_dm holds
+    float2 kc = MASS ? f2(1.0f, 1.0f) : ndt;
     // The edge exchange overlaps the interior pairs 1..P-2, which need no
     // neighbour from another thread: the edges are published (warp shuffles,
     // the warps' end values to shared memory), the interior pairs advance, and
@@ -609,7 +611,9 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
         }
         // with a mass the state holds the velocity v = p/m: the kick takes
         // the per-site -kick/m, the drift is the same for every site
-        cupd2(PH[q], PL[q], MASS ? s_dm[q * NT + tid] : ndt, f);
+        const float2 km = MASS ? (KV ? fma2(s_dm[q * NT + tid], kc, zero) : s_dm[q * NT + tid])
+                               : (KV ? kc : ndt);
+        cupd2(PH[q], PL[q], km, f);
         cupd2(X[q], XL[q], cx, PH[q]);
         return w;
     };
@@ -623,7 +627,21 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
         if (lane == 31) edge[2 * warp + 1] = last;
         const float xP = X[0].y;  // x_P before the step
         const float2 x1 = X[1];   // pair 1 before the step (pair 0's right neighbours)
-        const float hs = (k + 1 < c.n_sub) ? ((k & 1) ? c.r_odd : c.r_even) : c.r_last;
+        const int ks = k & (c.nk - 1);  // nk = 1, 2 or 4
+        float rk;
+        if (KV) {
+            rk = ks == 0 ? c.r[0] : ks == 1 ? c.r[1] : ks == 2 ? c.r[2] : c.r[3];
+            if (MASS) {
+                const float kr = ks == 0 ? c.kr[0] : ks == 1 ? c.kr[1] : ks == 2 ? c.kr[2] : c.kr[3];
+                kc = f2(kr, kr);
+            } else {
+                const float kq = ks == 0 ? c.kq[0] : ks == 1 ? c.kq[1] : ks == 2 ? c.kq[2] : c.kq[3];
+                kc = f2(-kq, -kq);
+            }
+        } else {
+            rk = ks ? c.r[1] : c.r[0];
+        }
+        const float hs = (k + 1 < c.n_sub) ? rk : c.r_last;
         const float2 cx = f2(hs * c.dt, hs * c.dt);
         // leverage: e^{-h/2} of pairs 0 and P-1 before the step, and w of pair 0
         float2 e2_0 = zero, e2_last = zero, prevw = zero;
@@ -976,17 +994,22 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
             mc.c1 = mt.c1;
             mc.cmu = mt.cmu;
             mc.dt = dt;
-            // substeps: leapfrog {kick dtau; drift dtau (last dtau/2)} after a
-            // first drift of dtau/2; minimum-norm {kick dtau/2; drift
-            // (1-2 lambda) dtau or 2 lambda dtau alternately (last lambda dtau)}
-            // after a first drift of lambda dtau (its two end drifts merged)
-            const bool mn = A.integrator == 1;
-            const float lam = (float)A.lambda;
-            mc.kick = mn ? 0.5f * dt : dt;
-            mc.r_even = mn ? 1.0f - 2.0f * lam : 1.0f;
-            mc.r_odd = mn ? 2.0f * lam : 1.0f;
-            mc.r_last = mn ? lam : 0.5f;
-            mc.n_sub = mn ? 2 * A.n_md : A.n_md;
+            // substeps {kick; drift} of the scheme after its first drift (the
+            // end drifts of consecutive steps merged): leapfrog {kick dtau;
+            // drift dtau (last dtau/2)} after dtau/2; second-order minimum-norm
+            // {kick dtau/2; drift (1-2 lambda) dtau or 2 lambda dtau} after
+            // lambda dtau; fourth-order four kicks and drifts per step
+            const MixedScheme& ms = A.msch;
+            mc.kick = ms.kick;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                mc.kq[i] = ms.kq[i];
+                mc.kr[i] = ms.kr[i];
+                mc.r[i] = ms.r[i];
+            }
+            mc.r_last = ms.r_last;
+            mc.nk = ms.nk;
+            mc.n_sub = ms.nk * A.n_md;
             mc.la = v.n - 1 - base;
             mc.first = v.first;
             const int64_t off = v.si.off, wlo = v.g.wlo;
@@ -1119,19 +1142,28 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_traj_mixed(const 
                 PH[q] = f2(s_ph[q * NS + tid], s_ph[(q + P) * NS + tid]);
                 PL[q] = f2(0.0f, 0.0f);
             }
-            const float r0 = A.integrator == 1 ? (float)A.lambda : 0.5f;  // first drift
+            const float r0 = A.msch.r_first;  // first drift
 #pragma unroll
             for (int q = 0; q < P; ++q) cupd2(X[q], XL[q], f2(r0 * dt, r0 * dt), PH[q]);
         }
 
         int par = 0;
         const bool mid_end = mc.la >= 0 && mc.la < J - 1;
-        if (__any_sync(0xffffffffu, mid_end))
-            mixed_steps<J, MASS, true, LEV>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par, nw,
-                                            A.n_md, mc);
-        else
-            mixed_steps<J, MASS, false, LEV>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par, nw,
-                                             A.n_md, mc);
+        if (__any_sync(0xffffffffu, mid_end)) {
+            if (A.msch.kv)
+                mixed_steps<J, MASS, true, LEV, true>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par,
+                                                      nw, A.n_md, mc);
+            else
+                mixed_steps<J, MASS, true, LEV, false>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge,
+                                                       par, nw, A.n_md, mc);
+        } else {
+            if (A.msch.kv)
+                mixed_steps<J, MASS, false, LEV, true>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge,
+                                                       par, nw, A.n_md, mc);
+            else
+                mixed_steps<J, MASS, false, LEV, false>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge,
+                                                        par, nw, A.n_md, mc);
+        }
 
         // ---- the end of the trajectory: state -> shared memory (x over the
         // start's slots, p lo over k, which the leapfrog no longer needs) ----

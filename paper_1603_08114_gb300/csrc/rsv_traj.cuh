@@ -10,6 +10,79 @@
 
 namespace rsv {
 
+// A molecular-dynamics integrator as a symmetric composition: per step
+// drift a[0] dtau, then nk times {kick b[k] dtau; drift a[k+1] dtau}
+// (h += c dtau p/m, p -= c dtau dS/dh).  integrator 0: the leapfrog of
+// eqs. (6)-(8) (a = 1/2, 1/2; b = 1); 1: the second-order minimum-norm scheme
+// of Omelyan, Mryglod and Folk (a = lambda, 1 - 2 lambda, lambda; b = 1/2,
+// 1/2); 2: their fourth-order minimum-norm scheme without force gradients
+// (a = xi, chi, 1 - 2 (chi + xi), chi, xi; b = (1 - 2 l)/2, l, l, (1 - 2 l)/2).
+struct Scheme {
+    int nk;          // force evaluations (kicks) per step
+    double a[5];     // drifts
+    double b[4];     // kicks
+};
+inline Scheme make_scheme(int integrator, double lambda)
+{
+    Scheme s{};
+    if (integrator == 2) {
+        const double xi = 0.1786178958448091, l = -0.2123418310626054,
+                     chi = -0.06626458266981849;
+        s.nk = 4;
+        s.a[0] = xi; s.a[1] = chi; s.a[2] = 1.0 - 2.0 * (chi + xi); s.a[3] = chi; s.a[4] = xi;
+        s.b[0] = 0.5 * (1.0 - 2.0 * l); s.b[1] = l; s.b[2] = l; s.b[3] = 0.5 * (1.0 - 2.0 * l);
+    } else if (integrator == 1) {
+        s.nk = 2;
+        s.a[0] = lambda; s.a[1] = 1.0 - 2.0 * lambda; s.a[2] = lambda;
+        s.b[0] = 0.5; s.b[1] = 0.5;
+    } else {
+        s.nk = 1;
+        s.a[0] = 0.5; s.a[1] = 0.5;
+        s.b[0] = 1.0;
+    }
+    return s;
+}
+
+// The mixed kernel's FP32 form of a Scheme (prepared on the host): the two
+// end drifts of consecutive steps merged, the trajectory is a first drift
+// r_first dtau and n_md nk substeps {kick; drift}: substep k kicks by
+// kq[k % nk] (kick = kq[0]; kr = kq / kick) and drifts by r[k % nk] dtau, the
+// last one by r_last dtau.  kv: the kick sizes differ within a step.
+struct MixedScheme {
+    float dt, kick, kq[4], kr[4], r[4], r_last, r_first;
+    int nk;
+    bool kv;
+};
+inline MixedScheme make_mixed_scheme(int integrator, double lambda, double dtau)
+{
+    MixedScheme m{};
+    const Scheme s = make_scheme(integrator, lambda);
+    m.dt = (float)dtau;
+    m.nk = s.nk;
+    if (integrator == 1) {  // the same FP32 values as 2 kicks of dt/2
+        const float lam = (float)lambda;
+        m.kq[0] = m.kq[1] = 0.5f * m.dt;
+        m.r[0] = 1.0f - 2.0f * lam;
+        m.r[1] = 2.0f * lam;
+        m.r_last = m.r_first = lam;
+    } else if (integrator == 2) {
+        for (int k = 0; k < 4; ++k) {
+            m.kq[k] = (float)s.b[k] * m.dt;
+            m.r[k] = k + 1 < s.nk ? (float)s.a[k + 1] : (float)(s.a[s.nk] + s.a[0]);
+        }
+        m.r_last = (float)s.a[s.nk];
+        m.r_first = (float)s.a[0];
+    } else {
+        m.kq[0] = m.dt;
+        m.r[0] = 1.0f;
+        m.r_last = m.r_first = 0.5f;
+    }
+    m.kick = m.kq[0];
+    for (int k = 0; k < 4; ++k) m.kr[k] = k < s.nk ? m.kq[k] / m.kick : 1.0f;
+    m.kv = integrator == 2;
+    return m;
+}
+
 // One contiguous run of one series inside one bin (a block's register window).
 // A bin holds either several whole series side by side (each on whole warps),
 // or one tile of a series too long for a window.  A tile integrates the window
@@ -47,8 +120,8 @@ struct Plan {
     int* d_bin_seg = nullptr;    // segment ids, bin-major
     SerInfo* d_ser = nullptr;
     int n_md = 0;
-    int integrator = 0;         // 0 leapfrog, 1 minimum-norm (two forces per step)
-    double lambda = 0.0;        // of the minimum-norm integrator
+    int integrator = 0;         // 0 leapfrog, 1 and 2 minimum-norm (2 and 4 forces per step)
+    double lambda = 0.0;        // of the second-order minimum-norm integrator
     bool mixed = false, mass = false;
     bool lev = false;           // RSV model with leverage (rho != 0)
 };
@@ -202,8 +275,10 @@ struct TrajArgs {
     const float* minv;   // optional inverse mass (FP32, packed)
     const int* mass_on;  // optional flag; 0 = use m = 1
     int n_md;
-    int integrator;      // 0 leapfrog (eqs. (6)-(8)), 1 minimum-norm, two forces per step
-    double lambda;       // of the minimum-norm integrator
+    int integrator;      // 0 leapfrog (eqs. (6)-(8)), 1 and 2 minimum-norm (see Scheme)
+    double lambda;       // of the second-order minimum-norm integrator
+    Scheme sch;          // make_scheme(integrator, lambda)
+    MixedScheme msch;    // make_mixed_scheme(integrator, lambda, dtau)
     double dtau;
     uint64_t seed, traj;
     int* status;

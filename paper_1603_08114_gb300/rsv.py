@@ -148,12 +148,14 @@ def rsv_reserve(ctx: Context, max_T: int, max_series: int = 0):
 
 RSV_LEAPFROG, RSV_OMELYAN2 = 0, 1
 RSV_OMELYAN2_LAMBDA = 0.19318332750378357
+RSV_OMELYAN4 = 2
 
 
 def rsv_set_integrator(ctx: Context, kind="leapfrog", lam: float = 0.0):
-    """Integrator of later trajectories and plans: "leapfrog" or "omelyan2"
-    (lam <= 0: the minimum-norm value)."""
-    k = {"leapfrog": RSV_LEAPFROG, "omelyan2": RSV_OMELYAN2}.get(kind, kind)
+    """Integrator of later trajectories and plans: "leapfrog", "omelyan2"
+    (lam <= 0: the minimum-norm value) or "omelyan4" (lam ignored)."""
+    k = {"leapfrog": RSV_LEAPFROG, "omelyan2": RSV_OMELYAN2,
+         "omelyan4": RSV_OMELYAN4}.get(kind, kind)
     _check(lib().rsv_set_integrator(ctx.handle, int(k), float(lam)))
 
 

@@ -108,15 +108,17 @@ def test_forward_matches_reference(rsv, ctx, problem, scaled):
 @pytest.mark.parametrize("scaled", [False, True])
 def test_forward_against_fp64_network_within_bf16_bound(rsv, ctx, problem, scaled):
     """The GPU network (BF16 operands, FP32 accumulation) against the plain
-    FP64 network, with a per-site bound derived from BF16 rounding alone:
-    round-to-nearest BF16 (8 significant bits) moves each operand by at most
-    u = 2^-8 relative, so to first order
-      |dz1_j| <= 2u sum_i |f_i W1_ji|                  (features and W1 rounded)
-      |dz2_k| <= sum_j |W2_kj| (|dz1_j| + 2u |a1_j|)     (tanh' <= 1; a1, W2 rounded)
-      |dz3|   <= sum_k |W3_k| |dz2_k|                  (W3 and a2 stay FP32)
-      |d ln m| <= sigmoid(z3) / (softplus(z3) + eps) |dz3|,
-    taken with 10 % for second-order terms plus 1e-5 for FP32 accumulation
-    and the FP32 tanh, exp and log1p."""
+    FP64 network, within a tolerance derived from BF16 rounding.  Rounding
+    to nearest BF16 (8 significant bits) moves each rounded operand x -- the
+    features, W1, the hidden activations a1 and W2 -- to x (1 + e), |e| <= 2^-8;
+    taken as independent with variance (2^-8)^2 / 3 (probabilistic rounding
+    error analysis, Higham and Mary, SIAM J. Sci. Comput. 41 (2019) A2815),
+    the first-order error of ln m at a site has the standard deviation
+      sigma = 2^-8 / sqrt(3) * || x * d(ln m)/dx ||_2  over the rounded operands,
+    the gradient taken through the FP64 network.  Every site must lie within
+    6 sigma (+ 1e-5 for FP32 accumulation and the FP32 tanh, exp and log1p),
+    and the errors must look like BF16 rounding: RMS of err / sigma <= 1.5
+    and visibly above FP32 level."""
     P = unflat(flat(problem["P"]))   # the FP32 parameters the GPU holds
     params = dev(flat(problem["P"]), torch.float32)
     m_gpu = torch.empty(problem["T"], dtype=torch.float32, device="cuda")
@@ -126,18 +128,30 @@ def test_forward_against_fp64_network_within_bf16_bound(rsv, ctx, problem, scale
                      log_scale=problem["log_s_dev"] if scaled else None)
     F = problem["Fnp"]
     ref = mlp.forward(P, F, bf=False, log_s=ls)
-    u = 2.0 ** -8
-    dz1 = 2 * u * (np.abs(F) @ np.abs(P["W1"]).T)
-    dz2 = (dz1 + 2 * u * np.abs(ref["a1"])) @ np.abs(P["W2"]).T
-    dz3 = dz2 @ np.abs(P["W3"])
-    sig = 1.0 / (1.0 + np.exp(-ref["z3"]))
-    bound = 1.1 * sig / ref["u"] * dz3 + 1e-5
+    a1, a2 = ref["a1"], ref["a2"]
+    # d ln m / d z3, then back through the layers
+    d3 = (1.0 / (1.0 + np.exp(-ref["z3"]))) / ref["u"]
+    d2 = d3[:, None] * P["W3"][None, :] * (1.0 - a2 ** 2)        # d/dz2_k
+    e1 = d2 @ P["W2"]                                             # d/d(rounded a1)_j
+    d1 = e1 * (1.0 - a1 ** 2)                                     # d/dz1_j
+    g2 = (e1 * a1) ** 2                                           # a1 rounding
+    g2 += (d2 ** 2) @ (P["W2"] ** 2) * a1 ** 2                    # W2 rounding
+    g2 = g2.sum(1)
+    g2 += ((d1 @ P["W1"]) * F) ** 2 @ np.ones(F.shape[1])         # feature rounding
+    g2 += ((d1 ** 2) @ (P["W1"] ** 2) * F ** 2).sum(1)            # W1 rounding
+    sigma = 2.0 ** -8 / np.sqrt(3.0) * np.sqrt(g2)
     lo, hi = mlp.mass_bounds(s.y, s.h_true, TH)
     m_ref = np.clip(ref["m"], lo, hi)   # the clamp is 1-Lipschitz in ln m
     err = np.abs(np.log(m_gpu.cpu().numpy().astype(np.float64)) - np.log(m_ref))
-    assert np.all(err <= bound), (err.max(), bound[np.argmax(err - bound)])
-    # the bound is not vacuous: BF16 rounding is visible against FP64
-    assert np.median(bound) < 0.1 and np.max(err) > 1e-5
+    inside = (m_ref > lo) & (m_ref < hi)
+    assert np.all(err <= 6.0 * sigma + 1e-5), (err.max(), sigma[np.argmax(err - 6 * sigma)])
+    if scaled:
+        # without the output scale the network sits below the mass floor and
+        # every site is clamped; with it most sites are free
+        assert inside.mean() > 0.5
+        rms = np.sqrt(np.mean((err[inside] / sigma[inside]) ** 2))
+        assert rms <= 1.5, rms
+        assert np.max(err) > 1e-5
 
 
 @pytest.mark.parametrize("batch,scaled", [(64, False), (4096, False), (4096, True)])
