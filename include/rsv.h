@@ -93,6 +93,21 @@ rsv_status rsv_sync_status(rsv_ctx* ctx, void* stream);
  * `tile` is kept whole.  All zero restores the automatic plan.  Results do not
  * depend on the tiling. */
 rsv_status rsv_set_schedule(rsv_ctx* ctx, int threads, int sites_per_thread, int64_t tile);
+/* rsv_set_persistent: 1 (the default) runs an rsv_hmc_chain call in RSV_MIXED
+ * precision on the model without leverage as ONE persistent cooperative
+ * launch when the tiles of its plan can all be resident on the GPU at once
+ * (else, or with 0, one trajectory kernel per trajectory and a theta-sweep
+ * kernel after it).  Every tile stays on its SM for the whole chain; after
+ * each trajectory one grid barrier, then every block sums all tiles' records
+ * in the same order and takes the same Metropolis decision and theta sweep.
+ * The results are bit for bit those of the per-trajectory launches. */
+rsv_status rsv_set_persistent(rsv_ctx* ctx, int enable);
+/* rsv_set_wait_limit: the clock cycles (per SM) a device-side wait of the
+ * persistent chain may spin before it gives up: it then records a timeout,
+ * which rsv_sync_status() returns as RSV_ETIMEOUT, and the kernel ends (the
+ * chain's results are invalid; the context stays usable).  0 restores the
+ * default, 2^31 cycles (about one second at 2 GHz); cycles < 0: RSV_EINVAL. */
+rsv_status rsv_set_wait_limit(rsv_ctx* ctx, int64_t cycles);
 
 /* ---- integrator -------------------------------------------------------------
  * The molecular-dynamics integrator of the trajectories run afterwards through
@@ -369,8 +384,9 @@ rsv_status rsv_draw_momenta(rsv_ctx* ctx, uint64_t seed, uint64_t series, uint64
  * rsv_timing: enable (1) / disable (0) CUDA-event timing of every trajectory
  * kernel launch (skipped while the stream is being captured).
  * rsv_stats: kernel launches made by the library, trajectory-kernel launches
- * and their summed device time (ms) since the last reset; synchronises the
- * recorded events; reset != 0 clears the counters after reading. */
+ * (a persistent chain launch counts each of its trajectories) and their summed
+ * device time (ms) since the last reset; synchronises the recorded events;
+ * reset != 0 clears the counters after reading. */
 rsv_status rsv_ess(rsv_ctx* ctx, const float* x, int64_t n, int64_t T, float* ess_out,
                    void* stream);
 /* rsv_pipe_probe: launch one probe kernel that keeps one on-chip unit busy on

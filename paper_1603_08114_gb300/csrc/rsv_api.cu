@@ -192,6 +192,21 @@ rsv_status rsv_set_integrator(rsv_ctx* c, rsv_integrator kind, double lambda)
     return RSV_OK;
 }
 
+rsv_status rsv_set_persistent(rsv_ctx* c, int enable)
+{
+    if (!c) return fail(RSV_EINVAL, "null context");
+    c->persistent = enable != 0;
+    return RSV_OK;
+}
+
+rsv_status rsv_set_wait_limit(rsv_ctx* c, int64_t cycles)
+{
+    if (!c) return fail(RSV_EINVAL, "null context");
+    if (cycles < 0) return fail(RSV_EINVAL, "wait limit must be >= 0");
+    c->wait_limit = cycles > 0 ? (long long)cycles : (1LL << 31);
+    return RSV_OK;
+}
+
 rsv_status rsv_set_leverage(rsv_ctx* c, double rho)
 {
     if (!c) return fail(RSV_EINVAL, "null context");

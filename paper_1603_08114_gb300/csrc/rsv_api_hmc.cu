@@ -9,6 +9,7 @@
 
 #include "rsv.h"
 #include "rsv_api_common.cuh"
+#include "rsv_chain.cuh"
 #include "rsv_ctx.cuh"
 #include "rsv_gibbs.cuh"
 #include "rsv_traj.cuh"
@@ -121,7 +122,72 @@ struct RunOpts {
     int fallback_window;
     int* mass_used_out;
     bool commit_only_accepted;  // mixed: write back only accepted series
+    bool chain;                 // rsv_hmc_chain (may run as one persistent launch)
 };
+
+// Trajectories per persistent launch at most: the grid barrier's counter
+// reaches trajectories x blocks (< 2^32).
+constexpr int64_t kChainMaxTraj = int64_t(1) << 24;
+
+// The whole chain in one persistent cooperative launch (rsv_chain.cu), if the
+// plan supports it and its blocks fit on the GPU at once; *done tells.
+rsv_status run_persistent(rsv_ctx* c, const Plan& P, const RunOpts& o, const TrajArgs& a,
+                          cudaStream_t s, bool* done)
+{
+    *done = false;
+    rsv_status st;
+    if ((st = ctx_ensure_partials(c, 2 * P.nsegs)) != RSV_OK) return st;
+    int* ints = c->ints.as<int>();
+    cudaError_t e = cudaMemsetAsync(ints + kChainBarrier, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return cuda_fail(e, "barrier reset");
+    ChainArgs ch;
+    memset(&ch, 0, sizeof(ch));
+    ch.A = a;
+    ch.A.ser_cur = nullptr;   // the kernel keeps the current buffer itself
+    ch.A.theta = nullptr;
+    ch.A.dH_out = nullptr;
+    ch.A.acc_out = nullptr;
+    ch.A.fb_state = nullptr;
+    ch.A.snap_prev = nullptr;
+    ch.A.traj = o.traj0;
+    ch.n_traj = o.n_traj;
+    ch.traj0 = o.traj0;
+    ch.update_theta = o.update_theta;
+    ch.theta = const_cast<double*>(o.theta);
+    ch.theta_out = o.theta_out;
+    ch.snaps = o.snaps;
+    ch.thin = o.thin > 0 ? o.thin : 1;
+    ch.dH_out = o.dH_out;
+    ch.acc_out = o.acc_out;
+    ch.partials = c->partials.as<double>();
+    ch.nsegs = P.nsegs;
+    ch.bar = reinterpret_cast<unsigned*>(ints + kChainBarrier);
+    ch.wait_limit = c->wait_limit;
+    ch.fallback_window = o.minv ? o.fallback_window : 0;
+    ch.mass_on_out = ints + kMassOn;
+    ch.ser_cur_out = c->ser_cur.as<int>();
+    const bool rec = c->timing && !capture_active();
+    if (rec && c->ev_used + 2 > c->ev.size()) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t ev;
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "event");
+            c->ev.push_back(ev);
+        }
+    }
+    if (rec) cudaEventRecord(c->ev[c->ev_used], s);
+    bool launched = false;
+    e = launch_chain(ch, P, c->num_sms, s, &launched);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent chain kernel");
+    if (!launched) return RSV_OK;
+    if (rec) {
+        cudaEventRecord(c->ev[c->ev_used + 1], s);
+        c->ev_used += 2;
+    }
+    c->launches += 1;
+    c->traj_launches += o.n_traj;  // the timed launch covers n_traj trajectories
+    *done = true;
+    return RSV_OK;
+}
 
 rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
 {
@@ -204,10 +270,17 @@ rsv_status run(rsv_ctx* c, const Plan& P, const RunOpts& o, cudaStream_t s)
         a.h0d = o.h;
         a.h1d = c->dbuf0.as<double>();
     }
+    // a mixed chain of one series without leverage: the whole chain in one
+    // persistent launch when it can be
+    bool done = false;
+    if (mixed && !P.lev && o.chain && c->persistent && !o.p && !o.log_u && o.n_traj > 0 &&
+        o.n_traj <= kChainMaxTraj && chain_supported(P) && !capture_active()) {
+        if ((st = run_persistent(c, P, o, a, s, &done)) != RSV_OK) return st;
+    }
     // mixed path: a snapshot that is due is written by the next trajectory's
     // load pass (its start state is that state), the last one by its own kernel
     float* pending_snap = nullptr;
-    for (int64_t i = 0; i < o.n_traj; ++i) {
+    for (int64_t i = 0; !done && i < o.n_traj; ++i) {
         a.traj = o.traj0 + (uint64_t)i;
         a.dH_out = o.dH_out ? o.dH_out + i * (int64_t)n : c->ser_dh.as<double>();
         a.acc_out = o.acc_out ? o.acc_out + i * (int64_t)n : c->ser_acc.as<int>();
@@ -367,6 +440,7 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
     o.fallback_window = fallback_window;
     o.mass_used_out = mass_used_out;
     o.commit_only_accepted = false;
+    o.chain = true;
     return run(c, *P, o, (cudaStream_t)stream);
 }
 

@@ -31,6 +31,7 @@ enum IntSlot : int {
     kActionCounter = 6,  // arrival counter of the action reduction
     kScratchAcc = 7,     // accept flag when the caller gives none
     kGibbsCounter = 8,   // arrival counter of the theta reduction
+    kChainBarrier = 9,   // grid barrier counter of the persistent chain
     kBatchCounter = 16,  // [..] per-call counters of other kernels
     kIntSlots = 64
 };
@@ -64,6 +65,8 @@ struct rsv_ctx {
     double lambda = 0.0;
     double rho = 0.0;               // rsv_set_leverage (0: no leverage)
     int64_t sched_tile = 0;
+    bool persistent = true;             // rsv_set_persistent
+    long long wait_limit = 1LL << 31;   // rsv_set_wait_limit (clock cycles)
     // accounting: kernel launches, and CUDA events around trajectory kernels
     int64_t launches = 0;
     int64_t traj_launches = 0;

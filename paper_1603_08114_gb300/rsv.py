@@ -63,6 +63,8 @@ def lib():
         L.rsv_set_schedule.argtypes = [_P, _INT, _INT, _I64]
         L.rsv_set_integrator.argtypes = [_P, _INT, ctypes.c_double]
         L.rsv_set_leverage.argtypes = [_P, ctypes.c_double]
+        L.rsv_set_persistent.argtypes = [_P, _INT]
+        L.rsv_set_wait_limit.argtypes = [_P, _I64]
         L.rsv_action.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
         L.rsv_force.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
         L.rsv_hmc_trajectory.argtypes = [_P, _P, _P, _P, _P, _I64, Theta, _P, _INT,
@@ -86,7 +88,8 @@ def lib():
                      "rsv_set_integrator", "rsv_set_leverage", "rsv_action", "rsv_force",
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
                      "rsv_timing", "rsv_stats", "rsv_gibbs_theta", "rsv_plan_create",
-                     "rsv_plan_info", "rsv_hmc_batched", "rsv_pipe_probe"):
+                     "rsv_plan_info", "rsv_hmc_batched", "rsv_pipe_probe", "rsv_set_persistent",
+                     "rsv_set_wait_limit"):
             getattr(L, name).restype = _INT
         _lib = L
     return _lib
@@ -157,6 +160,17 @@ def rsv_set_integrator(ctx: Context, kind="leapfrog", lam: float = 0.0):
     k = {"leapfrog": RSV_LEAPFROG, "omelyan2": RSV_OMELYAN2,
          "omelyan4": RSV_OMELYAN4}.get(kind, kind)
     _check(lib().rsv_set_integrator(ctx.handle, int(k), float(lam)))
+
+
+def rsv_set_persistent(ctx: Context, enable: bool = True):
+    """Run mixed single-series chains as one persistent launch (default) or
+    one trajectory kernel per trajectory."""
+    _check(lib().rsv_set_persistent(ctx.handle, int(bool(enable))))
+
+
+def rsv_set_wait_limit(ctx: Context, cycles: int = 0):
+    """Clock cycles a device-side wait may spin before RSV_ETIMEOUT (0: default)."""
+    _check(lib().rsv_set_wait_limit(ctx.handle, int(cycles)))
 
 
 def rsv_set_leverage(ctx: Context, rho: float = 0.0):
