@@ -47,7 +47,9 @@ def run(rsv, ctx, s, persistent, n, n_md, dtau, minv=None, update_theta=True, th
                           minv=minv, seed=seed, traj0=3, update_theta=update_theta, snaps=snaps,
                           thin=thin, theta_out=ths, dH_out=dH, accept_out=acc,
                           fallback_window=fb, mass_used_out=used)
-        rsv.rsv_sync_status(ctx)
+        # a trajectory whose dH is not finite is a rejection (the fallback
+        # case's steps are that large)
+        rsv.rsv_sync_status(ctx, allow_nonfinite=True)
     finally:
         rsv.rsv_set_persistent(ctx, True)
         rsv.rsv_set_integrator(ctx, "leapfrog")
