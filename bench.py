@@ -61,11 +61,11 @@ ALG_OPS_PER_SITE_STEP = 10
 # the compensated kick (4) and the compensated drift (4; the two half drifts
 # merged), i.e. 3 operations of compensation beyond the method's 10.
 IMPL_OPS_PER_SITE_STEP_MIXED = 13
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_traj_mixed launch of
-# the headline workload (learned mass, T = 2^20), from the capture summarised in
-# profiles/k_traj_mixed_T2p20.md (the inputs are read once per launch, so the
-# figure does not depend on n_md); valid for the kernel revision it was taken on.
-TRAFFIC = {"kernel_rev": 11, "bytes": 25270272}
+# dram__bytes_read.sum + dram__bytes_write.sum per trajectory of the headline's
+# kernel (the persistent chain kernel: one launch's bytes over its
+# trajectories; the inputs stay in L2 between trajectories), from the capture
+# summarised in profiles/; valid for the kernel revision it was taken on.
+TRAFFIC = {"kernel": "k_chain_mixed", "kernel_rev": 13, "bytes_per_trajectory": None}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -437,6 +437,7 @@ def run_ours(args):
         pl.close()
         nt_, j_ = pi["threads"], pi["sites_per_thread"]
         rsv.rsv_set_schedule(ctx, nt_, j_, nt_ * j_ - 2 * (n_hi + 1) - 3)
+        rsv.rsv_set_persistent(ctx, False)  # the per-trajectory kernels, compared alike
         out = []
         try:
             for n_md in (n_hi, 1):
@@ -454,6 +455,7 @@ def run_ours(args):
                 out.append(1e3 * ms / max(nl, 1))
         finally:
             rsv.rsv_set_schedule(ctx)
+            rsv.rsv_set_persistent(ctx, True)
         return (out[0] - out[1]) / (n_hi - 1), out[1], {"threads": nt_, "sites_per_thread": j_}
 
     def leverage_leg(steps):
@@ -827,13 +829,10 @@ def run_ours(args):
         rsv.rsv_timing(ctx, False)
         _, nl, ms = rsv.rsv_stats(ctx, reset=True)
         return 1e3 * ms / max(nl, 1)
-    # both lengths on the headline's tiling (its halo for n_md): the plan the
-    # library picks for n_md, its tile fixed for the one-step run too
-    pl = rsv.Plan(ctx, np.array([0, T_SITES], dtype=np.int64), head_nmd, "mixed",
-                  with_mass=minv is not None)
-    pi = pl.info()
-    pl.close()
-    nt_, j_ = pi["threads"], pi["sites_per_thread"]
+    # both lengths on the headline's tiling (its halo for n_md): the shape a
+    # chain call of the headline uses, its tile fixed for the one-step run too
+    cs = rsv.rsv_chain_schedule(ctx, T_SITES, head_nmd, "mixed", with_mass=minv is not None)
+    nt_, j_ = cs["threads"], cs["sites_per_thread"]
     rsv.rsv_set_schedule(ctx, nt_, j_, nt_ * j_ - 2 * (head_nmd + 1) - 3)
     t_hi, t_lo = kernel_us(head_nmd), kernel_us(1)
     rsv.rsv_set_schedule(ctx)
@@ -841,8 +840,10 @@ def run_ours(args):
     md = {"site_updates_per_s": ws * T_SITES / (per_step_us * 1e-6), "unit": UNIT,
           "us_per_step": per_step_us, "us_per_trajectory_fixed": t_lo - per_step_us,
           "kernel_us_per_trajectory": t_hi, "n_md": head_nmd,
-          "schedule": {"threads": nt_, "sites_per_thread": j_},
-          "how": "k_traj_mixed time at n_md minus at n_md = 1, per step (CUDA events)"}
+          "schedule": {"threads": nt_, "sites_per_thread": j_,
+                       "persistent": cs["persistent"]},
+          "how": "trajectory time of the chain kernel at n_md minus at n_md = 1, per step "
+                 "(CUDA events around a 10-trajectory chain call)"}
 
     # roofline of the headline's trajectory kernel: the method's algorithmic
     # work (ALG_OPS FP32 operations + 1 exp per site and leapfrog step) over
@@ -855,7 +856,8 @@ def run_ours(args):
     # DRAM bytes (read + write) of one headline launch from the ncu capture in
     # profiles/, valid only for the kernel revision it was taken on
     from paper_1603_08114_gb300 import autotune as _at
-    traffic = TRAFFIC["bytes"] if TRAFFIC["kernel_rev"] == _at.KERNEL_REV else None
+    traffic = (TRAFFIC["bytes_per_trajectory"] if TRAFFIC["kernel_rev"] == _at.KERNEL_REV
+               else None)
     fp64_roof = None
     if fp64 is not None:
         f_launch = fp64["traj_ms"] / 1e3 / max(fp64["traj_launches"], 1)
@@ -936,7 +938,8 @@ def run_ours(args):
                 for tag, r in mn4.items()},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
                          "unit": "Top/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                         "kernel": "k_traj_mixed",
+                         "kernel": "k_chain_mixed" if cs["persistent"] else "k_traj_mixed",
+                         "per": "trajectory" if cs["persistent"] else "launch",
                          "peak_kind": "measured FP32 FMA rate (rsv_pipe_probe, the larger of "
                                       "FFMA and FFMA2), this run",
                          "per_launch_ms": per_launch_s * 1e3,
@@ -997,10 +1000,8 @@ def table2_gpu(ctx, rsv, synth, torch, B_list, n_lo=10, n_hi=110):
         y = torch.tensor(s.y, device=dev)
         lr = torch.tensor(s.lnrv, device=dev)
         for prec in ("mixed", "fp64"):
-            pl = rsv.Plan(ctx, np.array([0, T], dtype=np.int64), n_hi, prec)
-            pi = pl.info()
-            pl.close()
-            nt, j = pi["threads"], pi["sites_per_thread"]
+            cs = rsv.rsv_chain_schedule(ctx, T, n_hi, prec)
+            nt, j = cs["threads"], cs["sites_per_thread"]
             if T > nt * j - 2 * (n_hi + 1) - 3:  # a tiled series: one tile size for both lengths
                 rsv.rsv_set_schedule(ctx, nt, j, nt * j - 2 * (n_hi + 1) - 3)
             times = []
@@ -1053,7 +1054,8 @@ def table2_summary(B_list, gpu, cpu):
         "fit": fits,
         "site_updates_per_s_at_largest_B": 512 * B_list[-1] / res["gpu_mixed"][-1],
         "paper": PAPER_TABLE2,
-        "how": "GPU: k_traj_mixed / k_traj_fp64 time at n_md = 110 minus at n_md = 10 "
+        "how": "GPU: trajectory time of a chain call (mixed: the persistent chain kernel; "
+               "FP64: one k_traj_fp64 launch per trajectory) at n_md = 110 minus at n_md = 10 "
                "(one tiling, CUDA events) / 100; oracle: FP64 leapfrog in plain C on one "
                "host core; fitted f(B) = A + C B like the paper's Table 2"})
     if cpu is not None:

@@ -108,6 +108,13 @@ rsv_status rsv_set_persistent(rsv_ctx* ctx, int enable);
  * chain's results are invalid; the context stays usable).  0 restores the
  * default, 2^31 cycles (about one second at 2 GHz); cycles < 0: RSV_EINVAL. */
 rsv_status rsv_set_wait_limit(rsv_ctx* ctx, int64_t cycles);
+/* rsv_chain_schedule: the block shape an rsv_hmc_chain call of this context
+ * with these arguments uses (threads per block, sites per thread, and the
+ * owned sites per tile: T when the series is not cut), and whether it runs as
+ * one persistent launch (1) or one kernel per trajectory (0).  Builds and
+ * caches the call's plan; any output may be NULL. */
+rsv_status rsv_chain_schedule(rsv_ctx* ctx, int64_t T, int n_md, rsv_precision prec, int with_mass,
+                              int* threads, int* sites_per_thread, int64_t* tile, int* persistent);
 
 /* ---- integrator -------------------------------------------------------------
  * The molecular-dynamics integrator of the trajectories run afterwards through

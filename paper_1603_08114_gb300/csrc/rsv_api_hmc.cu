@@ -44,13 +44,17 @@ cudaError_t timed_traj(rsv_ctx* c, const TrajArgs& a, const Plan& p, cudaStream_
     return e;
 }
 
-// Single-series plan from the context cache.
-rsv_status single_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, const Plan** out)
+// Single-series plan from the context cache.  chain: the plan of an
+// rsv_hmc_chain call that can run as one persistent launch (its own block
+// shape preference).
+rsv_status single_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, const Plan** out,
+                       bool chain = false)
 {
     for (auto& e : c->plans) {
         if (e.T == T && e.n_md == n_md && e.mixed == mixed && e.mass == mass &&
             e.lev == (c->rho != 0.0) && e.integrator == c->integrator && e.lambda == c->lambda &&
-            e.nt == c->sched_nt && e.j == c->sched_j && e.tile == c->sched_tile) {
+            e.nt == c->sched_nt && e.j == c->sched_j && e.tile == c->sched_tile &&
+            e.chain == chain) {
             *out = &e.plan;
             return RSV_OK;
         }
@@ -64,11 +68,11 @@ rsv_status single_plan(rsv_ctx* c, int64_t T, int n_md, bool mixed, bool mass, c
     }
     const int64_t off[2] = {0, T};
     const bool lev = c->rho != 0.0;
-    rsv_ctx::Cached e{T,    n_md, c->integrator, c->lambda,  mixed,         mass,
-                      lev,  c->sched_nt, c->sched_j, c->sched_tile, Plan()};
+    rsv_ctx::Cached e{T,   n_md, c->integrator, c->lambda,  mixed,         mass, lev,
+                      c->sched_nt, c->sched_j, c->sched_tile, chain, Plan()};
     const char* why = "";
     if (!make_plan(off, 1, n_md, c->integrator, c->lambda, mixed, mass, lev, c->num_sms,
-                   c->sched_nt, c->sched_j, c->sched_tile, e.plan, &why))
+                   c->sched_nt, c->sched_j, c->sched_tile, e.plan, &why, chain))
         return fail(RSV_EINVAL, "%s", why);
     c->plans.push_back(e);
     *out = &c->plans.back().plan;
@@ -419,7 +423,9 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
     if (update_theta && c->rho != 0.0)
         return fail(RSV_EINVAL, "the theta update is for the model without leverage (rho = 0)");
     const Plan* P = nullptr;
-    if ((st = single_plan(c, T, n_md, prec == RSV_MIXED, minv != nullptr, &P)) != RSV_OK) return st;
+    const bool chain = prec == RSV_MIXED && c->rho == 0.0 && c->persistent;
+    if ((st = single_plan(c, T, n_md, prec == RSV_MIXED, minv != nullptr, &P, chain)) != RSV_OK)
+        return st;
     RunOpts o;
     memset(&o, 0, sizeof(o));
     o.h = h;
@@ -442,6 +448,32 @@ rsv_status rsv_hmc_chain(rsv_ctx* c, double* h, const double* y, const double* l
     o.commit_only_accepted = false;
     o.chain = true;
     return run(c, *P, o, (cudaStream_t)stream);
+}
+
+rsv_status rsv_chain_schedule(rsv_ctx* c, int64_t T, int n_md, rsv_precision prec, int with_mass,
+                              int* threads, int* sites_per_thread, int64_t* tile, int* persistent)
+{
+    rsv_status st = ctx_begin(c, nullptr);
+    if (st != RSV_OK) return st;
+    if (T < 1) return fail(RSV_EINVAL, "T must be >= 1 (got %lld)", (long long)T);
+    if ((st = check_common(n_md, 1.0, prec)) != RSV_OK) return st;
+    const bool chain = prec == RSV_MIXED && c->rho == 0.0 && c->persistent;
+    const Plan* P = nullptr;
+    if ((st = single_plan(c, T, n_md, prec == RSV_MIXED, with_mass != 0, &P, chain)) != RSV_OK)
+        return st;
+    bool fits = false;
+    if (chain) {
+        cudaError_t e = chain_fits(*P, c->num_sms, &fits);
+        if (e != cudaSuccess) return cuda_fail(e, "chain occupancy");
+    }
+    if (threads) *threads = P->nt;
+    if (sites_per_thread) *sites_per_thread = P->j;
+    if (tile) {  // the owned sites of a tile (the series itself when it is not cut)
+        const int64_t K = (int64_t)n_md * make_scheme(P->integrator, P->lambda).nk + 1;
+        *tile = P->nbins > 1 ? (int64_t)P->nt * P->j - 2 * K - 3 : T;
+    }
+    if (persistent) *persistent = fits ? 1 : 0;
+    return RSV_OK;
 }
 
 rsv_status rsv_plan_create(rsv_ctx* c, const int64_t* offsets, int64_t n_series, int n_md,

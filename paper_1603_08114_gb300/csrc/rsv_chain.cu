@@ -91,29 +91,39 @@ __device__ __forceinline__ void draw_slots(const TrajArgs& A, uint64_t traj, con
     }
 }
 
-template <int J, bool MASS>
-__global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_chain_mixed(const ChainArgs C)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ MixedSmem<false> S;
-    __shared__ StatsRec s_rec;   // statistics of the current state
-    __shared__ float s_th[5];    // theta (FP32-valued once swept)
-    __shared__ double s_thd[5];  // theta as given (recorded while it is not swept)
-    __shared__ float2 s_red[kRecWords];
-    __shared__ int s_ok, s_fb[2];
-    const TrajArgs& A = C.A;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
-    const int nw = NT >> 5, NS = mixed_row(NT, J);
-    constexpr int P = J / 2;
-    // s_ph, the momentum row of the dynamic shared memory (see traj_mixed_bin)
-    float* s_ph = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) +
-                                           (size_t)(2 + (MASS ? 1 : 0)) * P * NT) +
-                  (size_t)2 * NS * J;
-    const int b = blockIdx.x;
-    const Seg g = A.segs[A.bin_seg[A.bin_first[b]]];
-    const int64_t T = A.ser[g.series].T;
-    const int nseg = A.ser[g.series].nseg, seg0 = A.ser[g.series].seg0;
+// The chain's state besides the trajectory body's (shared memory, so that no
+// value lives in registers across the body: the body's register pressure
+// stays that of the per-trajectory kernel).
+struct ChainShared {
+    StatsRec rec;          // statistics of the current state
+    float th[5];           // theta (FP32-valued once swept)
+    double thd[5];         // theta as given (recorded while it is not swept)
+    float2 red[kRecWords];
+    int ok, fb[2];
+    long long i;           // the trajectory about to run / just run
+    double u[2];           // the Metropolis uniforms of trajectories of each parity
+    Seg g;                 // the block's segment
+    int64_t T;
+    int nseg, seg0;
+};
 
+// s_ph, the momentum rows of the dynamic shared memory (see traj_mixed_bin).
+template <int J, bool MASS>
+__device__ __forceinline__ float* chain_s_ph(unsigned char* smem_raw)
+{
+    const int NT = blockDim.x, NS = mixed_row(NT, J);
+    return reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) +
+                                    (size_t)(2 + (MASS ? 1 : 0)) * (J / 2) * NT) +
+           (size_t)2 * NS * J;
+}
+
+template <int J, bool MASS>
+__device__ __noinline__ void chain_setup(const ChainArgs& C, MixedSmem<false>& S,
+                                         ChainShared& Q, unsigned char* smem_raw)
+{
+    const TrajArgs& A = C.A;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const Seg g = A.segs[A.bin_seg[A.bin_first[blockIdx.x]]];
     if (tid < 32) {
         const ff v = ff_from_double(exp2((double)tid / 32.0));
         S.exptab[tid] = make_float2(v.hi, v.lo);
@@ -121,141 +131,205 @@ __global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1) k_chain_mixed(const
     for (int i = tid; i < NWMAX * 32; i += NT)
         reinterpret_cast<float*>(S.mt)[i] = reinterpret_cast<const float*>(A.theta_f)[i & 31];
     if (tid < 5) {
-        s_thd[tid] = C.theta[tid];
-        s_th[tid] = (float)C.theta[tid];
+        Q.thd[tid] = C.theta[tid];
+        Q.th[tid] = (float)C.theta[tid];
     }
     if (tid == 0) {
-        s_rec = A.rstats[0];
+        Q.rec = A.rstats[0];
+        Q.fb[0] = Q.fb[1] = 0;
+        Q.i = 0;
+        Q.g = g;
+        Q.T = A.ser[g.series].T;
+        Q.nseg = A.ser[g.series].nseg;
+        Q.seg0 = A.ser[g.series].seg0;
+        Q.u[0] = metropolis_u(A.seed, g.series, C.traj0);
         S.cur = 0;
         S.mass_on = MASS ? 1 : 0;
-        s_fb[0] = s_fb[1] = 0;
     }
-    draw_slots<J>(A, C.traj0, g, s_ph, NS, tid, NT);
+    draw_slots<J>(A, C.traj0, g, chain_s_ph<J, MASS>(smem_raw), mixed_row(NT, J), tid, NT);
     __syncthreads();
+}
 
-    for (int64_t i = 0; i < C.n_traj; ++i) {
-        const uint64_t traj = C.traj0 + (uint64_t)i;
-        // records of this trajectory: the half of partials of its parity (set
-        // before the trajectory's first block barrier, read after its last)
-        if (tid == 0) S.partials = C.partials + (i & 1) * (int64_t)C.nsegs * kPartialWords;
+// After trajectory Q.i: the grid barrier, the decision, the theta sweep and
+// the next momenta; returns false if a barrier wait ran out.  Warps 0..7 sum
+// the tiles' records (one value each; named barrier 1 joins them), thread 0
+// decides and warp 0 then sweeps theta, while warps 8.. draw the next
+// trajectory's momenta (a block of fewer than 9 warps does the steps one
+// after the other).  Not inlined: inside the trajectory loop its
+// loop-invariant values (Philox and sweep constants, addresses) would be
+// hoisted out of the loop and held in registers through the leapfrog, which
+// then runs ~10 % slower.
+template <int J, bool MASS>
+__device__ __noinline__ bool chain_after(const ChainArgs& C, MixedSmem<false>& S,
+                                         ChainShared& Q, unsigned char* smem_raw)
+{
+    static_assert(kRecWords == 8, "warps 0..7 sum one record value each");
+    const TrajArgs& A = C.A;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
+    const int nw = NT >> 5;
+    const bool split = nw > kRecWords;  // warps 8.. draw momenta meanwhile
+    const long long i = Q.i;
+    const bool more = i + 1 < C.n_traj;
+    const uint64_t traj = C.traj0 + (uint64_t)i;
+    float* s_ph = chain_s_ph<J, MASS>(smem_raw);
+    const int NS = mixed_row(NT, J);
+    if (!grid_barrier(C.bar, (unsigned)(i + 1) * gridDim.x, C.wait_limit, A.status, &Q.ok))
+        return false;
+    if (warp < kRecWords) {
+        // every tile's record value f = warp in tile order (lane l takes tiles
+        // l, l + 32, ...; then a butterfly) -- the same order in every block
+        const float2* pf = reinterpret_cast<const float2*>(S.partials);
+        const int nseg = Q.nseg, seg0 = Q.seg0, f = warp;
+        ff sum = {0.f, 0.f};
+        for (int i0 = lane; i0 < nseg; i0 += 32 * 8) {
+            float2 w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                w[u] = i0 + 32 * u < nseg
+                           ? __ldcg(pf + (int64_t)(seg0 + i0 + 32 * u) * kPartialWords + f)
+                           : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + 32 * u < nseg) sum = ff_add(sum, ff{w[u].x, w[u].y});
+        }
+        sum = warp_sum_ff(sum);
+        if (lane == 0) Q.red[f] = make_float2(sum.hi, sum.lo);
+        if (split) asm volatile("bar.sync 1, %0;" ::"r"(kRecWords * 32) : "memory");
+        else __syncthreads();
+    } else {
+        if (more) draw_slots<J>(A, traj + 1, Q.g, s_ph, NS, tid - 32 * kRecWords,
+                                NT - 32 * kRecWords);
+    }
+    if (!split) __syncthreads();  // (the reducing warps passed one already)
+    if (tid == 0) {
+        const MixedTheta& mt = S.mt[0];
+        ff dk;
+        StatsRec r1;
+        rec_from(Q.red, dk, r1.s);
+        r1.mu = mt.mu;
+        r1.ximu = mt.ximu;
+        r1.sl = Q.rec.sl;
+        r1.sll = Q.rec.sll;
+        const double dH = stats_dH(dk, r1.s, Q.rec, mt, Q.T);
+        const int acc = metropolis_accept_u(Q.u[i & 1], dH);
+        if (acc) {
+            Q.rec = r1;
+            S.cur ^= 1;
+        }
+        if (blockIdx.x == 0) {
+            if (!isfinite(dH)) atomicOr(A.status, ST_NONFINITE);
+            if (C.dH_out) C.dH_out[i] = dH;
+            if (C.acc_out) C.acc_out[i] = acc;
+        }
+        if (MASS && C.fallback_window > 0) {
+            int na = Q.fb[0] + acc, nt = Q.fb[1] + 1;
+            if (nt >= C.fallback_window) {
+                if (S.mass_on && 10 * na < 6 * nt) S.mass_on = 0;
+                na = nt = 0;
+            }
+            Q.fb[0] = na;
+            Q.fb[1] = nt;
+        }
+    }
+    if (warp == 0) {
+        __syncwarp();
+        if (C.update_theta) {
+            // the theta sweep from the accepted state's statistics
+            float th[5], tot[NSTAT], x0;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) th[k] = Q.th[k];
+            record_sums(Q.rec, th, Q.T, tot, x0);
+            WarpDrawsF st;
+            st.seed = A.seed;
+            st.series = (uint64_t)Q.g.series;
+            st.traj = traj;
+            st.fill(Q.T);
+            int phi_acc = 0;
+            gibbs_draws_f(tot, x0, Q.T, th, st, 31, &phi_acc);
+            if (lane < 5) {
+                float v = th[0];
+#pragma unroll
+                for (int k = 1; k < 5; ++k)
+                    if (lane == k) v = th[k];
+                Q.th[lane] = v;
+                if (blockIdx.x == 0) {
+                    C.theta[lane] = (double)v;
+                    if (C.theta_out) C.theta_out[5 * i + lane] = (double)v;
+                }
+            }
+            if (lane == 0) S.mt[0] = mixed_theta_f(th);
+        } else if (blockIdx.x == 0 && C.theta_out && lane < 5) {
+            C.theta_out[5 * i + lane] = Q.thd[lane];
+        }
+    }
+    // the next test's uniform, off the critical path where there is a warp 1
+    if (more && tid == (nw > 1 ? 32 : 0))
+        Q.u[(i + 1) & 1] = metropolis_u(A.seed, Q.g.series, traj + 1);
+    __syncthreads();
+    if (!split && more) {  // a small block draws the momenta after the sweep
+        draw_slots<J>(A, traj + 1, Q.g, s_ph, NS, tid, NT);
+        __syncthreads();
+    }
+    if (C.update_theta)
+        for (int k = tid + 32; k < nw * 32; k += NT)
+            reinterpret_cast<float*>(S.mt)[k] = reinterpret_cast<const float*>(S.mt)[k & 31];
+    if (tid == 0) Q.i = i + 1;
+    __syncthreads();
+    return true;
+}
+
+template <int J, bool MASS>
+__global__ void __launch_bounds__(mixed_ntmax<J, MASS>(), 1)
+    k_chain_mixed(const __grid_constant__ ChainArgs C)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ MixedSmem<false> S;
+    __shared__ ChainShared Q;
+    chain_setup<J, MASS>(C, S, Q, smem_raw);
+    for (;;) {
+        const long long i = Q.i;
+        if (i >= C.n_traj) break;
+        // this trajectory's records go to the half of partials of its parity
+        // (set before the body's first block barrier, read after its last)
+        if (threadIdx.x == 0) S.partials = C.partials + (i & 1) * (int64_t)C.nsegs * kPartialWords;
         // the snapshot of the state this trajectory starts from, if due
         float* snap_prev = (C.snaps && i > 0 && i % C.thin == 0)
-                               ? C.snaps + (size_t)(i / C.thin - 1) * (size_t)T
+                               ? C.snaps + (size_t)(i / C.thin - 1) * (size_t)Q.T
                                : nullptr;
-        traj_mixed_bin<J, MASS, false, true>(A, b, S, smem_raw, snap_prev);
-        if (!grid_barrier(C.bar, (unsigned)(i + 1) * gridDim.x, C.wait_limit, A.status, &s_ok))
-            return;
-        // every tile's record in tile order (warp f sums value f; lane l takes
-        // tiles l, l + 32, ...; then a butterfly) -- the same order in every block
-        {
-            const float2* pf = reinterpret_cast<const float2*>(S.partials);
-            for (int f = warp; f < kRecWords; f += nw) {
-                ff sum = {0.f, 0.f};
-                for (int i0 = lane; i0 < nseg; i0 += 32 * 8) {
-                    float2 w[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        w[u] = i0 + 32 * u < nseg
-                                   ? __ldcg(pf + (int64_t)(seg0 + i0 + 32 * u) * kPartialWords + f)
-                                   : make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (i0 + 32 * u < nseg) sum = ff_add(sum, ff{w[u].x, w[u].y});
-                }
-                sum = warp_sum_ff(sum);
-                if (lane == 0) s_red[f] = make_float2(sum.hi, sum.lo);
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const MixedTheta& mt = S.mt[0];
-            ff dk;
-            StatsRec r1;
-            rec_from(s_red, dk, r1.s);
-            r1.mu = mt.mu;
-            r1.ximu = mt.ximu;
-            r1.sl = s_rec.sl;
-            r1.sll = s_rec.sll;
-            const double dH = stats_dH(dk, r1.s, s_rec, mt, T);
-            const int acc = metropolis_accept(nullptr, A.seed, g.series, traj, dH);
-            if (acc) {
-                s_rec = r1;
-                S.cur ^= 1;
-            }
-            if (b == 0) {
-                if (!isfinite(dH)) atomicOr(A.status, ST_NONFINITE);
-                if (C.dH_out) C.dH_out[i] = dH;
-                if (C.acc_out) C.acc_out[i] = acc;
-            }
-            if (MASS && C.fallback_window > 0) {
-                int na = s_fb[0] + acc, nt = s_fb[1] + 1;
-                if (nt >= C.fallback_window) {
-                    if (S.mass_on && 10 * na < 6 * nt) S.mass_on = 0;
-                    na = nt = 0;
-                }
-                s_fb[0] = na;
-                s_fb[1] = nt;
-            }
-        }
-        __syncthreads();
-        const bool more = i + 1 < C.n_traj;
-        if (C.update_theta) {
-            // warp 0: the theta sweep from the accepted state's statistics;
-            // the other warps: the next trajectory's momenta meanwhile
-            if (warp == 0) {
-                float th[5], tot[NSTAT], x0;
-#pragma unroll
-                for (int k = 0; k < 5; ++k) th[k] = s_th[k];
-                record_sums(s_rec, th, T, tot, x0);
-                WarpDrawsF st;
-                st.seed = A.seed;
-                st.series = (uint64_t)g.series;
-                st.traj = traj;
-                st.fill(T);
-                int phi_acc = 0;
-                gibbs_draws_f(tot, x0, T, th, st, 31, &phi_acc);
-                if (lane < 5) {
-                    float v = th[0];
-#pragma unroll
-                    for (int k = 1; k < 5; ++k)
-                        if (lane == k) v = th[k];
-                    s_th[lane] = v;
-                    if (b == 0) {
-                        C.theta[lane] = (double)v;
-                        if (C.theta_out) C.theta_out[5 * i + lane] = (double)v;
-                    }
-                }
-                if (lane == 0) S.mt[0] = mixed_theta_f(th);
-                if (!more || nw == 1) {
-                    if (more) draw_slots<J>(A, traj + 1, g, s_ph, NS, lane, 32);
-                }
-            } else if (more) {
-                draw_slots<J>(A, traj + 1, g, s_ph, NS, tid - 32, NT - 32);
-            }
-            __syncthreads();
-            for (int k = tid + 32; k < nw * 32; k += NT)
-                reinterpret_cast<float*>(S.mt)[k] = reinterpret_cast<const float*>(S.mt)[k & 31];
-        } else {
-            if (b == 0 && C.theta_out && tid < 5) C.theta_out[5 * i + tid] = s_thd[tid];
-            if (more) draw_slots<J>(A, traj + 1, g, s_ph, NS, tid, NT);
-        }
-        __syncthreads();
+        traj_mixed_bin<J, MASS, false, true>(C.A, blockIdx.x, S, smem_raw, snap_prev);
+        if (!chain_after<J, MASS>(C, S, Q, smem_raw)) return;
     }
-
     // the last snapshot, if due, and the final state selector and mass flag
     if (C.snaps && C.n_traj > 0 && C.n_traj % C.thin == 0) {
-        const float2* hc = S.cur ? A.h1f : A.h0f;
-        float* dst = C.snaps + (size_t)(C.n_traj / C.thin - 1) * (size_t)T;
-        const int64_t off = A.ser[g.series].off;
-        for (int64_t s = g.lo + tid; s < g.hi; s += NT) {
+        const float2* hc = S.cur ? C.A.h1f : C.A.h0f;
+        float* dst = C.snaps + (size_t)(C.n_traj / C.thin - 1) * (size_t)Q.T;
+        const int64_t off = C.A.ser[Q.g.series].off;
+        for (int64_t s = Q.g.lo + threadIdx.x; s < Q.g.hi; s += blockDim.x) {
             const float2 hv = __ldcg(hc + off + s);
             dst[off + s] = hv.x + hv.y;
         }
     }
-    if (b == 0 && tid == 0) {
-        C.ser_cur_out[g.series] = S.cur;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        C.ser_cur_out[Q.g.series] = S.cur;
         if (C.mass_on_out) *C.mass_on_out = S.mass_on;
     }
+}
+
+// Whether every block of the plan can be resident at once (the grid barrier
+// waits for all of them).
+template <int J, bool MASS>
+cudaError_t chain_fits_j(const Plan& p, int num_sms, bool* fits)
+{
+    auto k = k_chain_mixed<J, MASS>;
+    *fits = false;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p.smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p.nt, p.smem);
+    if (e != cudaSuccess) return e;
+    *fits = (int64_t)per_sm * num_sms >= p.nbins;
+    return cudaSuccess;
 }
 
 template <int J, bool MASS>
@@ -263,14 +337,10 @@ cudaError_t launch_chain_j(const ChainArgs& c, const Plan& p, int num_sms, cudaS
                            bool* launched)
 {
     auto k = k_chain_mixed<J, MASS>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)p.smem);
+    bool fits = false;
+    cudaError_t e = chain_fits_j<J, MASS>(p, num_sms, &fits);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p.nt, p.smem);
-    if (e != cudaSuccess) return e;
-    // every tile must be resident at once (the grid barrier waits for all)
-    if ((int64_t)per_sm * num_sms < p.nbins) {
+    if (!fits) {
         *launched = false;
         return cudaSuccess;
     }
@@ -287,6 +357,25 @@ bool chain_supported(const Plan& p)
 {
     return p.mixed && !p.lev && p.nseries == 1 && p.grid == p.nbins &&
            (p.j == 4 || p.j == 8 || p.j == 12 || p.j == 16 || p.j == 20);
+}
+
+cudaError_t chain_fits(const Plan& p, int num_sms, bool* fits)
+{
+    *fits = false;
+    if (!chain_supported(p)) return cudaSuccess;
+#define RSV_CF(JJ)                                                                        \
+    case JJ:                                                                              \
+        return p.mass ? chain_fits_j<JJ, true>(p, num_sms, fits)                          \
+                      : chain_fits_j<JJ, false>(p, num_sms, fits);
+    switch (p.j) {
+        RSV_CF(4)
+        RSV_CF(8)
+        RSV_CF(12)
+        RSV_CF(16)
+        RSV_CF(20)
+        default: return cudaSuccess;
+    }
+#undef RSV_CF
 }
 
 cudaError_t launch_chain(const ChainArgs& c, const Plan& p, int num_sms, cudaStream_t st,

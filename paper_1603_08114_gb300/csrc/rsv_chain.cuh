@@ -36,6 +36,8 @@ struct ChainArgs {
 // True if the plan can run as one persistent chain (mixed, no leverage, one
 // series, every bin on its own block, an instantiated block shape).
 bool chain_supported(const Plan& p);
+// *fits: the plan is supported and all its blocks can be resident at once.
+cudaError_t chain_fits(const Plan& p, int num_sms, bool* fits);
 // Launch the chain cooperatively; *launched is false (and nothing is
 // launched) if the plan's blocks cannot all be resident at once.
 cudaError_t launch_chain(const ChainArgs& c, const Plan& p, int num_sms, cudaStream_t st,

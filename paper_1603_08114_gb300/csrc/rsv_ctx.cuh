@@ -56,6 +56,7 @@ struct rsv_ctx {
         bool mixed, mass, lev;
         int nt, j;
         int64_t tile;
+        bool chain;
         rsv::Plan plan;
     };
     std::vector<Cached> plans;

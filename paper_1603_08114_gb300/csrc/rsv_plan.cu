@@ -62,7 +62,7 @@ void free_plan(Plan& p)
 
 bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambda, bool mixed,
                bool mass, bool lev, int num_sms, int sched_nt, int sched_j, int64_t sched_tile,
-               Plan& P, const char** why)
+               Plan& P, const char** why, bool chain)
 {
     // one site of staleness per force evaluation
     const int64_t K = (int64_t)n_md * make_scheme(integrator, lambda).nk + 1;
@@ -137,8 +137,14 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
                     double cost = (double)waves * (double)cap * bps;
                     // measured on the mixed kernel at T = 2^20 (fixed and
                     // per-step cost per block shape): J = 12 with ~600
-                    // threads is the fastest, J = 20 close, J = 16 and 8 slower
-                    if (mixed) cost *= js[ji] == 12 ? 1.0 : js[ji] == 20 ? 1.03 : 1.08;
+                    // threads is the fastest, J = 20 close, J = 16 and 8
+                    // slower; inside the persistent chain J = 16 with ~450
+                    // threads is the fastest (93.8 against 100.6 us per
+                    // trajectory for J = 12), J = 20 close
+                    if (mixed && chain)
+                        cost *= js[ji] == 16 ? 1.0 : js[ji] == 20 ? 1.02 : js[ji] == 12 ? 1.06 : 1.1;
+                    else if (mixed)
+                        cost *= js[ji] == 12 ? 1.0 : js[ji] == 20 ? 1.03 : 1.08;
                     cost *= 1.0 + 1e-3 * (double)(tmax - t) / tmax;
                     if (cost < best) {
                         best = cost;

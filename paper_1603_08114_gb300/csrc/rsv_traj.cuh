@@ -290,9 +290,11 @@ struct TrajArgs {
 // sched_nt / sched_j / sched_tile > 0 fix the tiling, 0 chooses it.
 // Returns false (reason in *why) if no tiling fits.
 // integrator / lambda: see Plan; the halo is n_md * (forces per step) + 1.
+// chain: the plan of a series run as one persistent chain (its own block-shape
+// preference).
 bool make_plan(const int64_t* offsets, int n, int n_md, int integrator, double lambda, bool mixed,
                bool mass, bool lev, int num_sms, int sched_nt, int sched_j, int64_t sched_tile,
-               Plan& plan, const char** why);
+               Plan& plan, const char** why, bool chain = false);
 void free_plan(Plan& plan);
 
 cudaError_t launch_traj(const TrajArgs& a, const Plan& p, cudaStream_t st);

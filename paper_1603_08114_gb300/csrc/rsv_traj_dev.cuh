@@ -123,23 +123,25 @@ __device__ __forceinline__ void load_bin(const TrajArgs& A, int b, int* s_wseg, 
 // 1e-6 (1 + |ln u|) of -dH, where the comparison could go either way, is it
 // taken in FP64, so the decision is the FP64 comparison's at the cost of one
 // FP64 logarithm in about a million trajectories.
+// The drawn uniform of trajectory traj's Metropolis test.
+__device__ __forceinline__ double metropolis_u(uint64_t seed, int series, uint64_t traj)
+{
+    const u64x4 w = philox_block(seed, (uint64_t)series, traj, STREAM_MH, 0);
+    return u01_53(w.w[0]);
+}
+__device__ int metropolis_accept_u(double u, double dH)
+{
+    if (!isfinite(dH)) return 0;
+    const float lf = logf((float)u);
+    const double gap = (double)lf + dH;  // ln u - (-dH), to within the margin
+    if (fabs(gap) > 1e-6 * (1.0 + fabs((double)lf))) return gap < 0.0 ? 1 : 0;
+    return log(u) < -dH ? 1 : 0;
+}
 __device__ int metropolis_accept(const double* log_u, uint64_t seed, int series, uint64_t traj,
                                  double dH)
 {
-    const bool fin = isfinite(dH);
-    int acc;
-    if (log_u) {
-        acc = (fin && log_u[series] < -dH) ? 1 : 0;
-    } else {
-        const u64x4 w = philox_block(seed, (uint64_t)series, traj, STREAM_MH, 0);
-        const double u = u01_53(w.w[0]);
-        const float lf = logf((float)u);
-        const double gap = (double)lf + dH;  // ln u - (-dH), to within the margin
-        if (!fin) acc = 0;
-        else if (fabs(gap) > 1e-6 * (1.0 + fabs((double)lf))) acc = gap < 0.0 ? 1 : 0;
-        else acc = log(u) < -dH ? 1 : 0;
-    }
-    return acc;
+    if (log_u) return (isfinite(dH) && log_u[series] < -dH) ? 1 : 0;
+    return metropolis_accept_u(metropolis_u(seed, series, traj), dH);
 }
 __device__ int decide(const TrajArgs& A, int series, double dH, int cur, bool flip)
 {
@@ -1030,14 +1032,16 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
     hparts_zero(acc);
     StateStats st;
     stats_zero(st);
-#pragma unroll 1
+    // four sites per iteration: each site's double-float sums are a long
+    // dependent chain, and interleaved chains keep the pipes busier
+#pragma unroll 4
     for (int j = 0; j < J; ++j) {
         const int64_t sg = wlo + base + j;
         if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
+        const float2 lr = A.lr_f[off + sg];
         const ff x = {s_xh[j * NS + tid], s_xl[j * NS + tid]};
         const int nidx = j + 1 < J ? (j + 1) * NS + tid : tid + 1;
         const ff xn = {s_xh[nidx], s_xl[nidx]};
-        const float2 lr = A.lr_f[off + sg];
         const ff mw = MASS ? mass_weight(mc.kick, dm_at(j)) : ff{1.f, 0.f};
         const bool has_next = sg + 1 < v.si.T;
         const ff pv = {s_ph[j * NS + tid], k_at(j)};

@@ -65,6 +65,9 @@ def lib():
         L.rsv_set_leverage.argtypes = [_P, ctypes.c_double]
         L.rsv_set_persistent.argtypes = [_P, _INT]
         L.rsv_set_wait_limit.argtypes = [_P, _I64]
+        L.rsv_chain_schedule.argtypes = [_P, _I64, _INT, _INT, _INT, ctypes.POINTER(_INT),
+                                         ctypes.POINTER(_INT), ctypes.POINTER(_I64),
+                                         ctypes.POINTER(_INT)]
         L.rsv_action.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
         L.rsv_force.argtypes = [_P, _P, _P, _P, _I64, Theta, _P, _P]
         L.rsv_hmc_trajectory.argtypes = [_P, _P, _P, _P, _P, _I64, Theta, _P, _INT,
@@ -89,7 +92,7 @@ def lib():
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
                      "rsv_timing", "rsv_stats", "rsv_gibbs_theta", "rsv_plan_create",
                      "rsv_plan_info", "rsv_hmc_batched", "rsv_pipe_probe", "rsv_set_persistent",
-                     "rsv_set_wait_limit"):
+                     "rsv_set_wait_limit", "rsv_chain_schedule"):
             getattr(L, name).restype = _INT
         _lib = L
     return _lib
@@ -171,6 +174,16 @@ def rsv_set_persistent(ctx: Context, enable: bool = True):
 def rsv_set_wait_limit(ctx: Context, cycles: int = 0):
     """Clock cycles a device-side wait may spin before RSV_ETIMEOUT (0: default)."""
     _check(lib().rsv_set_wait_limit(ctx.handle, int(cycles)))
+
+
+def rsv_chain_schedule(ctx: Context, T: int, n_md: int, prec="mixed", with_mass=False):
+    """The block shape of an rsv_hmc_chain call and whether it runs persistent."""
+    nt, j, tile, pers = _INT(), _INT(), _I64(), _INT()
+    _check(lib().rsv_chain_schedule(ctx.handle, int(T), int(n_md), _prec(prec),
+                                    int(bool(with_mass)), ctypes.byref(nt), ctypes.byref(j),
+                                    ctypes.byref(tile), ctypes.byref(pers)))
+    return {"threads": nt.value, "sites_per_thread": j.value, "tile": tile.value,
+            "persistent": bool(pers.value)}
 
 
 def rsv_set_leverage(ctx: Context, rho: float = 0.0):
