@@ -90,8 +90,9 @@ rsv_status rsv_sync_status(rsv_ctx* ctx, void* stream);
  * 16, 28; mixed: 4, 8, 16, 20) and `tile` owned sites per tile of a series cut
  * into tiles (tile + 2 (n_md + 1) + 3 <= threads * sites_per_thread, else the
  * call that uses it fails with RSV_EINVAL).  A single series no longer than
- * `tile` is kept whole.  All zero restores the automatic plan.  Results do not
- * depend on the tiling. */
+ * `tile` is kept whole (it then needs only T <= threads * sites_per_thread).
+ * All zero restores the automatic plan.  Results depend on the tiling only
+ * through rounding (the order of the sums). */
 rsv_status rsv_set_schedule(rsv_ctx* ctx, int threads, int sites_per_thread, int64_t tile);
 /* rsv_set_persistent: 1 (the default) runs an rsv_hmc_chain call in RSV_MIXED
  * precision on the model without leverage as ONE persistent cooperative

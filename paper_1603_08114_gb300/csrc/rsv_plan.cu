@@ -85,8 +85,11 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
     int nt = 0, j = 0;
     int64_t tile = 0;
     if (sched_nt > 0) {
+        // a single series no longer than the tile is kept whole: it needs the
+        // window only, no halo
+        const bool whole1 = n == 1 && sched_tile >= Tmax && Tmax <= (int64_t)sched_nt * sched_j;
         if (!valid_j(mixed, sched_j) || sched_nt % 32 || sched_nt > ntmax(mixed, mass, sched_j) ||
-            sched_tile < 1 || sched_tile + 2 * K + 3 > (int64_t)sched_nt * sched_j ||
+            sched_tile < 1 || (!whole1 && sched_tile + 2 * K + 3 > (int64_t)sched_nt * sched_j) ||
             smem_for(mixed, mass, lev, sched_nt, sched_j) > smem_cap) {
             *why = "the fixed schedule does not fit this call";
             return false;

@@ -33,7 +33,13 @@ def dev(a, dtype=torch.float64):
 
 def run(rsv, ctx, s, persistent, n, n_md, dtau, minv=None, update_theta=True, thin=1, fb=0,
         seed=5, integrator="leapfrog"):
+    """One chain call; both paths on the tiling the persistent chain takes
+    (the planner prefers another block shape for per-trajectory launches, and
+    results depend on the tiling through their rounding only)."""
     T = len(s.y)
+    rsv.rsv_set_integrator(ctx, integrator)
+    cs = rsv.rsv_chain_schedule(ctx, T, n_md, "mixed", with_mass=minv is not None)
+    rsv.rsv_set_schedule(ctx, cs["threads"], cs["sites_per_thread"], cs["tile"])
     h, th = dev(s.h_true), dev(TH)
     snaps = torch.full((n // thin, T), float("nan"), dtype=torch.float32, device="cuda")
     ths = torch.full((n, 5), float("nan"), dtype=torch.float64, device="cuda")
@@ -53,6 +59,7 @@ def run(rsv, ctx, s, persistent, n, n_md, dtau, minv=None, update_theta=True, th
     finally:
         rsv.rsv_set_persistent(ctx, True)
         rsv.rsv_set_integrator(ctx, "leapfrog")
+        rsv.rsv_set_schedule(ctx)
     return {k: v.cpu().numpy() for k, v in dict(h=h, th=th, snaps=snaps, ths=ths, dH=dH,
                                                  acc=acc, used=used).items()}
 
