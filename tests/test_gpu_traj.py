@@ -294,7 +294,8 @@ def test_invalid_arguments_rejected(rsv, ctx):
     with pytest.raises(rsv.RSVError, match="RSV_EINVAL"):
         rsv.rsv_force(ctx, h, y, lr, TH, F_out=h)
     with pytest.raises(rsv.RSVError, match="RSV_EINVAL"):
-        rsv.rsv_set_schedule(ctx, 64, 8, 10)
+        # T = 10 cut into tiles of 5 needs halos of 301 sites: no window holds them
+        rsv.rsv_set_schedule(ctx, 64, 8, 5)
         rsv.rsv_hmc_trajectory(ctx, h, None, y, lr, TH, 300, 0.02)
     rsv.rsv_set_schedule(ctx)
     assert np.array_equal(h.cpu().numpy(), s.h0)
