@@ -1078,6 +1078,44 @@ def run_table2(args):
     return 0
 
 
+def run_profile_chain(args):
+    """The headline's chain for a profiler: T = 2^20, a mass of the learned
+    mass's shape (m ~ 30, fixed: no training), 78 x 0.035, theta sampled,
+    every state recorded; one warm-up call, then one call of K trajectories
+    (`ncu -k regex:k_chain_mixed -s 1 -c 1` takes that one)."""
+    import torch
+
+    from paper_1603_08114_gb300 import rsv, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = rsv.Context(0)
+    K = int(args.profile_chain)
+    s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA)
+    y, lnrv = torch.tensor(s.y, device=dev), torch.tensor(s.lnrv, device=dev)
+    m = 30.0 + 3.0 * np.random.default_rng(3).random(T_SITES)
+    minv = torch.tensor((1.0 / m).astype(np.float32), device=dev)
+    rsv.rsv_reserve(ctx, T_SITES)
+    h = torch.tensor(s.h_true, device=dev)
+    th = torch.tensor(s.theta, dtype=torch.float64, device=dev)
+    snaps = torch.empty(K, T_SITES, dtype=torch.float32, device=dev)
+    thetas = torch.empty(K, 5, dtype=torch.float64, device=dev)
+    acc = torch.empty(K, dtype=torch.int32, device=dev)
+    for k in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, 78, 0.035, K, prec="mixed", minv=minv, seed=11,
+                          traj0=k * K, snaps=snaps, thin=1, theta_out=thetas, accept_out=acc,
+                          update_theta=True)
+        b.record()
+        b.synchronize()
+    rsv.rsv_sync_status(ctx)
+    cs = rsv.rsv_chain_schedule(ctx, T_SITES, 78, "mixed", with_mass=True)
+    print(json.dumps({"profile_chain": K, "us_per_trajectory": 1e3 * a.elapsed_time(b) / K,
+                      "accept_rate": float(acc.float().mean()), "schedule": cs}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1097,6 +1135,8 @@ def main():
                     help="plain-sampler snapshots for the learned mass")
     ap.add_argument("--table2", action="store_true",
                     help="time per elementary step vs B (T = 512 B) like the paper's Table 2")
+    ap.add_argument("--profile-chain", type=int, default=0,
+                    help="run the headline chain twice with K trajectories (profiling)")
     args = ap.parse_args()
     if args.traj_per_step:
         global N_TRAJ
@@ -1107,6 +1147,8 @@ def main():
         return run_reference(args)
     if args.table2:
         return run_table2(args)
+    if args.profile_chain:
+        return run_profile_chain(args)
     return run_ours(args)
 
 
