@@ -65,7 +65,9 @@ IMPL_OPS_PER_SITE_STEP_MIXED = 13
 # kernel (the persistent chain kernel: one launch's bytes over its
 # trajectories; the inputs stay in L2 between trajectories), from the capture
 # summarised in profiles/; valid for the kernel revision it was taken on.
-TRAFFIC = {"kernel": "k_chain_mixed", "kernel_rev": 13, "bytes_per_trajectory": None}
+# (the capture: `python bench.py --profile-chain 10`, one launch of 10
+# trajectories, cold L2: 25.34 MB read + 4.56 MB written).
+TRAFFIC = {"kernel": "k_chain_mixed", "kernel_rev": 13, "bytes_per_trajectory": 2989568}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -334,25 +336,25 @@ def run_ours(args):
                               seed=11 + rank, traj0=traj, snaps=sn, thin=1, accept_out=ac,
                               update_theta=True, theta_out=tho)
 
-    def site_moments(snaps_all, ess):
-        """Per-site posterior mean and variance of h over the chain, with their
-        Monte-Carlo standard errors (sd / sqrt(ESS); the variance's from the
-        squared deviations' own sd)."""
+    def site_moments(snaps_all):
+        """Per-site posterior mean and variance of h over the chain with their
+        Monte-Carlo standard errors by batch means (sqrt(n) batches of
+        consecutive draws; the variance's from the batch means of the squared
+        deviations): they include the slow theta direction that a per-site
+        ESS from the leading autocorrelations would miss."""
         n = snaps_all.shape[0]
-        m = torch.zeros(T_SITES, dtype=torch.float64, device=dev)
-        for i in range(0, n, 250):
-            m += snaps_all[i:i + 250].double().sum(0)
-        m /= n
-        v = torch.zeros_like(m)
-        q = torch.zeros_like(m)
-        for i in range(0, n, 250):
-            d2 = (snaps_all[i:i + 250].double() - m) ** 2
-            v += d2.sum(0)
-            q += (d2 ** 2).sum(0)
-        v /= n
-        sd_d2 = torch.sqrt(torch.clamp(q / n - v * v, min=0.0))
-        e = torch.clamp(ess.double(), min=1.0)
-        return dict(mean=m, var=v, mcse_mean=torch.sqrt(v / e), mcse_var=sd_d2 / torch.sqrt(e))
+        nb = max(2, int(n ** 0.5))
+        bl = n // nb
+        bm = torch.empty(nb, T_SITES, dtype=torch.float64, device=dev)
+        for b in range(nb):
+            bm[b] = snaps_all[b * bl:(b + 1) * bl].double().mean(0)
+        m = bm.mean(0)
+        bq = torch.empty_like(bm)
+        for b in range(nb):
+            bq[b] = ((snaps_all[b * bl:(b + 1) * bl].double() - m) ** 2).mean(0)
+        v = bq.mean(0)
+        return dict(mean=m, var=v, mcse_mean=bm.std(0) / nb ** 0.5,
+                    mcse_var=bq.std(0) / nb ** 0.5, batches=nb)
 
     def arm(prec, mass, warmup, steps, clocks=None, timing=False, n_md=N_MD, dtau=DTAU,
             sampler=None, moments=False, nvtx=False):
@@ -412,7 +414,7 @@ def run_ours(args):
         ess = rsv.rsv_ess(ctx, snaps_all)
         ess_th = rsv.rsv_ess(ctx, thetas_all.float().contiguous()).cpu().numpy()
         ess_med, ess_min = float(ess.median()), float(ess.min())
-        mom = site_moments(snaps_all, ess) if moments else None
+        mom = site_moments(snaps_all) if moments else None
         del snaps_all
         return dict(
             site_updates_per_s=job_rate(ws, T_SITES * md_per_step, sec_per_step),
@@ -657,14 +659,24 @@ def run_ours(args):
         z_m = (a["mean"] - b["mean"]).abs() / torch.sqrt(a["mcse_mean"] ** 2 + b["mcse_mean"] ** 2)
         z_v = (a["var"] - b["var"]).abs() / torch.sqrt(a["mcse_var"] ** 2 + b["mcse_var"] ** 2)
         q = torch.tensor([0.5, 0.999], dtype=torch.float64, device=dev)
+        # under equal moments z is about Student-t with (batches - 1) degrees of
+        # freedom (each MCSE from sqrt(n) batch means)
+        dof = min(a["batches"], b["batches"]) - 1
+        try:
+            from scipy import stats as sps
+            expected = float(2 * sps.t.sf(3.5, dof))
+        except ImportError:
+            expected = 4.65e-4
         return {"sites": T_SITES,
                 "mean_z_median_p999": [float(v) for v in torch.quantile(z_m[::8], q)],
                 "mean_frac_z_over_3.5": float((z_m > 3.5).double().mean()),
                 "var_z_median_p999": [float(v) for v in torch.quantile(z_v[::8], q)],
                 "var_frac_z_over_3.5": float((z_v > 3.5).double().mean()),
-                "expected_frac_z_over_3.5": 4.65e-4,
+                "expected_frac_z_over_3.5": expected,
+                "batches": [a["batches"], b["batches"]],
                 "how": "per-site mean and variance of h over each arm's whole timed chain; "
-                       "MCSE = sd / sqrt(ESS) (the variance's from the squared deviations)"}
+                       "MCSE by batch means with sqrt(n) batches (the variance's from the "
+                       "squared deviations); z = |difference| / combined MCSE"}
 
     # headline: mixed precision (diagonal mass when given)
     # learned diagonal mass (untimed set-up): moments of the plain sampler over
@@ -723,7 +735,9 @@ def run_ours(args):
     ident = fp64 = batched = mn = mn4 = levr = c1 = c4 = t2gpu = c5 = None
     if args.only != "mixed":
         if minv is not None:
-            ident = arm("mixed", None, min(args.warmup, 3), min(args.steps, 3), moments=True)
+            # the same chain length as the headline: the moment comparison
+            # needs both chains to have explored theta alike
+            ident = arm("mixed", None, min(args.warmup, 3), args.steps, moments=True)
             c5 = c5_compare(head, ident)
         fp64 = arm("fp64", None, min(args.warmup, 3), min(args.steps, 3), timing=True)
         batched = batched_leg(max(3, min(args.steps, 10)))
