@@ -147,6 +147,9 @@ __device__ __noinline__ void chain_setup(const ChainArgs& C, MixedSmem<false>& S
         S.mass_on = MASS ? 1 : 0;
     }
     draw_slots<J>(A, C.traj0, g, chain_s_ph<J, MASS>(smem_raw), mixed_row(NT, J), tid, NT);
+    // the block's view, filed for every trajectory of the chain
+    View v;
+    load_bin<false>(A, blockIdx.x, S.wseg, S.wacc, v, S.wg, S.wsi, S.wcur);
     __syncthreads();
 }
 
@@ -176,24 +179,28 @@ __device__ __noinline__ bool chain_after(const ChainArgs& C, MixedSmem<false>& S
     if (!grid_barrier(C.bar, (unsigned)(i + 1) * gridDim.x, C.wait_limit, A.status, &Q.ok))
         return false;
     if (warp < kRecWords) {
-        // every tile's record value f = warp in tile order (lane l takes tiles
-        // l, l + 32, ...; then a butterfly) -- the same order in every block
+        // every tile's record value f in tile order (lane l takes tiles l,
+        // l + 32, ...; then a butterfly) -- the same order in every block;
+        // warp w sums the values f = w, w + nw, ... (one each when the block
+        // has 8 warps or more)
         const float2* pf = reinterpret_cast<const float2*>(S.partials);
-        const int nseg = Q.nseg, seg0 = Q.seg0, f = warp;
-        ff sum = {0.f, 0.f};
-        for (int i0 = lane; i0 < nseg; i0 += 32 * 8) {
-            float2 w[8];
+        const int nseg = Q.nseg, seg0 = Q.seg0;
+        for (int f = warp; f < kRecWords; f += nw) {
+            ff sum = {0.f, 0.f};
+            for (int i0 = lane; i0 < nseg; i0 += 32 * 8) {
+                float2 w[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                w[u] = i0 + 32 * u < nseg
-                           ? __ldcg(pf + (int64_t)(seg0 + i0 + 32 * u) * kPartialWords + f)
-                           : make_float2(0.f, 0.f);
+                for (int u = 0; u < 8; ++u)
+                    w[u] = i0 + 32 * u < nseg
+                               ? __ldcg(pf + (int64_t)(seg0 + i0 + 32 * u) * kPartialWords + f)
+                               : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (i0 + 32 * u < nseg) sum = ff_add(sum, ff{w[u].x, w[u].y});
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + 32 * u < nseg) sum = ff_add(sum, ff{w[u].x, w[u].y});
+            }
+            sum = warp_sum_ff(sum);
+            if (lane == 0) Q.red[f] = make_float2(sum.hi, sum.lo);
         }
-        sum = warp_sum_ff(sum);
-        if (lane == 0) Q.red[f] = make_float2(sum.hi, sum.lo);
         if (split) asm volatile("bar.sync 1, %0;" ::"r"(kRecWords * 32) : "memory");
         else __syncthreads();
     } else {

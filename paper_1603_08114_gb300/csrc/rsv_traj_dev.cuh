@@ -71,8 +71,9 @@ struct View {
 };
 
 // This warp's view, from the segment ids already placed in s_wseg (no
-// barrier; a kernel may call it again after its step loop instead of keeping
-// the view in registers through the loop).
+// barrier).  TH: also theta of the series in FP64 (the mixed kernels keep
+// theta's constants in shared memory and skip those loads).
+template <bool TH = true>
 __device__ __forceinline__ void view_of(const TrajArgs& A, const int* s_wseg, View& v)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -80,14 +81,16 @@ __device__ __forceinline__ void view_of(const TrajArgs& A, const int* s_wseg, Vi
     if (v.sid >= 0) {
         v.g = A.segs[v.sid];
         v.si = A.ser[v.g.series];
-        v.th = A.theta ? load_theta(A.theta + 5 * (int64_t)v.g.series) : A.th_inline;
-        v.th.rho = A.rho;
+        if (TH) {
+            v.th = A.theta ? load_theta(A.theta + 5 * (int64_t)v.g.series) : A.th_inline;
+            v.th.rho = A.rho;
+        }
         v.cur = A.ser_cur ? *(volatile int*)(A.ser_cur + v.g.series) : 0;
     } else {
         // idle warp: an empty segment with harmless parameters
         v.g = Seg{0, 0, 0, 0, 0, warp, 1, 0};
         v.si = SerInfo{0, 1, 1, 0};
-        v.th = ThetaD{0.5, 0.0, 0.0, 1.0, 1.0};
+        if (TH) v.th = ThetaD{0.5, 0.0, 0.0, 1.0, 1.0};
         v.cur = 0;
     }
     const int ts = (warp - v.g.warp0) * 32 + lane;  // thread index inside the segment
@@ -96,8 +99,14 @@ __device__ __forceinline__ void view_of(const TrajArgs& A, const int* s_wseg, Vi
     v.first = (ts == 0);
 }
 
+// The segments of bin b into s_wseg (one id per warp, -1 for an idle warp) and
+// this warp's view.  With wg/wsi/wcur given, the warp also files its segment,
+// series and current-buffer selector there (view_filed reads them back without
+// global loads).
+template <bool TH = true>
 __device__ __forceinline__ void load_bin(const TrajArgs& A, int b, int* s_wseg, int* s_wacc,
-                                         View& v)
+                                         View& v, Seg* wg = nullptr, SerInfo* wsi = nullptr,
+                                         int* wcur = nullptr)
 {
     const int tid = threadIdx.x;
     __syncthreads();
@@ -113,7 +122,28 @@ __device__ __forceinline__ void load_bin(const TrajArgs& A, int b, int* s_wseg, 
         for (int w = g.warp0; w < g.warp0 + g.nwarp && w < NWMAX; ++w) s_wseg[w] = id;
     }
     __syncthreads();
-    view_of(A, s_wseg, v);
+    view_of<TH>(A, s_wseg, v);
+    if (wg && (tid & 31) == 0) {
+        const int warp = tid >> 5;
+        wg[warp] = v.g;
+        wsi[warp] = v.si;
+        wcur[warp] = v.cur;
+    }
+}
+
+// The view load_bin filed for this warp (theta not included).
+__device__ __forceinline__ void view_filed(const int* s_wseg, const Seg* wg, const SerInfo* wsi,
+                                           const int* wcur, View& v)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v.sid = s_wseg[warp];
+    v.g = wg[warp];
+    v.si = wsi[warp];
+    v.cur = wcur[warp];
+    const int ts = (warp - v.g.warp0) * 32 + lane;
+    v.n = (int)(v.g.whi - v.g.wlo);
+    v.base = ts;
+    v.first = (ts == 0);
 }
 
 // Metropolis decision of one series (Sec. 3): accept iff ln u < -dH; a
@@ -733,6 +763,10 @@ __device__ void finish_split_stats(const TrajArgs& A, const View& v, const float
 template <bool LEV>
 struct MixedSmem {
     int wseg[NWMAX], wacc[NWMAX], flag;
+    // each warp's segment, series and current-buffer selector (load_bin)
+    Seg wg[NWMAX];
+    SerInfo wsi[NWMAX];
+    int wcur[NWMAX];
     double edge_d[4 * NWMAX];
     float2 exptab[32];
     MixedTheta mt[NWMAX];
@@ -821,7 +855,10 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
     ff h0;             // this thread's owned-site H at the start
     {
         View v;
-        load_bin(A, b, s_wseg, s_wacc, v);
+        // a persistent chain filed its block's view once, before its first
+        // trajectory
+        if (PERSIST) view_filed(s_wseg, S.wg, S.wsi, S.wcur, v);
+        else load_bin<false>(A, b, s_wseg, s_wacc, v, S.wg, S.wsi, S.wcur);
         if (PERSIST) v.cur = S.cur;
         const int base = v.base * J;
         if (!PERSIST)  // a persistent chain keeps the constants of its theta in s_mt
@@ -1023,7 +1060,7 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
     }
     __syncthreads();
     View v;
-    view_of(A, s_wseg, v);
+    view_filed(s_wseg, S.wg, S.wsi, S.wcur, v);
     if (PERSIST) v.cur = S.cur;
     const int base = v.base * J;
     const MixedTheta& mt = s_mt[warp];
