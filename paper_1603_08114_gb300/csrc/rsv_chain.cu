@@ -113,7 +113,7 @@ __device__ __forceinline__ float* chain_s_ph(unsigned char* smem_raw)
 {
     const int NT = blockDim.x, NS = mixed_row(NT, J);
     return reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) +
-                                    (size_t)(2 + (MASS ? 1 : 0)) * (J / 2) * NT) +
+                                    (size_t)(2 + (MASS ? 1 : 0)) * (J / 2) * mixed_ntp(NT)) +
            (size_t)2 * NS * J;
 }
 

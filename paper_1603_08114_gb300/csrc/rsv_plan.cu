@@ -33,7 +33,8 @@ const int kNJ_fp64 = 4, kNJ_mixed = 5;
 size_t smem_for(bool mixed, bool mass, bool lev, int nt, int j)
 {
     if (mixed)
-        return ((2 + (mass ? 1 : 0) + (lev ? 1 : 0)) * (size_t)nt + 3 * (size_t)mixed_row(nt, j)) *
+        return ((2 + (mass ? 1 : 0) + (lev ? 1 : 0)) * (size_t)mixed_ntp(nt) +
+                3 * (size_t)mixed_row(nt, j)) *
                (size_t)j * sizeof(float);
     return (2 + (mass ? 1 : 0)) * (size_t)nt * (size_t)j * sizeof(double);
 }

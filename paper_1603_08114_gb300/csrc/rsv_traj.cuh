@@ -311,6 +311,12 @@ cudaError_t launch_theta_prep(const double* theta, ThetaD th_inline, int n, doub
 // of one owner land in different banks (2- to 3-way at most).
 __host__ __device__ constexpr int mixed_row_pad(int j) { return (32 + j - 1) / j; }
 __host__ __device__ constexpr int mixed_row(int nt, int j) { return nt + mixed_row_pad(j); }
+// Row stride (in pair slots) of the mixed kernel's pair arrays (site
+// constants, -kick/m, leverage v): the block, so that a warp's float4 row
+// segment, which the leapfrog reads every step, is four whole 128-byte lines
+// (rows one slot longer, against the load pass's store conflicts, made the
+// leapfrog ~10 % slower).
+__host__ __device__ constexpr int mixed_ntp(int nt) { return nt; }
 // Largest block (threads) of the mixed kernel with `j` sites per thread, with
 // or without a mass (0 if j is not instantiated).
 int mixed_max_threads(int j, bool mass);

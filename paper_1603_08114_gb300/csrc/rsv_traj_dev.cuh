@@ -296,18 +296,18 @@ __device__ __forceinline__ void segment_decisions_ff(const TrajArgs& A, const Vi
 // that a block can run up to 32 warps; the per-site constants of the force sit
 // in shared memory and are read as float4.  Dynamic shared memory (slot-major:
 // slot j of thread tid at [j][tid]; pairs (p, p + P), P = J/2):
-//   s_ak  float4 [P][NT]  (-a_p, -a_{p+P}, k_p, k_{p+P}): a = y^2/2,
+//   s_ak  float4 [P][NTP]  (-a_p, -a_{p+P}, k_p, k_{p+P}): a = y^2/2,
 //                         k = 1/2 - c'/s_u^2
-//   s_dm  float2 [P][NT]  -kick/m of the pair (with a mass only; the state
+//   s_dm  float2 [P][NTP]  -kick/m of the pair (with a mass only; the state
 //                         then holds the velocity v = p/m)
-//   s_v   float2 [P][NT]  the leverage weights v of the pair (leverage only)
+//   s_v   float2 [P][NTP]  the leverage weights v of the pair (leverage only)
 //   s_xh, s_xl, s_ph  float [J][NS]  x (hi, lo) and p hi at the start of the
 //                         trajectory and again at its end (p lo then over k);
 //                         rows NS = mixed_row(NT, J) slots apart
-// The arrays the leapfrog reads every step keep rows of NT slots: a warp's
-// float4 (float2) row segment is then four (two) whole 128-byte lines; the
-// rows of the start and end state, which only the load and write passes and
-// the energies touch, are padded against bank conflicts instead.
+// The arrays the leapfrog reads every step keep rows of NTP = NT slots: a
+// warp's float4 (float2) row segment is then four (two) whole 128-byte lines;
+// the rows of the start and end state, which only the load and write passes
+// and the energies touch, are padded against bank conflicts instead.
 // ---------------------------------------------------------------------------
 // (with a mass and J = 4 at most 768 threads: its load pass needs more than
 // the 64 registers a 1024-thread block leaves)
@@ -364,7 +364,7 @@ __device__ __forceinline__ void cupd2(float2& hi, float2& lo, float2 c, float2 u
 // site takes x_P from before the step.
 // EDGE: some thread of the warp ends a series before its last slot; the ghost
 // replaces the right neighbour there by a select.
-// s_ak: float4 [P][NT] = (-a_p, -a_{p+P}, k_p, k_{p+P}); s_dm: float2 [P][NT]
+// s_ak: float4 [P][NTP] = (-a_p, -a_{p+P}, k_p, k_{p+P}); s_dm: float2 [P][NTP]
 // of -kick/m: with a diagonal mass the state carries the velocity v = p/m, so
 // that the drift x += c dtau v is the same for every site and the mass enters
 // the kick v -= kick F/m alone.
@@ -375,7 +375,7 @@ __device__ __forceinline__ void cupd2(float2& hi, float2& lo, float2 c, float2 u
 // the y-term weight a/(1-rho^2) at sites with a successor (the eps^2 part of
 // d_t^2), and cst x_0 at the series' first site, where the stationary row
 // (1-phi^2) x_0/s_eta^2 differs from the ghost's B (1-phi^2) x_0.
-// e^{-h} is taken as (e^{-h/2})^2 from one ex2.  s_v: float2 [P][NT] of v.
+// e^{-h} is taken as (e^{-h/2})^2 from one ex2.  s_v: float2 [P][NTP] of v.
 template <int J, bool MASS, bool EDGE, bool LEV, bool KV>
 __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J / 2],
                                             float2 (&PH)[J / 2], float2 (&PL)[J / 2],
@@ -385,7 +385,7 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
                                             int& par, int nw, int n_md, const MixedConst& c)
 {
     constexpr int P = J / 2;
-    const int NT = blockDim.x, tid = threadIdx.x;
+    const int NTP = mixed_ntp(blockDim.x), tid = threadIdx.x;
     const float2 c0 = f2(c.c0, c.c0), c1 = f2(c.c1, c.c1);
     const float2 nl2e = f2(-kLog2e, -kLog2e), cmu = f2(c.cmu, c.cmu);
     const float2 nl2h = f2(-0.5f * kLog2e, -0.5f * kLog2e), cmh = f2(0.5f * c.cmu, 0.5f * c.cmu);
@@ -411,7 +411,7 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
     // left neighbours; returns the pair's w.
     auto advance = [&](int q, float2 prev, float2 nxt, float2 cx, float hs, float2 e2,
                        float2 prevw) -> float2 {
-        const float4 ak = s_ak[q * NT + tid];
+        const float4 ak = s_ak[q * NTP + tid];
         const float2 xq = X[q];
         if (EDGE) {
             if (q == c.la) nxt.x = c.phi * xq.x;
@@ -422,7 +422,7 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
         float2 w = zero;
         if (LEV) {
             f = fma2(f2(ak.x, ak.y), fma2(e2, e2, zero), f);
-            w = fma2(s_v[q * NT + tid], e2, zero);
+            w = fma2(s_v[q * NTP + tid], e2, zero);
             const float2 g = fma2(half, fma2(nphi2, xq, nxt), phi2);
             f = sub2(fma2(w, g, f), prevw);
             if (q == 0) f.x = fmaf(c.cfirst, xq.x, f.x);
@@ -433,7 +433,7 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
         }
         // with a mass the state holds the velocity v = p/m: the kick takes
         // the per-site -kick/m, the drift is the same for every site
-        const float2 km = MASS ? (KV ? fma2(s_dm[q * NT + tid], kc, zero) : s_dm[q * NT + tid])
+        const float2 km = MASS ? (KV ? fma2(s_dm[q * NTP + tid], kc, zero) : s_dm[q * NTP + tid])
                                : (KV ? kc : ndt);
         cupd2(PH[q], PL[q], km, f);
         cupd2(X[q], XL[q], cx, PH[q]);
@@ -491,7 +491,7 @@ __device__ __forceinline__ void mixed_steps(float2 (&X)[J / 2], float2 (&XL)[J /
         // pair 0 (X[P-1] is still the state before the step), then P-1
         float2 prevw0 = zero;
         if (LEV) {
-            const float2 vP = s_v[(P - 1) * NT + tid];
+            const float2 vP = s_v[(P - 1) * NTP + tid];
             prevw0 = f2(c.vL * ex2_approx(fmaf(-0.5f * kLog2e, xL, 0.5f * c.cmu)),
                         vP.x * e2_last.x);
         }
@@ -822,18 +822,19 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
     float2& s_splitf = S.splitf;
     auto s_wrec = S.wrec;
     float2* s_splitrec = S.splitrec;
-    const int NT = blockDim.x, NS = mixed_row(NT, J), WS = NS * J, nw = NT >> 5;
+    const int NT = blockDim.x, NTP = mixed_ntp(NT), NS = mixed_row(NT, J), WS = NS * J,
+              nw = NT >> 5;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     float* s_edge = reinterpret_cast<float*>(S.edge_d);
     constexpr int P = J / 2;
-    float4* s_ak = reinterpret_cast<float4*>(smem_raw);  // [P][NT] (-a, -a', k, k') of (p, p+P)
+    float4* s_ak = reinterpret_cast<float4*>(smem_raw);  // [P][NTP] (-a, -a', k, k') of (p, p+P)
     float* s_ak1 = reinterpret_cast<float*>(smem_raw);
-    float2* s_dm = reinterpret_cast<float2*>(s_ak + P * NT);  // [P][NT] -kick/m of (p, p+P)
+    float2* s_dm = reinterpret_cast<float2*>(s_ak + P * NTP);  // [P][NTP] -kick/m of (p, p+P)
     float* s_dm1 = reinterpret_cast<float*>(s_dm);
-    float2* s_v = s_dm + (MASS ? P * NT : 0);  // [P][NT] leverage v of (p, p+P)
+    float2* s_v = s_dm + (MASS ? P * NTP : 0);  // [P][NTP] leverage v of (p, p+P)
     float* s_v1 = reinterpret_cast<float*>(s_v);
-    float* s_xh = reinterpret_cast<float*>(s_v + (LEV ? P * NT : 0));  // [J][NS]
+    float* s_xh = reinterpret_cast<float*>(s_v + (LEV ? P * NTP : 0));  // [J][NS]
     float* s_xl = s_xh + WS;
     float* s_ph = s_xl + WS;
     const bool mass_on =
@@ -841,10 +842,10 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
     const float dt = (float)A.dtau;
     // slot j is lane j / P of pair j % P
     // slot j of thread t
-    auto na_t = [&](int j, int t) -> float& { return s_ak1[((j % P) * NT + t) * 4 + j / P]; };
-    auto k_t = [&](int j, int t) -> float& { return s_ak1[((j % P) * NT + t) * 4 + 2 + j / P]; };
-    auto dm_t = [&](int j, int t) -> float& { return s_dm1[((j % P) * NT + t) * 2 + j / P]; };
-    auto v_t = [&](int j, int t) -> float& { return s_v1[((j % P) * NT + t) * 2 + j / P]; };
+    auto na_t = [&](int j, int t) -> float& { return s_ak1[((j % P) * NTP + t) * 4 + j / P]; };
+    auto k_t = [&](int j, int t) -> float& { return s_ak1[((j % P) * NTP + t) * 4 + 2 + j / P]; };
+    auto dm_t = [&](int j, int t) -> float& { return s_dm1[((j % P) * NTP + t) * 2 + j / P]; };
+    auto v_t = [&](int j, int t) -> float& { return s_v1[((j % P) * NTP + t) * 2 + j / P]; };
     auto na_at = [&](int j) -> float& { return na_t(j, tid); };
     auto k_at = [&](int j) -> float& { return k_t(j, tid); };
     auto dm_at = [&](int j) -> float& { return dm_t(j, tid); };
@@ -919,14 +920,20 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
         // the previous trajectory's snapshot, which is this one's start
         // state, in a loop of its own: a global store between the load
         // pass's loads would keep them from being issued together
+        // (all of the lane's loads first: one L2 round trip, not one per site)
         if (snap_prev) {
             const int wb = (warp - v.g.warp0) * 32 * J;
-            for (int kk = lane; kk < 32 * J; kk += 32) {
-                const int64_t sg = wlo + wb + kk;
-                if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) {
-                    const float2 hv = ld_state<PERSIST>(hin + off + sg);
-                    snap_prev[off + sg] = hv.x + hv.y;
-                }
+            float2 hv[J];
+#pragma unroll
+            for (int it = 0; it < J; ++it) {
+                const int64_t sg = wlo + wb + lane + 32 * it;
+                const bool own = v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi;
+                hv[it] = own ? ld_state<PERSIST>(hin + off + sg) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int it = 0; it < J; ++it) {
+                const int64_t sg = wlo + wb + lane + 32 * it;
+                if (v.sid >= 0 && sg >= v.g.lo && sg < v.g.hi) snap_prev[off + sg] = hv[it].x + hv[it].y;
             }
         }
         // pass 1b: site constants, x, mass -> shared memory, and H at the
@@ -1010,7 +1017,7 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
             }
         }
         __syncthreads();
-        mc.vL = (LEV && !v.first) ? s_v1[((P - 1) * NT + tid - 1) * 2 + 1] : 0.0f;
+        mc.vL = (LEV && !v.first) ? s_v1[((P - 1) * NTP + tid - 1) * 2 + 1] : 0.0f;
         mc.cfirst = (LEV && v.first) ? mt.cst : 0.0f;
         h0 = LEV ? hparts_total(acc, mt) : ff_add(acc.K, ff{0.f, 0.f});
         // registers <- shared memory, then the first half step of eq. (6)
@@ -1055,8 +1062,8 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
         s_xl[(q + P) * NS + tid] = XL[q].y;
         s_ph[q * NS + tid] = PH[q].x;
         s_ph[(q + P) * NS + tid] = PH[q].y;
-        k_at(q) = PL[q].x;
-        k_at(q + P) = PL[q].y;
+        // (k, k') of the pair, one 8-byte store
+        *reinterpret_cast<float2*>(&k_at(q)) = PL[q];
     }
     __syncthreads();
     View v;
