@@ -142,11 +142,13 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
                     // measured on the mixed kernel at T = 2^20 (fixed and
                     // per-step cost per block shape): J = 12 with ~600
                     // threads is the fastest, J = 20 close, J = 16 and 8
-                    // slower; inside the persistent chain J = 16 with ~450
-                    // threads is the fastest (93.8 against 100.6 us per
-                    // trajectory for J = 12), J = 20 close
+                    // slower; inside the persistent chain (78 steps, mass,
+                    // every state recorded) J = 20 with 384 threads is the
+                    // fastest, 89.5 us per trajectory against 92.1 for
+                    // J = 16 (448 threads) and 91.9 for J = 12 (608): per
+                    // site of a window 0.0117, 0.0128 and 0.0126 us
                     if (mixed && chain)
-                        cost *= js[ji] == 16 ? 1.0 : js[ji] == 20 ? 1.02 : js[ji] == 12 ? 1.06 : 1.1;
+                        cost *= js[ji] == 20 ? 0.91 : js[ji] == 16 ? 1.0 : js[ji] == 12 ? 0.98 : 1.1;
                     else if (mixed)
                         cost *= js[ji] == 12 ? 1.0 : js[ji] == 20 ? 1.03 : 1.08;
                     cost *= 1.0 + 1e-3 * (double)(tmax - t) / tmax;
