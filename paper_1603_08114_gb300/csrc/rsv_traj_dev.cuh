@@ -349,6 +349,92 @@ __device__ __forceinline__ void cupd2(float2& hi, float2& lo, float2 c, float2 u
     hi = t;
 }
 
+// ---- double-float arithmetic on pairs of lanes (FADD2/FMUL2/FFMA2) --------
+// An ff2 holds two independent double-floats, (hi.x, lo.x) and (hi.y, lo.y);
+// every operation is the scalar ff operation of rsv_device.cuh lane by lane,
+// with the same roundings, at half the instruction count.
+struct ff2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ float2 neg2(float2 a) { return f2(-a.x, -a.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ ff2 ff2_zero() { return ff2{f2(0.f, 0.f), f2(0.f, 0.f)}; }
+__device__ __forceinline__ ff2 two_sum2(float2 a, float2 b)
+{
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    return ff2{s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ ff2 fast_two_sum2(float2 a, float2 b)
+{
+    const float2 s = add2(a, b);
+    return ff2{s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ ff2 two_prod2(float2 a, float2 b)
+{
+    const float2 p = mul2(a, b);
+    return ff2{p, fma2(a, b, neg2(p))};
+}
+__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b)
+{
+    ff2 s = two_sum2(a.hi, b.hi);
+    s.lo = add2(s.lo, add2(a.lo, b.lo));
+    return fast_two_sum2(s.hi, s.lo);
+}
+__device__ __forceinline__ ff2 ff2_sub(ff2 a, ff2 b) { return ff2_add(a, ff2{neg2(b.hi), neg2(b.lo)}); }
+__device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b)
+{
+    ff2 p = two_prod2(a.hi, b.hi);
+    p.lo = fma2(a.hi, b.lo, fma2(a.lo, b.hi, p.lo));
+    return fast_two_sum2(p.hi, p.lo);
+}
+__device__ __forceinline__ ff2 ff2_mul_f(ff2 a, float2 b)
+{
+    ff2 p = two_prod2(a.hi, b);
+    p.lo = fma2(a.lo, b, p.lo);
+    return fast_two_sum2(p.hi, p.lo);
+}
+// acc += v (the small part renormalised only when read, as ff_acc)
+__device__ __forceinline__ void ff2_acc(ff2& acc, ff2 v)
+{
+    const ff2 s = two_sum2(acc.hi, v.hi);
+    acc.hi = s.hi;
+    acc.lo = add2(acc.lo, add2(s.lo, v.lo));
+}
+// the two lanes' sum, lane x first
+__device__ __forceinline__ ff ff2_fold(ff2 a)
+{
+    return ff_add(ff_add(ff{a.hi.x, a.lo.x}, ff{0.f, 0.f}), ff{a.hi.y, a.lo.y});
+}
+// ff_exp lane by lane: the reduction by ln2/32 and the polynomial on the
+// pair, the table look-up and the power-of-two scale per lane
+__device__ __forceinline__ ff2 ff2_exp(ff2 t, const float2* tab)
+{
+    const float2 C_hi = f2(0x1.62e43p-6f, 0x1.62e43p-6f), C_lo = f2(-0x1.05c61p-34f, -0x1.05c61p-34f);
+    const float2 sh = f2(0x1.8p23f, 0x1.8p23f);
+    const float2 kr = fma2(t.hi, f2(46.166241308446828f, 46.166241308446828f), sh);
+    const int k0 = __float_as_int(kr.x) - 0x4B400000, k1 = __float_as_int(kr.y) - 0x4B400000;
+    const float2 kf = sub2(kr, sh);
+    ff2 kc = two_prod2(kf, C_hi);
+    kc.lo = fma2(kf, C_lo, kc.lo);
+    const ff2 r = ff2_sub(t, kc);
+    const float2 x = r.hi;
+    const float2 poly =
+        fma2(x, fma2(x, fma2(x, f2(1.0f / 120.0f, 1.0f / 120.0f), f2(1.0f / 24.0f, 1.0f / 24.0f)),
+                     f2(1.0f / 6.0f, 1.0f / 6.0f)),
+             f2(0.5f, 0.5f));
+    const float2 q = mul2(mul2(x, x), poly);
+    ff2 sm = two_sum2(x, q);
+    sm.lo = add2(sm.lo, r.lo);
+    ff2 e = two_sum2(f2(1.0f, 1.0f), sm.hi);
+    e.lo = add2(e.lo, sm.lo);
+    e = fast_two_sum2(e.hi, e.lo);
+    const float2 t0 = tab[k0 & 31], t1 = tab[k1 & 31];
+    const ff2 res = ff2_mul(ff2{f2(t0.x, t1.x), f2(t0.y, t1.y)}, e);
+    const float2 sc = f2(__int_as_float(((k0 >> 5) + 127) << 23), __int_as_float(((k1 >> 5) + 127) << 23));
+    return ff2{mul2(res.hi, sc), mul2(res.lo, sc)};
+}
+
 // n_md leapfrog steps (eqs. (6)-(8)) with the two half steps of consecutive
 // steps merged: x += dt/2 p;  n_md times { p -= dt F(x); x += (dt, or dt/2 at
 // the end) p }.  The force of eq. (7) is taken in its three-point form
@@ -576,6 +662,18 @@ __device__ __forceinline__ ff mass_weight(float kick, float km)
     const float q = -kick * t;
     const float r = fmaf(-q, km, -kick);  // -kick - q km, exact
     return fast_two_sum(q, r * t);
+}
+
+// mass_weight lane by lane
+__device__ __forceinline__ ff2 mass_weight2(float2 kick, float2 km)
+{
+    float t0, t1;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t0) : "f"(km.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t1) : "f"(km.y));
+    const float2 t = f2(t0, t1);
+    const float2 q = mul2(neg2(kick), t);
+    const float2 r = fma2(neg2(q), km, neg2(kick));
+    return fast_two_sum2(q, mul2(r, t));
 }
 
 // The stationary term (1 - phi^2) x_1^2 / (2 s_eta^2) of S, into Q (weighted
@@ -1080,29 +1178,72 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
     hparts_zero(acc);
     StateStats st;
     stats_zero(st);
-    // four sites per iteration: each site's double-float sums are a long
-    // dependent chain, and interleaved chains keep the pipes busier
+    if constexpr (LEV) {
+        // four sites per iteration: each site's double-float sums are a long
+        // dependent chain, and interleaved chains keep the pipes busier
 #pragma unroll 4
-    for (int j = 0; j < J; ++j) {
-        const int64_t sg = wlo + base + j;
-        if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
-        const float2 lr = A.lr_f[off + sg];
-        const ff x = {s_xh[j * NS + tid], s_xl[j * NS + tid]};
-        const int nidx = j + 1 < J ? (j + 1) * NS + tid : tid + 1;
-        const ff xn = {s_xh[nidx], s_xl[nidx]};
-        const ff mw = MASS ? mass_weight(mc.kick, dm_at(j)) : ff{1.f, 0.f};
-        const bool has_next = sg + 1 < v.si.T;
-        const ff pv = {s_ph[j * NS + tid], k_at(j)};
-        if (LEV) {
+        for (int j = 0; j < J; ++j) {
+            const int64_t sg = wlo + base + j;
+            if (v.sid < 0 || sg < v.g.lo || sg >= v.g.hi) continue;
+            const float2 lr = A.lr_f[off + sg];
+            const ff x = {s_xh[j * NS + tid], s_xl[j * NS + tid]};
+            const int nidx = j + 1 < J ? (j + 1) * NS + tid : tid + 1;
+            const ff xn = {s_xh[nidx], s_xl[nidx]};
+            const ff mw = MASS ? mass_weight(mc.kick, dm_at(j)) : ff{1.f, 0.f};
+            const bool has_next = sg + 1 < v.si.T;
+            const ff pv = {s_ph[j * NS + tid], k_at(j)};
             ff cp = two_sum(lr.x, -mt.ximu.hi);
             cp.lo += lr.y - mt.ximu.lo;
             const float a = has_next ? -na_at(j) * mt.omr : -na_at(j);
             hparts_site<LEV, MASS>(acc, x, pv, mw, cp, a, xn, has_next, mt, s_exptab,
                                    v_at(j) * mt.ibf);
-        } else {
-            ff_acc(acc.K, kinetic<MASS>(pv, mw));
-            stats_site(st, x, xn, has_next, ff{lr.x, lr.y}, -na_at(j), mt, s_exptab);
         }
+    } else {
+        // K and the statistics of the pair (q, q + P) at once, in the two
+        // lanes of packed instructions (each lane the scalar site formulas of
+        // kinetic and stats_site); a slot the segment does not own enters as
+        // zeros, which add nothing
+        ff2 K2 = ff2_zero(), sx2 = ff2_zero(), sxx2 = ff2_zero(), sxn2 = ff2_zero(),
+            sxl2 = ff2_zero(), se2 = ff2_zero();
+        const float2 kick2 = f2(mc.kick, mc.kick);
+        const ff2 nmu = {f2(-mt.mu.hi, -mt.mu.hi), f2(-mt.mu.lo, -mt.mu.lo)};
+#pragma unroll 2
+        for (int q = 0; q < P; ++q) {
+            const int j0 = q, j1 = q + P;
+            const int64_t g0 = wlo + base + j0, g1 = wlo + base + j1;
+            const bool o0 = v.sid >= 0 && g0 >= v.g.lo && g0 < v.g.hi;
+            const bool o1 = v.sid >= 0 && g1 >= v.g.lo && g1 < v.g.hi;
+            const bool n0 = o0 && g0 + 1 < v.si.T, n1 = o1 && g1 + 1 < v.si.T;
+            const float2 lr0 = o0 ? A.lr_f[off + g0] : f2(0.f, 0.f);
+            const float2 lr1 = o1 ? A.lr_f[off + g1] : f2(0.f, 0.f);
+            const int i0 = j0 * NS + tid, i1 = j1 * NS + tid;
+            const int m0 = (j0 + 1) * NS + tid, m1 = j1 + 1 < J ? (j1 + 1) * NS + tid : tid + 1;
+            const float4 akv = s_ak[q * NTP + tid];  // (-a, -a', p lo, p lo')
+            const ff2 x = {f2(o0 ? s_xh[i0] : 0.f, o1 ? s_xh[i1] : 0.f),
+                           f2(o0 ? s_xl[i0] : 0.f, o1 ? s_xl[i1] : 0.f)};
+            const ff2 xn = {f2(n0 ? s_xh[m0] : 0.f, n1 ? s_xh[m1] : 0.f),
+                            f2(n0 ? s_xl[m0] : 0.f, n1 ? s_xl[m1] : 0.f)};
+            const ff2 pv = {f2(o0 ? s_ph[i0] : 0.f, o1 ? s_ph[i1] : 0.f),
+                            f2(o0 ? akv.z : 0.f, o1 ? akv.w : 0.f)};
+            const float2 a = f2(o0 ? -akv.x : 0.f, o1 ? -akv.y : 0.f);
+            // K: p^2 (with a mass m v^2, m from the kick as mass_weight)
+            ff2 p2 = two_prod2(pv.hi, pv.hi);
+            p2.lo = fma2(mul2(f2(2.0f, 2.0f), pv.hi), pv.lo, p2.lo);
+            if (MASS) p2 = ff2_mul(p2, mass_weight2(kick2, s_dm[q * NTP + tid]));
+            ff2_acc(K2, p2);
+            // the statistics (stats_site)
+            ff2_acc(sx2, x);
+            ff2_acc(sxx2, ff2_mul(x, x));
+            ff2_acc(sxn2, ff2_mul(x, xn));
+            ff2_acc(sxl2, ff2_mul(x, ff2{f2(lr0.x, lr1.x), f2(lr0.y, lr1.y)}));
+            ff2_acc(se2, ff2_mul_f(ff2_exp(ff2_sub(nmu, x), s_exptab), a));
+        }
+        acc.K = ff2_fold(K2);
+        st.sx = ff2_fold(sx2);
+        st.sxx = ff2_fold(sxx2);
+        st.sxn = ff2_fold(sxn2);
+        st.sxl = ff2_fold(sxl2);
+        st.e = ff2_fold(se2);
     }
     if (!LEV && v.sid >= 0) {  // the series' first and last sites, where owned
         const int64_t s0 = wlo + base;
