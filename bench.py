@@ -1104,6 +1104,13 @@ def run_profile_chain(args):
     dev = torch.device("cuda", 0)
     ctx = rsv.Context(0)
     K = int(args.profile_chain)
+    # the same trajectory length at another step count (the leapfrog's share
+    # of a launch: compare captures at two counts)
+    n_md = int(args.profile_nmd)
+    dtau = 0.035 * 78 / n_md
+    if args.profile_tile:
+        cs = rsv.rsv_chain_schedule(ctx, T_SITES, 78, "mixed", with_mass=True)
+        rsv.rsv_set_schedule(ctx, cs["threads"], cs["sites_per_thread"], int(args.profile_tile))
     s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA)
     y, lnrv = torch.tensor(s.y, device=dev), torch.tensor(s.lnrv, device=dev)
     m = 30.0 + 3.0 * np.random.default_rng(3).random(T_SITES)
@@ -1117,14 +1124,14 @@ def run_profile_chain(args):
     for k in range(2):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, 78, 0.035, K, prec="mixed", minv=minv, seed=11,
+        rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, n_md, dtau, K, prec="mixed", minv=minv, seed=11,
                           traj0=k * K, snaps=snaps, thin=1, theta_out=thetas, accept_out=acc,
                           update_theta=True)
         b.record()
         b.synchronize()
     rsv.rsv_sync_status(ctx)
-    cs = rsv.rsv_chain_schedule(ctx, T_SITES, 78, "mixed", with_mass=True)
-    print(json.dumps({"profile_chain": K, "us_per_trajectory": 1e3 * a.elapsed_time(b) / K,
+    cs = rsv.rsv_chain_schedule(ctx, T_SITES, n_md, "mixed", with_mass=True)
+    print(json.dumps({"profile_chain": K, "n_md": n_md, "us_per_trajectory": 1e3 * a.elapsed_time(b) / K,
                       "accept_rate": float(acc.float().mean()), "schedule": cs}))
     ctx.close()
     return 0
@@ -1151,6 +1158,11 @@ def main():
                     help="time per elementary step vs B (T = 512 B) like the paper's Table 2")
     ap.add_argument("--profile-chain", type=int, default=0,
                     help="run the headline chain twice with K trajectories (profiling)")
+    ap.add_argument("--profile-nmd", type=int, default=78,
+                    help="leapfrog steps per trajectory of --profile-chain (dtau 0.035 x 78 / n)")
+    ap.add_argument("--profile-tile", type=int, default=0,
+                    help="owned sites per tile of --profile-chain, with the block shape of the "
+                         "78-step chain (0: the planner's tiling)")
     args = ap.parse_args()
     if args.traj_per_step:
         global N_TRAJ

@@ -470,7 +470,8 @@ rsv_status rsv_chain_schedule(rsv_ctx* c, int64_t T, int n_md, rsv_precision pre
     if (sites_per_thread) *sites_per_thread = P->j;
     if (tile) {  // the owned sites of a tile (the series itself when it is not cut)
         const int64_t K = (int64_t)n_md * make_scheme(P->integrator, P->lambda).nk + 1;
-        *tile = P->nbins > 1 ? (int64_t)P->nt * P->j - 2 * K - 3 : T;
+        const int64_t t = c->sched_nt > 0 ? c->sched_tile : (int64_t)P->nt * P->j - 2 * K - 3;
+        *tile = P->nbins > 1 ? t : T;
     }
     if (persistent) *persistent = fits ? 1 : 0;
     return RSV_OK;
