@@ -151,7 +151,14 @@ bool make_plan(const int64_t* off, int n, int n_md, int integrator, double lambd
                         cost *= js[ji] == 20 ? 0.91 : js[ji] == 16 ? 1.0 : js[ji] == 12 ? 0.98 : 1.1;
                     else if (mixed)
                         cost *= js[ji] == 12 ? 1.0 : js[ji] == 20 ? 1.03 : 1.08;
-                    cost *= 1.0 + 1e-3 * (double)(tmax - t) / tmax;
+                    // a series cut into tiles runs at the throughput of
+                    // its blocks, which falls with fewer warps (the
+                    // leapfrog is latency-bound): measured on the mixed
+                    // kernel at T = 2^22, 384 x 20 takes 0.382 ms a
+                    // trajectory in 4 waves, 288 x 20 0.449 ms in 5 (25 %
+                    // more per site); a whole series keeps the smallest
+                    // window (a tie-break toward more threads only)
+                    cost *= 1.0 + (b > 1 ? 1.0 : 1e-3) * (double)(tmax - t) / tmax;
                     if (cost < best) {
                         best = cost;
                         nt = t;
