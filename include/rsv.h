@@ -383,6 +383,21 @@ rsv_status rsv_mlp_mass(rsv_ctx* ctx, const float* feat, int64_t T, const float*
 rsv_status rsv_draw_momenta(rsv_ctx* ctx, uint64_t seed, uint64_t series, uint64_t traj,
                             int64_t T, const float* minv, int bits, double* p_out, void* stream);
 
+/* ---- double-float exponential (exposed for tests of the mixed energies) ----
+ * The exponential the MIXED path takes in its energies and state statistics
+ * (the return term (y^2/2) e^{-h} of S, Sec. 3), in double-float arithmetic:
+ * t = tk ln2/32 + r, |r| <= ln2/64, a degree-5 Taylor polynomial of e^r, the
+ * table value 2^{(k mod 32)/32} and an exact power of two.  t: [n] device
+ * FP64, each rounded to a double-float (hi = (float)t, lo = (float)(t - hi))
+ * as the kernels hold their arguments; out: [n] device FP64 = hi + lo of the
+ * scalar form; out2: [n] the two-lane form the end-of-trajectory statistics
+ * use (equal to out bit for bit); either may be NULL.  |t| < 80 keeps the
+ * result finite and normal (outside it the result is undefined; no error is
+ * raised); below t ~ -70 its small part is subnormal and the relative error
+ * grows past ~1e-11.  n >= 0, else RSV_EINVAL. */
+rsv_status rsv_ff_exp(rsv_ctx* ctx, const double* t, double* out, double* out2, int64_t n,
+                      void* stream);
+
 /* ---- measurement -----------------------------------------------------------
  * rsv_ess: effective sample size of every column t of x, a [n][T] FP32 matrix
  * of n chain samples (row k = sample k), by Geyer's initial monotone sequence

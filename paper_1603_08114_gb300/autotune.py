@@ -20,7 +20,7 @@ import torch
 from . import rsv
 
 # bumped whenever the trajectory kernels change, so cached choices are redone
-KERNEL_REV = 14
+KERNEL_REV = 15
 
 CANDIDATES = {
     "mixed": ([(nt, 20) for nt in (128, 192, 256, 320, 384)]

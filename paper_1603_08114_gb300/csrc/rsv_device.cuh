@@ -89,30 +89,34 @@ __device__ __forceinline__ void box_muller_f(float u1, float u2, float& z0, floa
 // ---------------------------------------------------------------------------
 // Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
 // two_sum (Knuth), fast_two_sum (Dekker, |a| >= |b|), two_prod by FMA.
+// Every add, subtract and multiply is an explicitly rounded intrinsic: the
+// error-free transformations need s = fl(a + b) exactly, and the compiler
+// would otherwise fuse a product feeding an add into an FMA (a different
+// rounding of s).
 // ---------------------------------------------------------------------------
 struct ff { float hi, lo; };
 
 __device__ __forceinline__ ff two_sum(float a, float b)
 {
-    const float s = a + b;
-    const float bb = s - a;
-    const float e = (a - (s - bb)) + (b - bb);
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
     return {s, e};
 }
 __device__ __forceinline__ ff fast_two_sum(float a, float b)
 {
-    const float s = a + b;
-    return {s, b - (s - a)};
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 __device__ __forceinline__ ff two_prod(float a, float b)
 {
-    const float p = a * b;
+    const float p = __fmul_rn(a, b);
     return {p, __fmaf_rn(a, b, -p)};
 }
 __device__ __forceinline__ ff ff_add(ff a, ff b)
 {
     ff s = two_sum(a.hi, b.hi);
-    s.lo += a.lo + b.lo;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
     return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
@@ -134,7 +138,7 @@ __device__ __forceinline__ void ff_acc(ff& acc, ff v)
 {
     ff s = two_sum(acc.hi, v.hi);
     acc.hi = s.hi;
-    acc.lo += s.lo + v.lo;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, v.lo));
 }
 __host__ __device__ __forceinline__ ff ff_from_double(double d)
 {
@@ -167,22 +171,24 @@ __device__ __forceinline__ ff ff_exp(ff t, const float2* tab)
     const float C_hi = 0x1.62e43p-6f, C_lo = -0x1.05c61p-34f;  // ln2/32
     const float kr = __fmaf_rn(t.hi, 46.166241308446828f, 0x1.8p23f);  // 32/ln2
     const int k = __float_as_int(kr) - 0x4B400000;
-    const float kf = kr - 0x1.8p23f;
+    const float kf = __fsub_rn(kr, 0x1.8p23f);
     ff kc = two_prod(kf, C_hi);
-    kc.lo = fmaf(kf, C_lo, kc.lo);
+    kc.lo = __fmaf_rn(kf, C_lo, kc.lo);
     const ff r = ff_sub(t, kc);
     const float x = r.hi;
-    const float q = x * x * fmaf(x, fmaf(x, fmaf(x, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f), 0.5f);
+    const float q = __fmul_rn(
+        __fmul_rn(x, x),
+        __fmaf_rn(x, __fmaf_rn(x, __fmaf_rn(x, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f), 0.5f));
     ff s = two_sum(x, q);
-    s.lo += r.lo;
+    s.lo = __fadd_rn(s.lo, r.lo);
     ff e = two_sum(1.0f, s.hi);
-    e.lo += s.lo;
+    e.lo = __fadd_rn(e.lo, s.lo);
     e = fast_two_sum(e.hi, e.lo);
     const float2 tv = tab[k & 31];
     ff res = ff_mul(ff{tv.x, tv.y}, e);
     // 2^(k div 32) as an exact power of two (|t| < 80 keeps it normal)
     const float sc = __int_as_float(((k >> 5) + 127) << 23);
-    return ff{res.hi * sc, res.lo * sc};
+    return ff{__fmul_rn(res.hi, sc), __fmul_rn(res.lo, sc)};
 }
 
 // ---------------------------------------------------------------------------

@@ -659,9 +659,9 @@ __device__ __forceinline__ ff mass_weight(float kick, float km)
 {
     float t;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(km));
-    const float q = -kick * t;
-    const float r = fmaf(-q, km, -kick);  // -kick - q km, exact
-    return fast_two_sum(q, r * t);
+    const float q = __fmul_rn(-kick, t);
+    const float r = __fmaf_rn(-q, km, -kick);  // -kick - q km, exact
+    return fast_two_sum(q, __fmul_rn(r, t));
 }
 
 // mass_weight lane by lane

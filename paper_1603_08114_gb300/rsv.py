@@ -85,6 +85,7 @@ def lib():
                                       _U64, _I64, _P, _P, _P, _P]
         L.rsv_timing.argtypes = [_P, _INT]
         L.rsv_pipe_probe.argtypes = [_P, _INT, _I64, ctypes.POINTER(ctypes.c_double), _P]
+        L.rsv_ff_exp.argtypes = [_P, _P, _P, _P, _I64, _P]
         L.rsv_stats.argtypes = [_P, _INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                 ctypes.POINTER(ctypes.c_double)]
         for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule",
@@ -92,7 +93,7 @@ def lib():
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
                      "rsv_timing", "rsv_stats", "rsv_gibbs_theta", "rsv_plan_create",
                      "rsv_plan_info", "rsv_hmc_batched", "rsv_pipe_probe", "rsv_set_persistent",
-                     "rsv_set_wait_limit", "rsv_chain_schedule"):
+                     "rsv_set_wait_limit", "rsv_chain_schedule", "rsv_ff_exp"):
             getattr(L, name).restype = _INT
         _lib = L
     return _lib
@@ -291,6 +292,18 @@ def rsv_ess(ctx: Context, x):
     _check(lib().rsv_ess(ctx.handle, _ptr(x, torch.float32, n * T, "x"), int(n), int(T),
                          _ptr(out, torch.float32, T, "ess_out"), _stream()))
     return out
+
+
+def rsv_ff_exp(ctx: Context, t):
+    """The mixed path's double-float exponential at the FP64 CUDA tensor t
+    (each argument rounded to a double-float): (scalar form, two-lane form)."""
+    n = t.numel()
+    out = torch.empty(n, dtype=torch.float64, device=t.device)
+    out2 = torch.empty(n, dtype=torch.float64, device=t.device)
+    _check(lib().rsv_ff_exp(ctx.handle, _ptr(t, torch.float64, n, "t"),
+                            _ptr(out, torch.float64, n, "out"), _ptr(out2, torch.float64, n, "out2"),
+                            int(n), _stream()))
+    return out, out2
 
 
 PROBE_KINDS = {"ffma": 0, "ffma2": 1, "ex2": 2, "lds": 3, "dfma": 4}
