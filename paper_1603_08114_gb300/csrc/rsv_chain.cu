@@ -71,13 +71,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, lon
 // t0 + step, ...: the slots of owner thread o are sites wlo + o J .. + J - 1,
 // Philox4x64-10 counter {site / 4, traj, STREAM_MOM, series}, 23-bit uniforms
 // and Box-Muller in FP32, exactly as the per-trajectory kernel draws them.
+// Only the Philox blocks idx in [lo, hi) of the segment's owners * J / 4 are
+// drawn (hi < 0: all from lo).
 template <int J>
 __device__ __forceinline__ void draw_slots(const TrajArgs& A, uint64_t traj, const Seg& g,
-                                           float* s_ph, int NS, int t0, int step)
+                                           float* s_ph, int NS, int t0, int step, int lo = 0,
+                                           int hi = -1)
 {
     constexpr int Q = J / 4;
     const int owners = g.nwarp * 32;
-    for (int idx = t0; idx < owners * Q; idx += step) {
+    const int end = hi < 0 ? owners * Q : hi;
+    for (int idx = lo + t0; idx < end; idx += step) {
         const int o = idx / Q, q = idx - o * Q;
         const int64_t s0 = g.wlo + (int64_t)o * J + 4 * q;
         const u64x4 r = philox_block(A.seed, (uint64_t)g.series, traj, STREAM_MOM,
@@ -156,9 +160,9 @@ __device__ __noinline__ void chain_setup(const ChainArgs& C, MixedSmem<false>& S
 // After trajectory Q.i: the grid barrier, the decision, the theta sweep and
 // the next momenta; returns false if a barrier wait ran out.  Warps 0..7 sum
 // the tiles' records (one value each; named barrier 1 joins them), thread 0
-// decides and warp 0 then sweeps theta, while warps 8.. draw the next
-// trajectory's momenta (a block of fewer than 9 warps does the steps one
-// after the other).  Not inlined: inside the trajectory loop its
+// decides and warp 0 then sweeps theta, while warps 8.. and then 1..7 draw
+// the next trajectory's momenta (a block of fewer than 9 warps does the steps
+// one after the other).  Not inlined: inside the trajectory loop its
 // loop-invariant values (Philox and sweep constants, addresses) would be
 // hoisted out of the loop and held in registers through the leapfrog, which
 // then runs ~10 % slower.
@@ -178,6 +182,13 @@ __device__ __noinline__ bool chain_after(const ChainArgs& C, MixedSmem<false>& S
     const int NS = mixed_row(NT, J);
     if (!grid_barrier(C.bar, (unsigned)(i + 1) * gridDim.x, C.wait_limit, A.status, &Q.ok))
         return false;
+    // the next momenta (Philox blocks [0, mom_split) by warps 8.., which start
+    // at once, the rest by warps 1..7 after their share of the record sum):
+    // twice the blocks per thread for the early warps
+    const int mom_total = Q.g.nwarp * 32 * (J / 4);
+    const int n_early = NT - 32 * kRecWords, n_late = 32 * (kRecWords - 1);
+    const int mom_split =
+        split ? (int)((int64_t)mom_total * 2 * n_early / (2 * n_early + n_late)) : mom_total;
     if (warp < kRecWords) {
         // every tile's record value f in tile order (lane l takes tiles l,
         // l + 32, ...; then a butterfly) -- the same order in every block;
@@ -203,9 +214,12 @@ __device__ __noinline__ bool chain_after(const ChainArgs& C, MixedSmem<false>& S
         }
         if (split) asm volatile("bar.sync 1, %0;" ::"r"(kRecWords * 32) : "memory");
         else __syncthreads();
+        // warps 1..7 then join the momenta (warp 0 decides and sweeps)
+        if (split && more && warp > 0)
+            draw_slots<J>(A, traj + 1, Q.g, s_ph, NS, tid - 32, 32 * (kRecWords - 1), mom_split);
     } else {
         if (more) draw_slots<J>(A, traj + 1, Q.g, s_ph, NS, tid - 32 * kRecWords,
-                                NT - 32 * kRecWords);
+                                NT - 32 * kRecWords, 0, mom_split);
     }
     if (!split) __syncthreads();  // (the reducing warps passed one already)
     if (tid == 0) {
