@@ -14,7 +14,8 @@ The mass is a function of the frozen hbar only, so HMC with it stays exact.
 The sampler that uses it (`MassSampler`) runs the chain in windows of
 trajectories and falls back for good to the plain identity-mass sampler (its
 own step size and trajectory length) when a window's acceptance rate is below
-0.6.
+0.6 (checked while the next window runs, so the switch comes one window
+later).
 """
 from __future__ import annotations
 
@@ -127,11 +128,20 @@ class MassSampler:
     fell_back: bool = False
     history: list = field(default_factory=list)
     md_steps: int = 0   # leapfrog steps run so far (per site)
+    _pin: list = field(default_factory=list)  # two pinned host scalars (window rates)
 
     def run(self, h, y, lnrv, theta_dev, n_traj: int, seed: int, traj0: int = 0, snaps=None,
             theta_out=None, accept_out=None, update_theta: bool = True):
         T = h.numel()
         done = 0
+        # a window's acceptance is read back without waiting for it: the
+        # previous window's is checked while this one runs (so a collapse
+        # switches to the plain sampler one window later, and the stream
+        # never waits on the host between windows)
+        pending = None
+        if not self._pin:
+            self._pin = [torch.empty((), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+        slot = 0
         while done < n_traj:
             k = min(self.window, n_traj - done)
             acc = (accept_out[done:done + k] if accept_out is not None
@@ -150,9 +160,23 @@ class MassSampler:
                                   snaps=sn, thin=1, theta_out=tho, accept_out=acc,
                                   update_theta=update_theta)
                 self.md_steps += k * self.n_md
-                rate = float(acc.float().mean())
-                self.history.append(rate)
-                if rate < 0.6:
-                    self.fell_back = True
+                host = self._pin[slot]
+                slot ^= 1
+                host.copy_(acc.float().mean(), non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record()
+                prev, pending = pending, (ev, host)
+                if prev is not None:
+                    self._check(prev)
             done += k
+        if pending is not None:
+            self._check(pending)
         return h
+
+    def _check(self, p):
+        ev, host = p
+        ev.synchronize()
+        rate = float(host)
+        self.history.append(rate)
+        if rate < 0.6:
+            self.fell_back = True
