@@ -66,8 +66,8 @@ IMPL_OPS_PER_SITE_STEP_MIXED = 13
 # trajectories; the inputs stay in L2 between trajectories), from the capture
 # summarised in profiles/; valid for the kernel revision it was taken on.
 # (the capture: `python bench.py --profile-chain 10`, one launch of 10
-# trajectories, cold L2: 25.38 MB read + 4.22 MB written).
-TRAFFIC = {"kernel": "k_chain_mixed", "kernel_rev": 14, "bytes_per_trajectory": 2960282}
+# trajectories, cold L2: 25.38 MB read + 4.36 MB written).
+TRAFFIC = {"kernel": "k_chain_mixed", "kernel_rev": 15, "bytes_per_trajectory": 2974362}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
