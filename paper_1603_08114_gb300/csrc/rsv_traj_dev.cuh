@@ -904,64 +904,6 @@ __device__ __forceinline__ void persist_record(double* partials, const View& v,
         make_float2(di.hi, di.lo);
 }
 
-// The leapfrog of one trajectory on the block's registers: the state from
-// shared memory (x as (hi, lo), the momenta; p lo starts at 0), the first
-// half step of eq. (6), the n_md steps, and the end state back to shared
-// memory (x over the start's slots, p lo over k, which the leapfrog no longer
-// needs).  Out of line, so that the register allocation of the step loop
-// does not depend on the code around it (the load pass and the end
-// statistics).
-template <int J, bool MASS, bool LEV>
-__device__ __noinline__ void trajectory_steps(float* s_xh, float* s_xl, float* s_ph, float4* s_ak,
-                                              const float2* s_dm, const float2* s_v, float* s_edge,
-                                              int NS, int nw, int n_md, const MixedConst mc,
-                                              float r0, bool kv)
-{
-    constexpr int P = J / 2;
-    const int tid = threadIdx.x, NTP = mixed_ntp(blockDim.x);
-    float2 X[P], XL[P], PH[P], PL[P];
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-        X[q] = f2(s_xh[q * NS + tid], s_xh[(q + P) * NS + tid]);
-        XL[q] = f2(s_xl[q * NS + tid], s_xl[(q + P) * NS + tid]);
-        PH[q] = f2(s_ph[q * NS + tid], s_ph[(q + P) * NS + tid]);
-        PL[q] = f2(0.0f, 0.0f);
-    }
-#pragma unroll
-    for (int q = 0; q < P; ++q) cupd2(X[q], XL[q], f2(r0 * mc.dt, r0 * mc.dt), PH[q]);
-
-    int par = 0;
-    const bool mid_end = mc.la >= 0 && mc.la < J - 1;
-    if (__any_sync(0xffffffffu, mid_end)) {
-        if (kv)
-            mixed_steps<J, MASS, true, LEV, true>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par, nw,
-                                                  n_md, mc);
-        else
-            mixed_steps<J, MASS, true, LEV, false>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par, nw,
-                                                   n_md, mc);
-    } else {
-        if (kv)
-            mixed_steps<J, MASS, false, LEV, true>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par, nw,
-                                                   n_md, mc);
-        else
-            mixed_steps<J, MASS, false, LEV, false>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par,
-                                                    nw, n_md, mc);
-    }
-    __syncthreads();  // every warp is done reading k and the start state
-    float* s_ak1 = reinterpret_cast<float*>(s_ak);
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-        s_xh[q * NS + tid] = X[q].x;
-        s_xh[(q + P) * NS + tid] = X[q].y;
-        s_xl[q * NS + tid] = XL[q].x;
-        s_xl[(q + P) * NS + tid] = XL[q].y;
-        s_ph[q * NS + tid] = PH[q].x;
-        s_ph[(q + P) * NS + tid] = PH[q].y;
-        // (k, k') of the pair, one 8-byte store
-        *reinterpret_cast<float2*>(&s_ak1[(q * NTP + tid) * 4 + 2]) = PL[q];
-    }
-}
-
 // One bin of a mixed trajectory (the whole block).  PERSIST: a bin of the
 // persistent chain kernel (rsv_chain.cu): theta's constants already in
 // s_mt, the momenta already in s_ph, the current buffer in S.cur, state
@@ -1011,6 +953,7 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
     auto dm_at = [&](int j) -> float& { return dm_t(j, tid); };
     auto v_at = [&](int j) -> float& { return v_t(j, tid); };
 
+    float2 X[P], XL[P], PH[P], PL[P];
     MixedConst mc;
     ff h0;             // this thread's owned-site H at the start
     {
@@ -1179,11 +1122,51 @@ __device__ __forceinline__ void traj_mixed_bin(const TrajArgs& A, int b, MixedSm
         mc.vL = (LEV && !v.first) ? s_v1[((P - 1) * NTP + tid - 1) * 2 + 1] : 0.0f;
         mc.cfirst = (LEV && v.first) ? mt.cst : 0.0f;
         h0 = LEV ? hparts_total(acc, mt) : ff_add(acc.K, ff{0.f, 0.f});
+        // registers <- shared memory, then the first half step of eq. (6)
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            X[q] = f2(s_xh[q * NS + tid], s_xh[(q + P) * NS + tid]);
+            XL[q] = f2(s_xl[q * NS + tid], s_xl[(q + P) * NS + tid]);
+            PH[q] = f2(s_ph[q * NS + tid], s_ph[(q + P) * NS + tid]);
+            PL[q] = f2(0.0f, 0.0f);
+        }
+        const float r0 = A.msch.r_first;  // first drift
+#pragma unroll
+        for (int q = 0; q < P; ++q) cupd2(X[q], XL[q], f2(r0 * dt, r0 * dt), PH[q]);
     }
-    // the leapfrog, out of line (registers <- shared memory, the first half
-    // step of eq. (6), the steps, the end state back to shared memory)
-    trajectory_steps<J, MASS, LEV>(s_xh, s_xl, s_ph, s_ak, s_dm, s_v, s_edge, NS, nw, A.n_md, mc,
-                                   A.msch.r_first, A.msch.kv != 0);
+
+    int par = 0;
+    const bool mid_end = mc.la >= 0 && mc.la < J - 1;
+    if (__any_sync(0xffffffffu, mid_end)) {
+        if (A.msch.kv)
+            mixed_steps<J, MASS, true, LEV, true>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge, par,
+                                                  nw, A.n_md, mc);
+        else
+            mixed_steps<J, MASS, true, LEV, false>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge,
+                                                   par, nw, A.n_md, mc);
+    } else {
+        if (A.msch.kv)
+            mixed_steps<J, MASS, false, LEV, true>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge,
+                                                   par, nw, A.n_md, mc);
+        else
+            mixed_steps<J, MASS, false, LEV, false>(X, XL, PH, PL, s_ak, s_dm, s_v, s_edge,
+                                                    par, nw, A.n_md, mc);
+    }
+
+    // ---- the end of the trajectory: state -> shared memory (x over the
+    // start's slots, p lo over k, which the leapfrog no longer needs) ----
+    __syncthreads();  // every warp is done reading k and the start state
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        s_xh[q * NS + tid] = X[q].x;
+        s_xh[(q + P) * NS + tid] = X[q].y;
+        s_xl[q * NS + tid] = XL[q].x;
+        s_xl[(q + P) * NS + tid] = XL[q].y;
+        s_ph[q * NS + tid] = PH[q].x;
+        s_ph[(q + P) * NS + tid] = PH[q].y;
+        // (k, k') of the pair, one 8-byte store
+        *reinterpret_cast<float2*>(&k_at(q)) = PL[q];
+    }
     __syncthreads();
     View v;
     view_filed(s_wseg, S.wg, S.wsi, S.wcur, v);
