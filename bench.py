@@ -709,7 +709,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         t_tune = time.perf_counter() - t1
         minv = tm.minv
-        sampler = learned.MassSampler(ctx, minv, head_dt, head_nmd, DTAU, N_MD, window=100)
+        # one window per step: the mass's acceptance is checked once per 200
+        # trajectories, and a step is one chain call
+        sampler = learned.MassSampler(ctx, minv, head_dt, head_nmd, DTAU, N_MD, window=N_TRAJ)
         m = (1.0 / minv).float()
         losses = tm.losses.cpu().numpy()
         learned_info = {"snapshots": int(cnt), "snapshot_s": t_snap,
