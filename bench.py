@@ -1098,7 +1098,9 @@ def run_profile_chain(args):
     """The headline's chain for a profiler: T = 2^20, a mass of the learned
     mass's shape (m ~ 30, fixed: no training), 78 x 0.035, theta sampled,
     every state recorded; one warm-up call, then one call of K trajectories
-    (`ncu -k regex:k_chain_mixed -s 1 -c 1` takes that one)."""
+    (`ncu -k regex:k_chain_mixed -s 1 -c 1` takes that one).  With
+    --profile-prec fp64: the FP64 arm's chain instead (identity mass, 100 x
+    0.005, one k_traj_fp64 launch per trajectory)."""
     import torch
 
     from paper_1603_08114_gb300 import rsv, synth
@@ -1110,6 +1112,9 @@ def run_profile_chain(args):
     # of a launch: compare captures at two counts)
     n_md = int(args.profile_nmd)
     dtau = 0.035 * 78 / n_md
+    fp64 = args.profile_prec == "fp64"
+    if fp64:
+        n_md, dtau = N_MD, DTAU
     if args.profile_tile:
         cs = rsv.rsv_chain_schedule(ctx, T_SITES, 78, "mixed", with_mass=True)
         rsv.rsv_set_schedule(ctx, cs["threads"], cs["sites_per_thread"], int(args.profile_tile))
@@ -1126,14 +1131,15 @@ def run_profile_chain(args):
     for k in range(2):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, n_md, dtau, K, prec="mixed", minv=minv, seed=11,
-                          traj0=k * K, snaps=snaps, thin=1, theta_out=thetas, accept_out=acc,
-                          update_theta=True)
+        rsv.rsv_hmc_chain(ctx, h, y, lnrv, th, n_md, dtau, K, prec="fp64" if fp64 else "mixed",
+                          minv=None if fp64 else minv, seed=11, traj0=k * K, snaps=snaps, thin=1,
+                          theta_out=thetas, accept_out=acc, update_theta=True)
         b.record()
         b.synchronize()
     rsv.rsv_sync_status(ctx)
-    cs = rsv.rsv_chain_schedule(ctx, T_SITES, n_md, "mixed", with_mass=True)
-    print(json.dumps({"profile_chain": K, "n_md": n_md, "us_per_trajectory": 1e3 * a.elapsed_time(b) / K,
+    cs = rsv.rsv_chain_schedule(ctx, T_SITES, n_md, "fp64" if fp64 else "mixed",
+                                with_mass=not fp64)
+    print(json.dumps({"profile_chain": K, "prec": "fp64" if fp64 else "mixed", "n_md": n_md, "us_per_trajectory": 1e3 * a.elapsed_time(b) / K,
                       "accept_rate": float(acc.float().mean()), "schedule": cs}))
     ctx.close()
     return 0
@@ -1162,6 +1168,8 @@ def main():
                     help="run the headline chain twice with K trajectories (profiling)")
     ap.add_argument("--profile-nmd", type=int, default=78,
                     help="leapfrog steps per trajectory of --profile-chain (dtau 0.035 x 78 / n)")
+    ap.add_argument("--profile-prec", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of --profile-chain's chain (fp64: the FP64 arm's)")
     ap.add_argument("--profile-tile", type=int, default=0,
                     help="owned sites per tile of --profile-chain, with the block shape of the "
                          "78-step chain (0: the planner's tiling)")
