@@ -269,9 +269,18 @@ def _host():
     return {"cpu": model or platform.machine(), "nproc": os.cpu_count()}
 
 
+# The headline's trajectory shape: the step size and step count the tuner
+# picks for the learned mass in every run so far (the largest step of its
+# ladder that reaches 0.8 acceptance); the reference arm times the oracle on
+# it, with a fixed diagonal mass of the learned mass's shape in its place.
+HEAD_NMD, HEAD_DTAU = 78, 0.035
+
+
 def run_reference(args):
-    """--impl reference: the FP64 CPU oracle on the host cores, each step one
-    trajectory of the workload (a bounded sample of one 200-trajectory step)."""
+    """--impl reference: the FP64 CPU oracle on the host cores on the
+    headline's trajectory shape (T = 2^20, 78 x 0.035, theta sampled, a fixed
+    diagonal mass m ~ 30 in place of the learned one), each step one
+    trajectory (a bounded sample of one 200-trajectory step)."""
     import oracle
     from paper_1603_08114_gb300 import synth
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -279,24 +288,37 @@ def run_reference(args):
     if rank != 0:
         return 0
     s = synth.rsv_series(T_SITES, synth.THETA_STD, seed=SEED_DATA)
+    minv = 1.0 / (30.0 + 3.0 * np.random.default_rng(3).random(T_SITES))
     h = s.h_true.copy()
+    th = s.theta
     k = 0
+
+    def one(h, th, k):
+        r = oracle.chain(h, s.y, s.lnrv, th, HEAD_NMD, HEAD_DTAU, seed=7, n_traj=1, traj0=k,
+                         update_theta=True, minv=minv)
+        return r["h"], r["theta"]
+
     for _ in range(args.warmup):
-        h = oracle.chain(h, s.y, s.lnrv, s.theta, N_MD, DTAU, seed=7, n_traj=1, traj0=k)["h"]
+        h, th = one(h, th, k)
         k += 1
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        h = oracle.chain(h, s.y, s.lnrv, s.theta, N_MD, DTAU, seed=7, n_traj=1, traj0=k)["h"]
+        h, th = one(h, th, k)
         k += 1
     el = time.perf_counter() - t0
-    v = T_SITES * N_MD * args.steps / el
-    sample = f"1 FP64 oracle trajectory (T=2^20, 100 x 0.005) per step, single-threaded C"
+    v = T_SITES * HEAD_NMD * args.steps / el
+    sample = (f"1 FP64 oracle trajectory (T=2^20, {HEAD_NMD} x {HEAD_DTAU}, theta sampled, fixed "
+              f"diagonal mass m ~ 30) per step, single-threaded C")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "T": T_SITES, "n_md": N_MD,
-                                        "dtau": DTAU, "step": "1 trajectory"},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "T": T_SITES, "n_md": HEAD_NMD, "dtau": HEAD_DTAU,
+                   "traj_per_step": N_TRAJ, "precision": "fp64",
+                   "mass": "diagonal m ~ 30 (fixed, the learned mass's shape)",
+                   "l2": "host", "parallelism": f"replicas{ws}",
+                   "step": "1 trajectory (a bounded sample of the 200-trajectory step)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample, "host": _host()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
