@@ -134,3 +134,23 @@ def test_barrier_wait_that_runs_out_reports_timeout(rsv, ctx):
 def test_wait_limit_rejects_negative(rsv, ctx):
     with pytest.raises(rsv.RSVError, match="RSV_EINVAL"):
         rsv.rsv_set_wait_limit(ctx, -1)
+
+
+def test_planner_block_shapes_at_the_measured_sizes(rsv, ctx):
+    """The planner's choices where they were measured: the headline chain
+    (T = 2^20, mass, 78 steps) runs persistent on 384 x 20 (140 tiles; per
+    trajectory 88.5 us against 92.1 on 448 x 16), and a series of 2^22 sites
+    cut into 4 waves of tiles takes the same full blocks (0.382 ms a
+    trajectory against 0.449 on 288 x 20).  A fixed schedule is reported
+    with its own tile."""
+    cs = rsv.rsv_chain_schedule(ctx, 1 << 20, 78, "mixed", with_mass=True)
+    assert (cs["threads"], cs["sites_per_thread"], cs["persistent"]) == (384, 20, True)
+    assert cs["tile"] == 384 * 20 - 2 * 79 - 3
+    cs = rsv.rsv_chain_schedule(ctx, 1 << 22, 100, "mixed", with_mass=False)
+    assert (cs["threads"], cs["sites_per_thread"], cs["persistent"]) == (384, 20, False)
+    rsv.rsv_set_schedule(ctx, 384, 20, 7000)
+    try:
+        cs = rsv.rsv_chain_schedule(ctx, 1 << 20, 78, "mixed", with_mass=True)
+        assert cs["tile"] == 7000
+    finally:
+        rsv.rsv_set_schedule(ctx)
