@@ -1,7 +1,8 @@
-// rsv_dfexp.cu -- the double-float exponential of the mixed path's energies,
-// exposed for tests: ff_exp (one double-float) and its two-lane form ff2_exp
-// (the end-of-trajectory statistics), evaluated at given arguments.  Not a
-// step of the method; the tests compare it with exp in FP64.
+// rsv_dfexp.cu -- the exponentials of the trajectory kernels, exposed for
+// tests: the mixed path's double-float ff_exp (one double-float) and its
+// two-lane form ff2_exp (the end-of-trajectory statistics), and the FP64
+// path's table-driven exp_tab, evaluated at given arguments.  Not steps of
+// the method; the tests compare them with exp in FP64.
 #include <algorithm>
 #include <cstdint>
 
@@ -45,6 +46,18 @@ __global__ void __launch_bounds__(kDfThreads) k_ff_exp(const double* __restrict_
     }
 }
 
+// exp_tab (the FP64 trajectory kernel's exponential) at each argument.
+__global__ void __launch_bounds__(kDfThreads) k_exp_tab(const double* __restrict__ t, int64_t n,
+                                                        double* __restrict__ out)
+{
+    __shared__ double tab[32];
+    if (threadIdx.x < 32) tab[threadIdx.x] = kExp2Tab[threadIdx.x];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = exp_tab(t[i], tab);
+}
+
 }  // namespace
 }  // namespace rsv
 
@@ -64,4 +77,18 @@ extern "C" rsv_status rsv_ff_exp(rsv_ctx* c, const double* t, double* out, doubl
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? RSV_OK : cuda_fail(e, "k_ff_exp");
+}
+
+extern "C" rsv_status rsv_fp64_exp(rsv_ctx* c, const double* t, double* out, int64_t n, void* stream)
+{
+    rsv_status st = ctx_begin(c, stream);
+    if (st != RSV_OK) return st;
+    if (n < 0) return fail(RSV_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
+    if (n == 0) return RSV_OK;
+    if (!t || !out) return fail(RSV_EINVAL, "null t or out");
+    const int grid = (int)std::min<int64_t>((n + kDfThreads - 1) / kDfThreads, 4 * (int64_t)c->num_sms);
+    k_exp_tab<<<grid, kDfThreads, 0, (cudaStream_t)stream>>>(t, n, out);
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RSV_OK : cuda_fail(e, "k_exp_tab");
 }

@@ -56,7 +56,9 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_wseg[NWMAX], s_wacc[NWMAX], s_flag;
     __shared__ double s_wpart[NWMAX], s_red[32], s_edge[4 * NWMAX], s_split;
+    __shared__ double s_e2[32];  // 2^(j/32), the table of exp_tab
     const int NT = blockDim.x, W = NT * J, nw = NT >> 5, tid = threadIdx.x;
+    if (tid < 32) s_e2[tid] = kExp2Tab[tid];  // read after load_bin's barriers
     double* s_a = reinterpret_cast<double*>(smem_raw);
     double* s_kc = s_a + W;
     double* s_mi = s_kc + W;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
         auto lev_terms = [&](const double (&xx)[J], double (&eps)[J], double (&e)[J]) {
 #pragma unroll
             for (int j = 0; j < J; ++j) {
-                eps[j] = s_a[j * NT + tid] * exp(-0.5 * xx[j]);
+                eps[j] = s_a[j * NT + tid] * exp_tab(-0.5 * xx[j], s_e2);
                 if (!(edge_thread && j == la)) e[j] = fma(-rs, eps[j], e[j]);
             }
         };
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
                 if (v.sid >= 0 && s >= v.g.lo && s < v.g.hi) {
                     const double cp = (A.lnrv[off + s] - th.xi) - mu;
                     const double r = cp - x[j];
-                    const double ey = LEV ? 0.5 * eps[j] * eps[j] : s_a[j * NT + tid] * exp(-x[j]);
+                    const double ey = LEV ? 0.5 * eps[j] * eps[j] : s_a[j * NT + tid] * exp_tab(-x[j], s_e2);
                     double val = 0.5 * x[j] + ey + 0.5 * iu * r * r + 0.5 * ib * e[j] * e[j];
                     if (s == 0) val += 0.5 * ie * st0 * x[j] * x[j];
                     const double mi = MASS ? s_mi[j * NT + tid] : 1.0;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
                 double eprev = v.first ? stB * x[0] : fma(-phi, xL, x[0]);
                 if (LEV) {
                     lev_terms(x, eps, e);
-                    if (!v.first) eprev = fma(-rs, yL * exp(-0.5 * xL), eprev);
+                    if (!v.first) eprev = fma(-rs, yL * exp_tab(-0.5 * xL, s_e2), eprev);
                 }
                 // eq. (7): p -= kick dS/dh
                 const double kick = A.sch.b[st] * dt;
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
                     } else {
                         const double ar = fma(-phi, e[j], eprev);
                         f = fma(ie, ar, f);
-                        f = fma(-s_a[j * NT + tid], exp(-x[j]), f);
+                        f = fma(-s_a[j * NT + tid], exp_tab(-x[j], s_e2), f);
                     }
                     eprev = e[j];
                     p[j] = fma(-kick, f, p[j]);

@@ -86,6 +86,7 @@ def lib():
         L.rsv_timing.argtypes = [_P, _INT]
         L.rsv_pipe_probe.argtypes = [_P, _INT, _I64, ctypes.POINTER(ctypes.c_double), _P]
         L.rsv_ff_exp.argtypes = [_P, _P, _P, _P, _I64, _P]
+        L.rsv_fp64_exp.argtypes = [_P, _P, _P, _I64, _P]
         L.rsv_stats.argtypes = [_P, _INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                 ctypes.POINTER(ctypes.c_double)]
         for name in ("rsv_create", "rsv_reserve", "rsv_sync_status", "rsv_set_schedule",
@@ -93,7 +94,7 @@ def lib():
                      "rsv_hmc_trajectory", "rsv_hmc_chain", "rsv_draw_momenta", "rsv_ess",
                      "rsv_timing", "rsv_stats", "rsv_gibbs_theta", "rsv_plan_create",
                      "rsv_plan_info", "rsv_hmc_batched", "rsv_pipe_probe", "rsv_set_persistent",
-                     "rsv_set_wait_limit", "rsv_chain_schedule", "rsv_ff_exp"):
+                     "rsv_set_wait_limit", "rsv_chain_schedule", "rsv_ff_exp", "rsv_fp64_exp"):
             getattr(L, name).restype = _INT
         _lib = L
     return _lib
@@ -304,6 +305,15 @@ def rsv_ff_exp(ctx: Context, t):
                             _ptr(out, torch.float64, n, "out"), _ptr(out2, torch.float64, n, "out2"),
                             int(n), _stream()))
     return out, out2
+
+
+def rsv_fp64_exp(ctx: Context, t):
+    """The FP64 path's table-driven exponential at the FP64 CUDA tensor t."""
+    n = t.numel()
+    out = torch.empty(n, dtype=torch.float64, device=t.device)
+    _check(lib().rsv_fp64_exp(ctx.handle, _ptr(t, torch.float64, n, "t"),
+                              _ptr(out, torch.float64, n, "out"), int(n), _stream()))
+    return out
 
 
 PROBE_KINDS = {"ffma": 0, "ffma2": 1, "ex2": 2, "lds": 3, "dfma": 4}
