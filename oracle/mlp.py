@@ -1,7 +1,7 @@
 """FP64 reference of the learned diagonal mass (TEST INFRASTRUCTURE ONLY).
 
-The paper has no learned part; this is the reference for the network the task
-adds.  A site's mass is m_t = s (softplus(z_t) + eps_m) with z_t the output of a
+The paper has no learned part; this is the reference for the network the
+library adds.  A site's mass is m_t = s (softplus(z_t) + eps_m) with z_t the output of a
 20 -> 32 -> 32 -> 1 MLP (tanh hidden units) on 20 features of the site; it is
 trained by Adam on the squared error between log m_t and the target
 log(1 / Var(h_t)) estimated from sampler snapshots.  s is a fixed output scale
@@ -15,7 +15,8 @@ hidden activation a1, and the back-propagated dz1/dz2 - and accumulates in
 FP64.  With ``bf16=False`` it is the plain FP64 network (used by the
 finite-difference pins).
 
-Features of site t (20, the reading of the task's list; see the design notes):
+Features of site t (20: the local data y_t^2 and lnRV_t, an 8-neighbour window of
+the frozen posterior mean, theta, and position terms):
   0  y_t^2                      1  lnRV_t
   2..10  hbar_{t-4} .. hbar_{t+4} (frozen posterior mean of h; 0 past the ends)
   11..15 phi, mu, xi, s_eta^2, s_u^2

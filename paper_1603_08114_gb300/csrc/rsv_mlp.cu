@@ -1,7 +1,7 @@
 // rsv_mlp.cu -- the learned diagonal mass: sampler moments, features, a BF16
 // MLP trained by Adam, and mass inference.
 //
-// Not part of the paper (which has no learned component): the task adds a
+// Not part of the paper (which has no learned component): this library adds a
 // per-site mass m_t = s (softplus(z_t) + eps) for HMC, where z_t is a 20 -> 32 ->
 // 32 -> 1 MLP (tanh hidden units) on 20 features of site t computed from a
 // FROZEN state (the posterior mean hbar of a plain sampler), so the mass never
