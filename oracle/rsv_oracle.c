@@ -17,8 +17,9 @@
  *     with l = k * dtau (Sec. 3);
  *   - Metropolis acceptance with probability min{1, exp(-dH)} (Sec. 3).
  * The paper does not write f out; S(h) = -ln f below is derived from
- * eqs. (1)-(3) with the stationary AR(1) law for h_1 (see the readings in the
- * design notes).  Indices are 0-based here (the paper's t = 1..T is t = 0..T-1).
+ * eqs. (1)-(3) with the stationary AR(1) law for h_1 (a reading: the paper
+ * leaves the law of h_1 unstated).  Indices are 0-based here (the paper's
+ * t = 1..T is t = 0..T-1).
  *
  * Parity status of each function is stated beside it; every one is pinned by a
  * CPU test (finite differences, reversibility, dtau^2 scaling, Kalman smoother,
