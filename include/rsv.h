@@ -398,9 +398,9 @@ rsv_status rsv_draw_momenta(rsv_ctx* ctx, uint64_t seed, uint64_t series, uint64
 rsv_status rsv_ff_exp(rsv_ctx* ctx, const double* t, double* out, double* out2, int64_t n,
                       void* stream);
 /* rsv_fp64_exp: the exponential of the FP64 path's force and energies
- * (exp_tab): Tang's table-driven method, t = k ln2/32 + r, |r| <= ln2/64,
- * e^t = 2^(k div 32) 2^((k mod 32)/32) (1 + p(r)), p the degree-6 Taylor
- * polynomial of e^r - 1, the table 2^(j/32) rounded to double; |t| >= 512
+ * (exp_tab): Tang's table-driven method, t = k ln2/64 + r, |r| <= ln2/128,
+ * e^t = 2^(k div 64) 2^((k mod 64)/64) (1 + p(r)), p the degree-5 Taylor
+ * polynomial of e^r - 1, the table 2^(j/64) rounded to double; |t| >= 512
  * falls back to CUDA's exp.  t, out: [n] device FP64.  n >= 0 and non-NULL
  * pointers when n > 0, else RSV_EINVAL. */
 rsv_status rsv_fp64_exp(rsv_ctx* ctx, const double* t, double* out, int64_t n, void* stream);

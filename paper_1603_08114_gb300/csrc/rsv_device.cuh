@@ -194,43 +194,51 @@ __device__ __forceinline__ ff ff_exp(ff t, const float2* tab)
 // ---------------------------------------------------------------------------
 // exp in FP64 for the FP64 trajectory kernel, table-driven after P. T. P. Tang
 // ("Table-driven implementation of the exponential function in IEEE
-// floating-point arithmetic", ACM TOMS 15, 1989): a = k ln2/32 + r with k the
-// integer nearest to 32 a/ln2 and |r| <= ln2/64 (ln2/32 split in a head of 32
+// floating-point arithmetic", ACM TOMS 15, 1989): a = k ln2/64 + r with k the
+// integer nearest to 64 a/ln2 and |r| <= ln2/128 (ln2/64 split in a head of 32
 // significant bits, so that k times it is exact, and a tail), and
-//   e^a = 2^(k div 32) 2^((k mod 32)/32) (1 + p(r)),
-// p the Taylor polynomial of e^r - 1 to degree 6 (remainder < 4e-18 for
-// |r| <= ln2/64).  kExp2Tab holds 2^(j/32) rounded to double (computed to 200
-// bits).  |a| >= 512 takes exp (the scaling by 2^(k div 32) through the
-// exponent field assumes a normal result).
+//   e^a = 2^(k div 64) 2^((k mod 64)/64) (1 + p(r)),
+// p the Taylor polynomial of e^r - 1 to degree 5 (remainder < 4e-17 for
+// |r| <= ln2/128): 10 FP64 instructions.  kExp2Tab holds 2^(j/64) rounded to
+// double (computed to 200 bits).  |a| >= 512 takes exp (the scaling by
+// 2^(k div 64) through the exponent field assumes a normal result).
 // ---------------------------------------------------------------------------
-static __constant__ double kExp2Tab[32] = {
-    0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
-    0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
-    0x1.306fe0a31b715p+0, 0x1.371a7373aa9cbp+0, 0x1.3dea64c123422p+0, 0x1.44e086061892dp+0,
-    0x1.4bfdad5362a27p+0, 0x1.5342b569d4f82p+0, 0x1.5ab07dd485429p+0, 0x1.6247eb03a5585p+0,
-    0x1.6a09e667f3bcdp+0, 0x1.71f75e8ec5f74p+0, 0x1.7a11473eb0187p+0, 0x1.82589994cce13p+0,
-    0x1.8ace5422aa0dbp+0, 0x1.93737b0cdc5e5p+0, 0x1.9c49182a3f090p+0, 0x1.a5503b23e255dp+0,
-    0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
-    0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0,
+constexpr int kExpTabN = 64;
+static __constant__ double kExp2Tab[kExpTabN] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0, 0x1.0874518759bc8p+0,
+    0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0, 0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0,
+    0x1.172b83c7d517bp+0, 0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0, 0x1.2d285a6e4030bp+0,
+    0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0, 0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0,
+    0x1.3dea64c123422p+0, 0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0, 0x1.56f4736b527dap+0,
+    0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0, 0x1.6247eb03a5585p+0, 0x1.6623882552225p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0, 0x1.868d99b4492edp+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0, 0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0,
+    0x1.9c49182a3f090p+0, 0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0, 0x1.bcc1e904bc1d2p+0,
+    0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0, 0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0,
+    0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0,
 };
 __device__ __forceinline__ double exp_tab(double a, const double* tab)
 {
     const long long ab = __double_as_longlong(a);
     if (((ab >> 52) & 0x7ff) >= 1032) return exp(a);  // |a| >= 512
     const double sh = 0x1.8p52;  // adding it rounds to an integer
-    const double ks = fma(a, 0x1.71547652b82fep+5, sh);  // 32/ln2
+    const double ks = fma(a, 0x1.71547652b82fep+6, sh);  // 64/ln2
     const int k = (int)(__double_as_longlong(ks) - __double_as_longlong(sh));
     const double kd = ks - sh;
-    double r = fma(-kd, 0x1.62e42fee00000p-6, a);  // head of ln2/32
-    r = fma(-kd, 0x1.a39ef35793c76p-38, r);         // its tail
-    double q = fma(r, 0x1.6c16c16c16c17p-10, 0x1.1111111111111p-7);  // 1/720, 1/120
-    q = fma(r, q, 0x1.5555555555555p-5);                               // 1/24
+    double r = fma(-kd, 0x1.62e42fee00000p-7, a);  // head of ln2/64
+    r = fma(-kd, 0x1.a39ef35793c76p-39, r);          // its tail
+    double q = fma(r, 0x1.1111111111111p-7, 0x1.5555555555555p-5);  // 1/120, 1/24
     q = fma(r, q, 0x1.5555555555555p-3);                               // 1/6
     q = fma(r, q, 0.5);
     const double p = fma(r * r, q, r);
-    const double t = tab[k & 31];
+    const double t = tab[k & (kExpTabN - 1)];
     const double e = fma(t, p, t);
-    return __longlong_as_double(__double_as_longlong(e) + ((long long)(k >> 5) << 52));
+    return __longlong_as_double(__double_as_longlong(e) + ((long long)(k >> 6) << 52));
 }
 
 // ---------------------------------------------------------------------------

@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(kDfThreads) k_ff_exp(const double* __restrict_
 __global__ void __launch_bounds__(kDfThreads) k_exp_tab(const double* __restrict__ t, int64_t n,
                                                         double* __restrict__ out)
 {
-    __shared__ double tab[32];
-    if (threadIdx.x < 32) tab[threadIdx.x] = kExp2Tab[threadIdx.x];
+    __shared__ double tab[kExpTabN];
+    if (threadIdx.x < kExpTabN) tab[threadIdx.x] = kExp2Tab[threadIdx.x];
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)

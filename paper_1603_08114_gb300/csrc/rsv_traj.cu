@@ -56,9 +56,9 @@ __global__ void __launch_bounds__(256, 1) k_traj_fp64(const TrajArgs A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_wseg[NWMAX], s_wacc[NWMAX], s_flag;
     __shared__ double s_wpart[NWMAX], s_red[32], s_edge[4 * NWMAX], s_split;
-    __shared__ double s_e2[32];  // 2^(j/32), the table of exp_tab
+    __shared__ double s_e2[kExpTabN];  // 2^(j/64), the table of exp_tab
     const int NT = blockDim.x, W = NT * J, nw = NT >> 5, tid = threadIdx.x;
-    if (tid < 32) s_e2[tid] = kExp2Tab[tid];  // read after load_bin's barriers
+    if (tid < kExpTabN) s_e2[tid] = kExp2Tab[tid];  // read after load_bin's barriers
     double* s_a = reinterpret_cast<double*>(smem_raw);
     double* s_kc = s_a + W;
     double* s_mi = s_kc + W;
