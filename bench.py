@@ -962,7 +962,12 @@ def run_ours(args):
             "learned": learned_info,
             "learned_vs_identity": learned_cmp,
             "c1": c1, "c4": c4, "table2": t2,
-            "batched": batched,
+            "batched": None if batched is None else dict(batched, roofline={
+                "bound": "alu", "unit": "Top/s", "peak": fp32_peak / 1e12,
+                "achieved": batched["site_updates_per_s"] * ALG_OPS_PER_SITE_STEP / 1e12,
+                "frac": batched["site_updates_per_s"] * ALG_OPS_PER_SITE_STEP / fp32_peak,
+                "how": "the method's 10 FP32 operations per site-step of all series over a "
+                       "trajectory's time, against the measured FP32 FMA rate"}),
             "leverage": levr,
             "mixed_omelyan2": None if mn is None else {
                 tag: arm_summary(r, {"integrator": "minimum-norm (Omelyan), 2 force "
