@@ -247,7 +247,11 @@ rsv_status rsv_hmc_trajectory(rsv_ctx* ctx, double* h, double* p, const double* 
  *  fallback_window: if > 0 and minv != NULL, after every fallback_window
  *          trajectories the mass is switched to m = 1 for the rest of the
  *          call when that window's acceptance rate is below 0.6.
- *  mass_used_out: device int32 scalar (1 while the mass is in use), or NULL. */
+ *  mass_used_out: device int32 scalar (1 while the mass is in use), or NULL.
+ * In RSV_MIXED precision on the model without leverage the whole call runs as
+ * one persistent cooperative launch when the plan's tiles can all be resident
+ * (see rsv_set_persistent, rsv_chain_schedule); the results equal those of
+ * one launch per trajectory bit for bit. */
 rsv_status rsv_hmc_chain(rsv_ctx* ctx, double* h, const double* y, const double* lnrv, int64_t T,
                          double* theta, const float* minv, int n_md, double dtau,
                          rsv_precision prec, uint64_t seed, uint64_t traj0, int64_t n_traj,
